@@ -1,0 +1,145 @@
+/*
+ * bez.h -- C ABI of libbez.so: batched evaluation of Bezier curves, C0
+ * piecewise chains, B-splines / NURBS, tensor-product surfaces and volumes,
+ * and the adjoint of curve evaluation, on an NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow "A Texture Lookup Approach to Bezier Curve
+ * Evaluation on the GPU" (Anas & Wolfe): a curve is evaluated at many
+ * parameter values either in registers (power-basis Horner, Bernstein sum,
+ * de Casteljau, Seiler interpolation) or by hardware-filtered texture lookups
+ * of de Casteljau / Seiler control textures.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Arrays are contiguous, row-major, caller-owned.  A pointer may be device
+ *   memory (cudaMalloc / torch CUDA tensor) or host memory (pageable or
+ *   pinned).  Host arrays are staged through library-owned device buffers:
+ *   inputs are copied in on `stream`, outputs copied back, and the call then
+ *   synchronises `stream` before returning so the host output is valid.
+ *   With device arrays only, calls are asynchronous on `stream` unless
+ *   opts->sync is nonzero.  The library never frees or retains caller arrays.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * - Argument errors are found on the host before any launch: the call returns
+ *   BEZ_ERR_INVALID_ARG (or BEZ_ERR_UNSUPPORTED for a valid but unsupported
+ *   variant / degree / dtype combination) and leaves outputs untouched.  A
+ *   failed CUDA call returns BEZ_ERR_CUDA, a failed allocation BEZ_ERR_OOM;
+ *   bez_last_error() gives the message.
+ * - Parameters outside the domain are clamped to it (t in [0,1] for curves,
+ *   [0,n_seg] for chains, [U_p, U_n] for splines); NaN propagates to the
+ *   output.  Empty inputs (zero curves or zero samples) are valid no-ops.
+ * - Outputs are FP32.  Control points are FP32 unless opts->dtype selects
+ *   FP16 / BF16 storage (math stays FP32).
+ */
+#ifndef BEZ_H
+#define BEZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bez_status {
+    BEZ_OK = 0,
+    BEZ_ERR_INVALID_ARG = 1,
+    BEZ_ERR_UNSUPPORTED = 2,
+    BEZ_ERR_CUDA = 3,
+    BEZ_ERR_OOM = 4,
+    BEZ_ERR_TIMEOUT = 5
+} bez_status;
+
+/* Evaluator.  Register forms: paper Sec. 2 (de Casteljau as recursive lerps),
+ * Sec. 3 (Seiler interpolation), Sec. 2.2 (power basis <-> Bernstein; the
+ * "Polynomial" shader of Sec. 5).  Texture forms: Sec. 2 (de Casteljau
+ * tiles), Sec. 4 (Seiler tiles), Fig. 3 (hybrid). */
+typedef enum bez_variant {
+    BEZ_VAR_AUTO = 0,            /* library choice (currently BEZ_VAR_SEILER)           */
+    BEZ_VAR_HORNER = 1,          /* power basis about t=0, Horner, FP32 (baseline)       */
+    BEZ_VAR_HORNER_CENTRED = 2,  /* power basis about t=1/2, Horner                      */
+    BEZ_VAR_BERNSTEIN = 3,       /* Bernstein polynomial sum                             */
+    BEZ_VAR_DECASTELJAU = 4,     /* de Casteljau, d(d+1)/2 lerps                          */
+    BEZ_VAR_SEILER = 5,          /* Seiler interpolation, d lerps                         */
+    BEZ_VAR_TEX_DECASTELJAU = 6, /* tex3D 2x2x2 de Casteljau tile (+ register levels)    */
+    BEZ_VAR_TEX_SEILER = 7,      /* tex2D (d=2,3) / tex3D (d=4,5) Seiler tile            */
+    BEZ_VAR_TEX_HYBRID = 8,      /* two bilinear reads + FP32 lerp (cubic)               */
+    BEZ_VAR_TENSOR = 9           /* surfaces / volumes: tensor-core contraction          */
+} bez_variant;
+
+typedef enum bez_dtype { BEZ_F32 = 0, BEZ_F16 = 1, BEZ_BF16 = 2 } bez_dtype;
+
+typedef enum bez_out_mode {
+    BEZ_OUT_POINTS = 0,          /* out [n_curves][n_t][dim]                              */
+    BEZ_OUT_POLYLINE_LENGTH = 1  /* out [n_curves] = sum_{j>=1} |P_j - P_{j-1}|, FP32 acc */
+} bez_out_mode;
+
+typedef enum bez_t_mode {
+    BEZ_T_SHARED = 0,    /* t [n_t], same parameters for every curve                   */
+    BEZ_T_PER_CURVE = 1, /* t [n_curves][n_t]                                          */
+    BEZ_T_UNIFORM = 2,   /* t_j = fl32(j) / fl32(n_t - 1) (0 when n_t == 1); t unused   */
+    BEZ_T_HASH = 3       /* t drawn in-kernel (lowbias32 counter hash of seed, stream,   *
+                          * curve, j); t unused.  See bez_eval.                         */
+} bez_t_mode;
+
+typedef struct bez_opts {
+    int32_t variant;   /* bez_variant                                                   */
+    int32_t dtype;     /* bez_dtype of the control points                               */
+    int32_t out_mode;  /* bez_out_mode                                                  */
+    int32_t t_mode;    /* bez_t_mode                                                    */
+    uint64_t seed;     /* BEZ_T_HASH only                                               */
+    uint32_t stream_id;/* BEZ_T_HASH only: independent parameter stream under one seed  */
+    int32_t sync;      /* nonzero: synchronise `stream` before returning                 */
+    int32_t* err_word; /* device int32 or NULL: incremented for data faults (NURBS zero  *
+                        * denominators)                                                 */
+} bez_opts;
+
+/* Opaque context: owns staging buffers, texture atlases, timing events. */
+typedef struct bez_ctx_s* bez_ctx;
+
+/* Create a context on CUDA device `device` (makes it current on this thread). */
+bez_status bez_create(bez_ctx* ctx, int device);
+/* Destroy a context and everything it owns; waits for its pending work. */
+bez_status bez_destroy(bez_ctx ctx);
+/* Message for the last non-OK status returned on the calling thread. */
+const char* bez_last_error(void);
+/* Library version string. */
+const char* bez_version(void);
+
+/* Launch accounting.  `launches` counts every kernel this context launched
+ * since the last reset.  With timing enabled, the main evaluator kernel of
+ * every call is bracketed by CUDA events on the launching stream;
+ * bez_get_stats waits for those events and reports their count and summed
+ * duration. */
+typedef struct bez_stats {
+    int64_t launches;
+    int64_t timed_launches;
+    double timed_ms;
+} bez_stats;
+bez_status bez_set_timing(bez_ctx ctx, int enable);
+bez_status bez_get_stats(bez_ctx ctx, bez_stats* out);
+bez_status bez_reset_stats(bez_ctx ctx);
+
+/*
+ * bez_eval -- Bezier curves at many parameters.
+ *
+ * Paper Sec. 2 (de Casteljau recursion, pixel-centre t remap), Sec. 2.2
+ * (power basis <-> Bernstein), Sec. 3 (Seiler interpolation, arbitrary
+ * degree via the difference terms d_i), Sec. 4 (Seiler textures).
+ *
+ *   ctrl  [n_curves][degree+1][dim], element type opts->dtype
+ *   t     per opts->t_mode (NULL for UNIFORM / HASH)
+ *   out   POINTS: [n_curves][n_t][dim] FP32;  POLYLINE_LENGTH: [n_curves] FP32
+ *   degree 1..15 for register variants; dim 1..4.
+ *
+ * BEZ_T_HASH draws t_(c,j) = (h >> 9) * 2^-23 with
+ *   h = H(H(key ^ c) ^ j),  key = H(lo(seed) ^ H(hi(seed) ^ H(stream_id))),
+ *   H = lowbias32 (Wellons 2018: x^=x>>16; x*=0x7feb352d; x^=x>>15;
+ *   x*=0x846ca68b; x^=x>>16), c < 2^32, j < 2^32.
+ */
+bez_status bez_eval(bez_ctx ctx, const void* ctrl, int64_t n_curves, int degree, int dim,
+                    const float* t, int64_t n_t, float* out, const bez_opts* opts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEZ_H */

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libbez.so (C ABI in include/bez.h).
+
+Argument marshalling only: every step of evaluation runs in the library's
+CUDA kernels.  Arrays are torch tensors (CUDA or CPU; CPU tensors are staged
+by the library itself) or NumPy arrays (host).  The binding never falls back
+to a CPU implementation: if libbez.so is missing or no CUDA device is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbez.so")
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    INVALID_ARG = 1
+    UNSUPPORTED = 2
+    CUDA = 3
+    OOM = 4
+    TIMEOUT = 5
+
+
+class Variant(enum.IntEnum):
+    AUTO = 0
+    HORNER = 1
+    HORNER_CENTRED = 2
+    BERNSTEIN = 3
+    DECASTELJAU = 4
+    SEILER = 5
+    TEX_DECASTELJAU = 6
+    TEX_SEILER = 7
+    TEX_HYBRID = 8
+    TENSOR = 9
+
+
+class DType(enum.IntEnum):
+    F32 = 0
+    F16 = 1
+    BF16 = 2
+
+
+class OutMode(enum.IntEnum):
+    POINTS = 0
+    POLYLINE_LENGTH = 1
+
+
+class TMode(enum.IntEnum):
+    SHARED = 0
+    PER_CURVE = 1
+    UNIFORM = 2
+    HASH = 3
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("dtype", ctypes.c_int32), ("out_mode", ctypes.c_int32),
+                ("t_mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
+                ("sync", ctypes.c_int32), ("err_word", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64), ("timed_ms", ctypes.c_double)]
+
+
+class BezError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{Status(status).name}: {msg}")
+        self.status = Status(status)
+
+
+_lib = None
+_lib_lock = threading.Lock()
+_VP, _I64, _INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+
+
+def lib():
+    """Load libbez.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libbez.so not found at {LIB_PATH}: build it with "
+                                   "`python -m paper_2603_15447_gb300.build` (needs nvcc)")
+            L = ctypes.CDLL(LIB_PATH)
+            L.bez_version.restype = ctypes.c_char_p
+            L.bez_last_error.restype = ctypes.c_char_p
+            L.bez_create.argtypes = [ctypes.POINTER(_VP), _INT]
+            L.bez_destroy.argtypes = [_VP]
+            L.bez_set_timing.argtypes = [_VP, _INT]
+            L.bez_get_stats.argtypes = [_VP, ctypes.POINTER(Stats)]
+            L.bez_reset_stats.argtypes = [_VP]
+            L.bez_eval.argtypes = [_VP, _VP, _I64, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts), _VP]
+            for name in ("bez_create", "bez_destroy", "bez_set_timing", "bez_get_stats", "bez_reset_stats",
+                         "bez_eval"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise BezError(st, lib().bez_last_error().decode())
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    """Raw address of a contiguous torch tensor / NumPy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous, "arrays must be C-contiguous"
+        return x.ctypes.data
+    assert x.is_contiguous(), "tensors must be contiguous"
+    return x.data_ptr()
+
+
+def _is_cuda(x):
+    return x is not None and not isinstance(x, np.ndarray) and x.is_cuda
+
+
+def _stream_handle(stream, device):
+    torch = _torch()
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(x):
+    if isinstance(x, np.ndarray):
+        m = {np.dtype(np.float32): DType.F32, np.dtype(np.float16): DType.F16}
+        return m[x.dtype]
+    torch = _torch()
+    m = {torch.float32: DType.F32, torch.float16: DType.F16, torch.bfloat16: DType.BF16}
+    if x.dtype not in m:
+        raise TypeError(f"control points must be float32/float16/bfloat16, got {x.dtype}")
+    return m[x.dtype]
+
+
+def _empty_like_location(ref, shape):
+    torch = _torch()
+    if isinstance(ref, np.ndarray):
+        return np.empty(shape, np.float32)
+    return torch.empty(shape, dtype=torch.float32, device=ref.device)
+
+
+class Context:
+    """A libbez context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = _VP()
+        _check(lib().bez_create(ctypes.byref(h), device))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().bez_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_timing(self, on: bool):
+        _check(lib().bez_set_timing(self.handle, int(on)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().bez_get_stats(self.handle, ctypes.byref(s)))
+        return {"launches": s.launches, "timed_launches": s.timed_launches, "timed_ms": s.timed_ms}
+
+    def reset_stats(self):
+        _check(lib().bez_reset_stats(self.handle))
+
+
+_contexts: dict[int, Context] = {}
+
+
+def context(device: int | None = None) -> Context:
+    if device is None:
+        device = _torch().cuda.current_device()
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+def _opts(variant, dtype, out_mode, t_mode, seed, stream_id, sync):
+    return Opts(int(variant), int(dtype), int(out_mode), int(t_mode), int(seed) & (2 ** 64 - 1),
+                int(stream_id) & 0xFFFFFFFF, int(sync), None)
+
+
+# ---------------------------------------------------------------- entry points
+
+def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.POINTS, t_mode=None,
+             seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None):
+    """Evaluate Bezier curves ``ctrl`` [n_curves][degree+1][dim].
+
+    ``t``: [n_t] (shared) or [n_curves][n_t] (per curve), or None with
+    ``t_mode`` UNIFORM / HASH and ``n_t`` given.  Returns points
+    [n_curves][n_t][dim] or polyline lengths [n_curves] (FP32), on the same
+    device as ``ctrl``."""
+    n_curves, d1, dim = ctrl.shape
+    if t_mode is None:
+        t_mode = TMode.SHARED if (t is not None and t.ndim == 1) else TMode.PER_CURVE
+    if t is not None:
+        n_t = t.shape[-1]
+    assert n_t is not None, "n_t is required when t is None"
+    shape = (n_curves, n_t, dim) if out_mode == OutMode.POINTS else (n_curves,)
+    if out is None:
+        out = _empty_like_location(ctrl, shape)
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
+    _check(lib().bez_eval(c.handle, _ptr(ctrl), n_curves, d1 - 1, dim, _ptr(t), n_t, _ptr(out), ctypes.byref(o),
+                          _stream_handle(stream, dev)))
+    return out

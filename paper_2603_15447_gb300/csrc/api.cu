@@ -1,0 +1,383 @@
+// api.cu -- host runtime of libbez.so: contexts, argument validation, host
+// staging, launch accounting and dispatch to the kernels.  The C ABI is
+// declared in include/bez.h.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "../../include/bez.h"
+#include "internal.h"
+
+using namespace bez;
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+static bez_status fail(bez_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static bez_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(BEZ_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(BEZ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BEZ_CUDA(call, what)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
+    } while (0)
+
+// ---------------------------------------------------------------- context
+
+struct StageBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct bez_ctx_s {
+    int device = 0;
+    int sm_count = 0;
+    bool timing = false;
+    int64_t launches = 0;
+    int64_t timed_launches = 0;
+    double timed_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> spare;
+    cudaEvent_t cur_begin = nullptr;
+    StageBuf stage[8];
+    std::mutex mu;
+};
+
+namespace {
+
+cudaEvent_t take_event(bez_ctx c)
+{
+    if (!c->spare.empty()) {
+        cudaEvent_t e = c->spare.back();
+        c->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void hook_begin(void* self, cudaStream_t s)
+{
+    bez_ctx c = static_cast<bez_ctx>(self);
+    c->launches += 1;
+    if (!c->timing) return;
+    c->cur_begin = take_event(c);
+    cudaEventRecord(c->cur_begin, s);
+}
+
+void hook_end(void* self, cudaStream_t s)
+{
+    bez_ctx c = static_cast<bez_ctx>(self);
+    if (!c->timing || !c->cur_begin) return;
+    cudaEvent_t e = take_event(c);
+    cudaEventRecord(e, s);
+    c->pending.emplace_back(c->cur_begin, e);
+    c->cur_begin = nullptr;
+}
+
+LaunchHooks hooks_of(bez_ctx c) { return LaunchHooks{hook_begin, hook_end, c, c->sm_count}; }
+
+enum MemKind { MEM_NULL, MEM_DEVICE, MEM_HOST };
+
+MemKind classify(const void* p)
+{
+    if (!p) return MEM_NULL;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MEM_HOST;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? MEM_DEVICE : MEM_HOST;
+}
+
+bez_status ensure_stage(bez_ctx c, int slot, size_t bytes, cudaStream_t s)
+{
+    StageBuf& b = c->stage[slot];
+    if (b.cap >= bytes) return BEZ_OK;
+    if (b.p) {
+        BEZ_CUDA(cudaStreamSynchronize(s), "staging resize sync");
+        BEZ_CUDA(cudaFree(b.p), "cudaFree staging");
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t cap = bytes < (1u << 20) ? (1u << 20) : bytes + bytes / 4;
+    BEZ_CUDA(cudaMalloc(&b.p, cap), "cudaMalloc staging");
+    b.cap = cap;
+    return BEZ_OK;
+}
+
+// Staging plan of one call: host arrays are copied to device buffers owned by
+// the context, outputs are copied back after the kernels.
+struct Staging {
+    bez_ctx c;
+    cudaStream_t s;
+    bool any_host = false;
+    struct Out {
+        void* host;
+        void* dev;
+        size_t bytes;
+    };
+    std::vector<Out> outs;
+
+    bez_status in(const void* p, size_t bytes, int slot, const void** dev)
+    {
+        MemKind k = classify(p);
+        if (k != MEM_HOST) {
+            *dev = p;
+            return BEZ_OK;
+        }
+        any_host = true;
+        if (bytes == 0) {
+            *dev = p;
+            return BEZ_OK;
+        }
+        bez_status st = ensure_stage(c, slot, bytes, s);
+        if (st != BEZ_OK) return st;
+        BEZ_CUDA(cudaMemcpyAsync(c->stage[slot].p, p, bytes, cudaMemcpyHostToDevice, s), "copy input to device");
+        *dev = c->stage[slot].p;
+        return BEZ_OK;
+    }
+
+    bez_status out(void* p, size_t bytes, int slot, void** dev)
+    {
+        MemKind k = classify(p);
+        if (k != MEM_HOST) {
+            *dev = p;
+            return BEZ_OK;
+        }
+        any_host = true;
+        if (bytes == 0) {
+            *dev = p;
+            return BEZ_OK;
+        }
+        bez_status st = ensure_stage(c, slot, bytes, s);
+        if (st != BEZ_OK) return st;
+        *dev = c->stage[slot].p;
+        outs.push_back({p, c->stage[slot].p, bytes});
+        return BEZ_OK;
+    }
+
+    bez_status finish(int sync)
+    {
+        for (auto& o : outs)
+            BEZ_CUDA(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, s), "copy output to host");
+        if (any_host || sync) BEZ_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+        return BEZ_OK;
+    }
+};
+
+size_t dtype_size(int dt) { return dt == BEZ_F32 ? 4 : 2; }
+
+bez_status check_common(bez_ctx c, const bez_opts* o)
+{
+    if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
+    if (!o) return fail(BEZ_ERR_INVALID_ARG, "null opts");
+    if (o->dtype < BEZ_F32 || o->dtype > BEZ_BF16) return fail(BEZ_ERR_INVALID_ARG, "bad dtype %d", o->dtype);
+    if (o->out_mode < BEZ_OUT_POINTS || o->out_mode > BEZ_OUT_POLYLINE_LENGTH)
+        return fail(BEZ_ERR_INVALID_ARG, "bad out_mode %d", o->out_mode);
+    if (o->t_mode < BEZ_T_SHARED || o->t_mode > BEZ_T_HASH) return fail(BEZ_ERR_INVALID_ARG, "bad t_mode %d", o->t_mode);
+    if (o->variant < BEZ_VAR_AUTO || o->variant > BEZ_VAR_TENSOR)
+        return fail(BEZ_ERR_INVALID_ARG, "bad variant %d", o->variant);
+    return BEZ_OK;
+}
+
+}  // namespace
+
+namespace bez {
+
+int persistent_grid(const void* kernel, int block, size_t smem, int sm_count, int64_t work_blocks)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(kernel);
+        if (it != cache.end()) per_sm = it->second;
+    }
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        std::lock_guard<std::mutex> g(mu);
+        cache[kernel] = per_sm;
+    }
+    int64_t full = (int64_t)per_sm * sm_count;
+    if (work_blocks < 1) work_blocks = 1;
+    return (int)(work_blocks < full ? work_blocks : full);
+}
+
+}  // namespace bez
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* bez_version(void) { return "bez 0.1 (sm_103a)"; }
+
+const char* bez_last_error(void) { return g_last_error.c_str(); }
+
+bez_status bez_create(bez_ctx* out, int device)
+{
+    if (!out) return fail(BEZ_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    int n = 0;
+    BEZ_CUDA(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(BEZ_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, n);
+    BEZ_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    cudaDeviceProp prop;
+    BEZ_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+    if (prop.major < 10) return fail(BEZ_ERR_UNSUPPORTED, "device %d is sm_%d%d; this build targets sm_103a", device,
+                                     prop.major, prop.minor);
+    bez_ctx c = new bez_ctx_s();
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    *out = c;
+    return BEZ_OK;
+}
+
+bez_status bez_destroy(bez_ctx c)
+{
+    if (!c) return BEZ_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& pr : c->pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto e : c->spare) cudaEventDestroy(e);
+    for (auto& b : c->stage)
+        if (b.p) cudaFree(b.p);
+    delete c;
+    return BEZ_OK;
+}
+
+bez_status bez_set_timing(bez_ctx c, int enable)
+{
+    if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
+    c->timing = enable != 0;
+    return BEZ_OK;
+}
+
+bez_status bez_get_stats(bez_ctx c, bez_stats* out)
+{
+    if (!c || !out) return fail(BEZ_ERR_INVALID_ARG, "null argument");
+    for (auto& pr : c->pending) {
+        BEZ_CUDA(cudaEventSynchronize(pr.second), "cudaEventSynchronize");
+        float ms = 0.f;
+        BEZ_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second), "cudaEventElapsedTime");
+        c->timed_ms += ms;
+        c->timed_launches += 1;
+        c->spare.push_back(pr.first);
+        c->spare.push_back(pr.second);
+    }
+    c->pending.clear();
+    out->launches = c->launches;
+    out->timed_launches = c->timed_launches;
+    out->timed_ms = c->timed_ms;
+    return BEZ_OK;
+}
+
+bez_status bez_reset_stats(bez_ctx c)
+{
+    bez_stats tmp;
+    bez_status st = bez_get_stats(c, &tmp);
+    if (st != BEZ_OK) return st;
+    c->launches = 0;
+    c->timed_launches = 0;
+    c->timed_ms = 0.0;
+    return BEZ_OK;
+}
+
+bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, int dim, const float* t, int64_t n_t,
+                    float* out, const bez_opts* o, void* stream)
+{
+    bez_status st = check_common(c, o);
+    if (st != BEZ_OK) return st;
+    if (n_curves < 0 || n_t < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n_t > 0x7fffffff) return fail(BEZ_ERR_INVALID_ARG, "n_t %lld exceeds 2^31-1", (long long)n_t);
+    if (o->t_mode == BEZ_T_HASH && n_curves > 0xffffffffLL)
+        return fail(BEZ_ERR_INVALID_ARG, "hash parameters index curves with 32 bits");
+    if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
+    if (degree < 1) return fail(BEZ_ERR_INVALID_ARG, "degree %d < 1", degree);
+    int var = o->variant == BEZ_VAR_AUTO ? BEZ_VAR_SEILER : o->variant;
+    if (var > BEZ_VAR_SEILER) return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for bez_eval", var);
+    if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
+    if (n_curves == 0 || (n_t == 0 && o->out_mode == BEZ_OUT_POINTS)) return BEZ_OK;
+    if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");
+    const bool t_array = o->t_mode == BEZ_T_SHARED || o->t_mode == BEZ_T_PER_CURVE;
+    if (t_array && n_t > 0 && !t) return fail(BEZ_ERR_INVALID_ARG, "null t for t_mode %d", o->t_mode);
+
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    CurveArgs a{};
+    const size_t ctrl_bytes = (size_t)n_curves * (degree + 1) * dim * dtype_size(o->dtype);
+    st = stg.in(ctrl, ctrl_bytes, 0, &a.ctrl);
+    if (st != BEZ_OK) return st;
+    if (t_array) {
+        const size_t tb = (size_t)n_t * sizeof(float) * (o->t_mode == BEZ_T_PER_CURVE ? (size_t)n_curves : 1);
+        const void* td = nullptr;
+        st = stg.in(t, tb, 1, &td);
+        if (st != BEZ_OK) return st;
+        a.t = static_cast<const float*>(td);
+        a.t_stride = o->t_mode == BEZ_T_PER_CURVE ? n_t : 0;
+    }
+    const size_t out_bytes =
+        o->out_mode == BEZ_OUT_POINTS ? (size_t)n_curves * n_t * dim * sizeof(float) : (size_t)n_curves * sizeof(float);
+    void* od = nullptr;
+    st = stg.out(out, out_bytes, 2, &od);
+    if (st != BEZ_OK) return st;
+    a.out = static_cast<float*>(od);
+    a.dtype = o->dtype;
+    a.degree = degree;
+    a.dim = dim;
+    a.n_t = (int32_t)n_t;
+    a.n_curves = n_curves;
+    const uint32_t seed_lo = (uint32_t)(o->seed & 0xffffffffu), seed_hi = (uint32_t)(o->seed >> 32);
+    a.key = lowbias32(seed_lo ^ lowbias32(seed_hi ^ lowbias32(o->stream_id)));
+    const int tm = t_array ? TM_ARRAY : (o->t_mode == BEZ_T_UNIFORM ? TM_UNIFORM : TM_HASH);
+    const int om = o->out_mode == BEZ_OUT_POINTS ? OM_POINTS : OM_LENGTH;
+
+    LaunchHooks h = hooks_of(c);
+    LaunchResult r{0, cudaSuccess};
+    switch (var) {
+    case BEZ_VAR_HORNER: r = launch_curve_horner(a, tm, om, s, h); break;
+    case BEZ_VAR_HORNER_CENTRED: r = launch_curve_horner_centred(a, tm, om, s, h); break;
+    case BEZ_VAR_BERNSTEIN: r = launch_curve_bernstein(a, tm, om, s, h); break;
+    case BEZ_VAR_DECASTELJAU: r = launch_curve_decasteljau(a, tm, om, s, h); break;
+    default: r = launch_curve_seiler(a, tm, om, s, h); break;
+    }
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
+    return stg.finish(o->sync);
+}
+
+}  // extern "C"

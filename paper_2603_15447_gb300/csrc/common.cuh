@@ -1,0 +1,76 @@
+// common.cuh -- device helpers shared by the libbez kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bez {
+
+constexpr int kMaxDegree = 15;   // register evaluators: degree 1..15
+constexpr unsigned kFull = 0xffffffffu;
+
+// parameter-stream kinds as seen by kernels (the C enum's SHARED / PER_CURVE
+// both become TM_ARRAY with a per-curve stride of 0 or n_t)
+enum { TM_ARRAY = 0, TM_UNIFORM = 1, TM_HASH = 2 };
+enum { OM_POINTS = 0, OM_LENGTH = 1 };
+enum { VAR_HORNER = 1, VAR_HORNER_CENTRED = 2, VAR_BERNSTEIN = 3, VAR_DECASTELJAU = 4, VAR_SEILER = 5 };
+
+__host__ __device__ constexpr int binom_c(int n, int k)
+{
+    return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : binom_c(n - 1, k - 1) + binom_c(n - 1, k);
+}
+
+// lowbias32 (C. Wellons, 2018): xorshift-multiply integer mixer.
+__host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// 23 high bits of h as a uniform in [0,1): 1.m - 1 is exact in FP32.
+__device__ __forceinline__ float hash_unit(uint32_t h)
+{
+    return __uint_as_float(0x3f800000u | (h >> 9)) - 1.0f;
+}
+
+// a + t (b - a) written as (a - t a) + t b: exact at t = 0 and t = 1, and
+// lerp(a, a, t) == a for every t in [0, 1].
+__device__ __forceinline__ float lerp(float a, float b, float t)
+{
+    return fmaf(t, b, fmaf(-t, a, a));
+}
+
+// clamp to [0,1] keeping NaN (fminf/fmaxf would drop it)
+__device__ __forceinline__ float clamp01(float t)
+{
+    return t < 0.f ? 0.f : (t > 1.f ? 1.f : t);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float load_elem(const void* p, int dtype, int64_t i)
+{
+    if (dtype == 0) return __ldg(static_cast<const float*>(p) + i);
+    if (dtype == 1) return __half2float(static_cast<const __half*>(p)[i]);
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+}  // namespace bez

@@ -1,0 +1,9 @@
+// curve_decasteljau.cu -- instantiates the decasteljau register evaluator (see curve_eval.cuh).
+#include "curve_eval.cuh"
+
+namespace bez {
+LaunchResult launch_curve_decasteljau(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h)
+{
+    return launch_curve_variant<VAR_DECASTELJAU>(a, tm, om, s, h);
+}
+}  // namespace bez

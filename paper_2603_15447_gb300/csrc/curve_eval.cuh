@@ -1,0 +1,602 @@
+// curve_eval.cuh -- register evaluators for Bezier curves and the warp-per-curve
+// kernel that drives them.
+//
+// Each evaluator is a struct with setup(b) (per curve, once) and eval(t, P)
+// (per parameter).  D is the degree when known at compile time, or 0 for the
+// runtime-degree fallback (degree <= kMaxDegree).  DIM is the point dimension.
+//
+//   Horner          power basis about t = 0 (paper Sec. 2.2: power basis <->
+//                   Bernstein); coefficients a_k = binom(d,k) Delta^k b_0.
+//   HornerCentred   power basis about t = 1/2; c_k = binom(d,k) times the
+//                   Bernstein value at 1/2 of the k-th forward differences.
+//   Bernstein       sum_i binom(d,i) (1-t)^(d-i) t^i b_i ("Polynomial" of Sec. 5).
+//   DeCasteljau     d(d+1)/2 lerps at the same t (Sec. 2).
+//   Seiler          C = L(b0, bd, t) + st D_1, D_i = L(d_i, d_(d-i), t) + st D_(i+1)
+//                   (Sec. 3.1); d_i from the closed forms for degree <= 5 and
+//                   by exact peeling of the s-power form above that.
+//
+// Setup runs in FP32 up to degree 7 and in FP64 from degree 8 on.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace bez {
+
+template <int D>
+struct Deg {
+    __device__ __forceinline__ static int get(int) { return D; }
+    static constexpr int N = D + 1;  // array extent
+};
+template <>
+struct Deg<0> {
+    __device__ __forceinline__ static int get(int d) { return d; }
+    static constexpr int N = kMaxDegree + 1;
+};
+
+// ---------------------------------------------------------------- setup helpers
+
+// Forward differences of b (degree d) in place: after the call
+// w[k] = Delta^k b_0 for k = 0..d.  Templated on the arithmetic type S.
+template <typename S, int N>
+__device__ __forceinline__ void forward_differences_at0(S (&w)[N], int d)
+{
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+        if (k > d) break;
+#pragma unroll
+        for (int i = N - 1; i >= 1; --i)
+            if (i >= k && i <= d) w[i] = w[i] - w[i - 1];
+    }
+}
+
+// ---------------------------------------------------------------- evaluators
+
+template <int VAR, int D, int DIM>
+struct Eval;
+
+template <int D, int DIM>
+struct Eval<VAR_HORNER, D, DIM> {
+    static constexpr int N = Deg<D>::N;
+    float a[N][DIM];
+    int d;
+    template <typename S>
+    __device__ __forceinline__ void setup_t(const float (&b)[N][DIM])
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            S w[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) w[i] = (i <= d) ? (S)b[i][k] : (S)0;
+            forward_differences_at0<S, N>(w, d);
+            S bin = 1;  // binom(d, i) built incrementally
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                if (i <= d) a[i][k] = (float)(bin * w[i]);
+                bin = bin * (S)(d - i) / (S)(i + 1);
+            }
+        }
+    }
+    __device__ __forceinline__ void setup(const float (&b)[N][DIM], int deg)
+    {
+        d = Deg<D>::get(deg);
+        if (D == 0 && d >= 8) setup_t<double>(b);
+        else setup_t<float>(b);
+    }
+    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            float acc = a[N - 1][k];
+            if (D == 0) acc = a[d][k];
+#pragma unroll
+            for (int i = N - 2; i >= 0; --i)
+                if (i < d) acc = fmaf(acc, t, a[i][k]);
+            P[k] = acc;
+        }
+    }
+};
+
+template <int D, int DIM>
+struct Eval<VAR_HORNER_CENTRED, D, DIM> {
+    static constexpr int N = Deg<D>::N;
+    float a[N][DIM];
+    int d;
+    template <typename S>
+    __device__ __forceinline__ void setup_t(const float (&b)[N][DIM])
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            S w[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) w[i] = (i <= d) ? (S)b[i][k] : (S)0;
+            S bin = 1;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                if (m > d) break;
+                // w[0..d-m] holds Delta^m b; its Bernstein value at 1/2 by halving
+                S h[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) h[i] = w[i];
+#pragma unroll
+                for (int r = 1; r < N; ++r)
+#pragma unroll
+                    for (int i = 0; i < N - 1; ++i)
+                        if (r <= d - m && i <= d - m - r) h[i] = (S)0.5 * (h[i] + h[i + 1]);
+                a[m][k] = (float)(bin * h[0]);
+                bin = bin * (S)(d - m) / (S)(m + 1);
+#pragma unroll
+                for (int i = 0; i < N - 1; ++i)
+                    if (i < d - m) w[i] = w[i + 1] - w[i];
+            }
+        }
+    }
+    __device__ __forceinline__ void setup(const float (&b)[N][DIM], int deg)
+    {
+        d = Deg<D>::get(deg);
+        if (D == 0 && d >= 8) setup_t<double>(b);
+        else setup_t<float>(b);
+    }
+    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
+    {
+        const float u = t - 0.5f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            float acc = a[N - 1][k];
+            if (D == 0) acc = a[d][k];
+#pragma unroll
+            for (int i = N - 2; i >= 0; --i)
+                if (i < d) acc = fmaf(acc, u, a[i][k]);
+            P[k] = acc;
+        }
+    }
+};
+
+template <int D, int DIM>
+struct Eval<VAR_BERNSTEIN, D, DIM> {
+    static constexpr int N = Deg<D>::N;
+    float p[N][DIM];  // binom(d,i) b_i
+    int d;
+    __device__ __forceinline__ void setup(const float (&b)[N][DIM], int deg)
+    {
+        d = Deg<D>::get(deg);
+        float bin = 1.f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) p[i][k] = bin * b[i][k];
+            bin = bin * (float)(d - i) / (float)(i + 1);
+        }
+    }
+    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
+    {
+        const float s = 1.0f - t;
+        float tp[N], sp[N];
+        tp[0] = 1.f;
+        sp[0] = 1.f;
+#pragma unroll
+        for (int i = 1; i < N; ++i) {
+            tp[i] = tp[i - 1] * t;
+            sp[i] = sp[i - 1] * s;
+        }
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) P[k] = 0.f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (i > d) break;
+            const float B = (D == 0) ? tp[i] * sp[d - i] : tp[i] * sp[N - 1 - i];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) P[k] = fmaf(B, p[i][k], P[k]);
+        }
+    }
+};
+
+template <int D, int DIM>
+struct Eval<VAR_DECASTELJAU, D, DIM> {
+    static constexpr int N = Deg<D>::N;
+    float b[N][DIM];
+    int d;
+    __device__ __forceinline__ void setup(const float (&bb)[N][DIM], int deg)
+    {
+        d = Deg<D>::get(deg);
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) b[i][k] = bb[i][k];
+    }
+    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            float w[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) w[i] = b[i][k];
+#pragma unroll
+            for (int r = 1; r < N; ++r)
+#pragma unroll
+                for (int i = 0; i < N - 1; ++i)
+                    if (r <= d && i <= d - r) w[i] = lerp(w[i], w[i + 1], t);
+            P[k] = w[0];
+        }
+    }
+};
+
+// Seiler difference terms.  lo[k] = d_k, hi[k] = d_(d-k) for k = 0..floor(d/2)
+// (lo[0] = b_0, hi[0] = b_d).
+template <int D, int DIM>
+struct Eval<VAR_SEILER, D, DIM> {
+    static constexpr int N = Deg<D>::N;
+    static constexpr int H = N / 2 + 1;
+    float lo[H][DIM], hi[H][DIM];
+    int d;
+
+    // closed forms of Sec. 3.1 (valid for d <= 5)
+    __device__ __forceinline__ void setup_closed(const float (&b)[N][DIM])
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const float b0 = b[0][k], bd = b[d][k];
+            lo[0][k] = b0;
+            hi[0][k] = bd;
+            if (d >= 2) {
+                const float fd = (float)d;
+                lo[1][k] = fd * (b[1][k] - b0) - (bd - b0);
+                hi[1][k] = fd * (b[d - 1][k] - bd) - (b0 - bd);
+            }
+            if (H > 2 && d >= 4) {
+                const float c2 = (float)(d * (d - 1) / 2), c2m = (float)((d - 2) * (d - 3) / 2);
+                const float e = (float)(d - 3);
+                lo[2][k] = c2 * (b[2][k] - b[1][k]) - c2m * (b[1][k] - b0) - e * (b[d - 1][k] - bd) -
+                           3.f * (b[d - 1][k] - b[1][k]);
+                hi[2][k] = c2 * (b[d - 2][k] - b[d - 1][k]) - c2m * (b[d - 1][k] - bd) - e * (b[1][k] - b0) -
+                           3.f * (b[1][k] - b[d - 1][k]);
+            }
+        }
+    }
+
+    // Any degree: peel P = L(P(0), P(1), t) + t(1-t) Q repeatedly in the
+    // Bernstein basis; Q has coefficients q_(j+1) m(m-1)/((j+1)(m-1-j)) where
+    // q_i = c_i - ((1 - i/m) c_0 + (i/m) c_m).
+    template <typename S>
+    __device__ __forceinline__ void setup_peel(const float (&b)[N][DIM])
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            S c[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) c[i] = (i <= d) ? (S)b[i][k] : (S)0;
+            int m = d;
+#pragma unroll
+            for (int lvl = 0; lvl < H; ++lvl) {
+                if (m < 0) break;
+                lo[lvl][k] = (float)c[0];
+                hi[lvl][k] = (float)c[m < 0 ? 0 : m];
+                if (m < 2) break;
+                const S c0 = c[0], cm = c[m];
+                const S mm = (S)m;
+#pragma unroll
+                for (int j = 0; j < N - 2; ++j) {
+                    if (j <= m - 2) {
+                        const S i1 = (S)(j + 1);
+                        const S q = c[j + 1] - (((S)1 - i1 / mm) * c0 + (i1 / mm) * cm);
+                        c[j] = q * (mm * (mm - (S)1)) / (i1 * (mm - (S)1 - (S)j));
+                    }
+                }
+                m -= 2;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void setup(const float (&b)[N][DIM], int deg)
+    {
+        d = Deg<D>::get(deg);
+        if (d <= 5) setup_closed(b);
+        else if (d >= 8) setup_peel<double>(b);
+        else setup_peel<float>(b);
+    }
+
+    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
+    {
+        const float st = fmaf(-t, t, t);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            if (D == 1 || (D == 0 && d == 1)) {
+                P[k] = lerp(lo[0][k], hi[0][k], t);
+                continue;
+            }
+            // innermost level kmax = floor(d/2): constant d_(d/2) for even d,
+            // L(d_kmax, d_(d-kmax), t) for odd d
+            float acc;
+            const int kmax = (D ? D : d) / 2;
+            if (D) {
+                constexpr int KM = (D ? D : 2) / 2;
+                acc = (D % 2 == 0) ? lo[KM][k] : lerp(lo[KM][k], hi[KM][k], t);
+#pragma unroll
+                for (int l = KM - 1; l >= 0; --l) acc = fmaf(st, acc, lerp(lo[l][k], hi[l][k], t));
+            } else {
+                acc = (d % 2 == 0) ? lo[kmax][k] : lerp(lo[kmax][k], hi[kmax][k], t);
+                for (int l = kmax - 1; l >= 0; --l) acc = fmaf(st, acc, lerp(lo[l][k], hi[l][k], t));
+            }
+            P[k] = acc;
+        }
+    }
+};
+
+
+// ---------------------------------------------------------------- runtime degree
+
+// Fallback for degrees not instantiated at compile time (and for dim != 3):
+// the same arithmetic as the fixed-degree evaluators, written with plain
+// loops over the runtime degree.  Setup is FP64 from degree 8 on.
+template <int VAR, int DIM>
+struct EvalDyn {
+    static constexpr int N = kMaxDegree + 1;
+    float c[N][DIM];          // Horner / centred: power coeffs; Bernstein: binom*b; dC: b
+    float lo[N / 2 + 1][DIM]; // Seiler d_k
+    float hi[N / 2 + 1][DIM]; // Seiler d_(d-k)
+    int d;
+
+    template <typename S>
+    __device__ void setup_t(const float (&b)[N][DIM])
+    {
+        for (int k = 0; k < DIM; ++k) {
+            S w[N];
+            for (int i = 0; i <= d; ++i) w[i] = (S)b[i][k];
+            if (VAR == VAR_HORNER) {
+                for (int m = 1; m <= d; ++m)
+                    for (int i = d; i >= m; --i) w[i] = w[i] - w[i - 1];
+                S bin = 1;
+                for (int i = 0; i <= d; ++i) {
+                    c[i][k] = (float)(bin * w[i]);
+                    bin = bin * (S)(d - i) / (S)(i + 1);
+                }
+            } else if (VAR == VAR_HORNER_CENTRED) {
+                S bin = 1;
+                for (int m = 0; m <= d; ++m) {
+                    S h[N];
+                    for (int i = 0; i <= d - m; ++i) h[i] = w[i];
+                    for (int r = 1; r <= d - m; ++r)
+                        for (int i = 0; i <= d - m - r; ++i) h[i] = (S)0.5 * (h[i] + h[i + 1]);
+                    c[m][k] = (float)(bin * h[0]);
+                    bin = bin * (S)(d - m) / (S)(m + 1);
+                    for (int i = 0; i < d - m; ++i) w[i] = w[i + 1] - w[i];
+                }
+            } else if (VAR == VAR_SEILER) {
+                int m = d;
+                for (int lvl = 0; m >= 0; ++lvl) {
+                    lo[lvl][k] = (float)w[0];
+                    hi[lvl][k] = (float)w[m];
+                    if (m < 2) break;
+                    const S c0 = w[0], cm = w[m], mm = (S)m;
+                    for (int j = 0; j <= m - 2; ++j) {
+                        const S i1 = (S)(j + 1);
+                        const S q = w[j + 1] - (((S)1 - i1 / mm) * c0 + (i1 / mm) * cm);
+                        w[j] = q * (mm * (mm - (S)1)) / (i1 * (mm - (S)1 - (S)j));
+                    }
+                    m -= 2;
+                }
+            } else if (VAR == VAR_BERNSTEIN) {
+                S bin = 1;
+                for (int i = 0; i <= d; ++i) {
+                    c[i][k] = (float)(bin * w[i]);
+                    bin = bin * (S)(d - i) / (S)(i + 1);
+                }
+            } else {
+                for (int i = 0; i <= d; ++i) c[i][k] = b[i][k];
+            }
+        }
+    }
+    __device__ void setup(const float (&b)[N][DIM], int deg)
+    {
+        d = deg;
+        if (d >= 8 && VAR != VAR_DECASTELJAU && VAR != VAR_BERNSTEIN) setup_t<double>(b);
+        else setup_t<float>(b);
+    }
+    __device__ void eval(float t, float (&P)[DIM]) const
+    {
+        for (int k = 0; k < DIM; ++k) {
+            float acc;
+            if (VAR == VAR_HORNER || VAR == VAR_HORNER_CENTRED) {
+                const float u = VAR == VAR_HORNER ? t : t - 0.5f;
+                acc = c[d][k];
+                for (int i = d - 1; i >= 0; --i) acc = fmaf(acc, u, c[i][k]);
+            } else if (VAR == VAR_BERNSTEIN) {
+                const float s = 1.0f - t;
+                acc = 0.f;
+                for (int i = 0; i <= d; ++i) {
+                    float B = 1.f;
+                    for (int r = 0; r < i; ++r) B *= t;
+                    for (int r = 0; r < d - i; ++r) B *= s;
+                    acc = fmaf(B, c[i][k], acc);
+                }
+            } else if (VAR == VAR_DECASTELJAU) {
+                float w[N];
+                for (int i = 0; i <= d; ++i) w[i] = c[i][k];
+                for (int r = 1; r <= d; ++r)
+                    for (int i = 0; i <= d - r; ++i) w[i] = lerp(w[i], w[i + 1], t);
+                acc = w[0];
+            } else {
+                const float st = fmaf(-t, t, t);
+                const int kmax = d / 2;
+                if (d == 1) acc = lerp(lo[0][k], hi[0][k], t);
+                else {
+                    acc = (d % 2 == 0) ? lo[kmax][k] : lerp(lo[kmax][k], hi[kmax][k], t);
+                    for (int l = kmax - 1; l >= 0; --l) acc = fmaf(st, acc, lerp(lo[l][k], hi[l][k], t));
+                }
+            }
+            P[k] = acc;
+        }
+    }
+};
+
+template <int VAR, int D, int DIM>
+struct Pick {
+    using type = Eval<VAR, D, DIM>;
+};
+template <int VAR, int DIM>
+struct Pick<VAR, 0, DIM> {
+    using type = EvalDyn<VAR, DIM>;
+};
+
+// ---------------------------------------------------------------- kernel
+
+constexpr int kWarps = 8;  // warps per block; one curve per warp per iteration
+
+template <int TM>
+__device__ __forceinline__ float param(const CurveArgs& a, int64_t c, int j, uint32_t kc)
+{
+    if (TM == TM_ARRAY) return clamp01(__ldg(a.t + c * a.t_stride + j));
+    if (TM == TM_UNIFORM) return a.n_t > 1 ? __fdiv_rn((float)j, (float)(a.n_t - 1)) : 0.f;
+    return hash_unit(lowbias32(kc ^ (uint32_t)j));
+}
+
+template <int DIM>
+__device__ __forceinline__ float seg_len(const float (&p)[DIM], const float (&q)[DIM])
+{
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float e = p[k] - q[k];
+        s = fmaf(e, e, s);
+    }
+    return sqrt_approx(s);
+}
+
+template <int VAR, int D, int DIM, int TM, int OM>
+__global__ void __launch_bounds__(kWarps * 32) k_curve(const CurveArgs a)
+{
+    using E = typename Pick<VAR, D, DIM>::type;
+    constexpr int N = E::N;
+    __shared__ float s_ctrl[kWarps * N * DIM];
+    __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * DIM : 1];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int deg = Deg<D>::get(a.degree);
+    const int per = (deg + 1) * DIM;
+
+    for (int64_t base = (int64_t)blockIdx.x * kWarps; base < a.n_curves; base += (int64_t)gridDim.x * kWarps) {
+        // coalesced load of this block's control points into shared memory
+        const int64_t n_here = min((int64_t)kWarps, a.n_curves - base);
+        const int count = (int)n_here * per;
+        for (int i = threadIdx.x; i < count; i += kWarps * 32) s_ctrl[i] = load_elem(a.ctrl, a.dtype, base * per + i);
+        __syncthreads();
+
+        const int64_t c = base + wib;
+        if (c < a.n_curves) {
+            float b[N][DIM];
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) b[i][k] = (i <= deg) ? s_ctrl[wib * per + i * DIM + k] : 0.f;
+            E e;
+            e.setup(b, deg);
+            const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
+            const int n_t = a.n_t;
+
+            if (OM == OM_POINTS) {
+                float* stage = s_stage + wib * 32 * DIM;
+                for (int j0 = 0; j0 < n_t; j0 += 32) {
+                    const int j = j0 + lane;
+                    float P[DIM];
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) P[k] = 0.f;
+                    if (j < n_t) e.eval(param<TM>(a, c, j, kc), P);
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) stage[lane * DIM + k] = P[k];
+                    __syncwarp();
+                    const int valid = min(32, n_t - j0) * DIM;
+                    float* o = a.out + (c * n_t + j0) * DIM;
+#pragma unroll
+                    for (int m = 0; m < DIM; ++m) {
+                        const int idx = lane + 32 * m;
+                        if (idx < valid) o[idx] = stage[idx];
+                    }
+                    __syncwarp();
+                }
+            } else {
+                // each lane walks a contiguous run of samples; the segment
+                // joining two runs is closed with one shuffle
+                const int chunk = (n_t + 31) / 32;
+                const int jb = lane * chunk;
+                const int je = min(jb + chunk, n_t);
+                float acc = 0.f;
+                float first[DIM], prev[DIM];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) first[k] = prev[k] = 0.f;
+                if (jb < je) {
+                    e.eval(param<TM>(a, c, jb, kc), first);
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) prev[k] = first[k];
+#pragma unroll 4
+                    for (int j = jb + 1; j < je; ++j) {
+                        float P[DIM];
+                        e.eval(param<TM>(a, c, j, kc), P);
+                        acc += seg_len<DIM>(P, prev);
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) prev[k] = P[k];
+                    }
+                }
+                float pl[DIM];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) pl[k] = __shfl_up_sync(kFull, prev[k], 1);
+                if (lane > 0 && jb < je) acc += seg_len<DIM>(first, pl);
+                acc = warp_sum(acc);
+                if (lane == 0) a.out[c] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- dispatch
+
+template <int VAR, int D, int DIM, int TM, int OM>
+LaunchResult launch_one(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h)
+{
+    auto kern = k_curve<VAR, D, DIM, TM, OM>;
+    const int64_t work = (a.n_curves + kWarps - 1) / kWarps;
+    const int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    h.begin(h.self, s);
+    kern<<<grid, kWarps * 32, 0, s>>>(a);
+    cudaError_t err = cudaGetLastError();
+    h.end(h.self, s);
+    return {1, err};
+}
+
+template <int VAR, int D, int DIM>
+LaunchResult launch_modes(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h)
+{
+    if (om == OM_POINTS) {
+        if (tm == TM_ARRAY) return launch_one<VAR, D, DIM, TM_ARRAY, OM_POINTS>(a, s, h);
+        if (tm == TM_UNIFORM) return launch_one<VAR, D, DIM, TM_UNIFORM, OM_POINTS>(a, s, h);
+        return launch_one<VAR, D, DIM, TM_HASH, OM_POINTS>(a, s, h);
+    }
+    if (tm == TM_ARRAY) return launch_one<VAR, D, DIM, TM_ARRAY, OM_LENGTH>(a, s, h);
+    if (tm == TM_UNIFORM) return launch_one<VAR, D, DIM, TM_UNIFORM, OM_LENGTH>(a, s, h);
+    return launch_one<VAR, D, DIM, TM_HASH, OM_LENGTH>(a, s, h);
+}
+
+template <int VAR>
+LaunchResult launch_curve_variant(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h)
+{
+    if (a.dim == 3) {
+        switch (a.degree) {
+        case 1: return launch_modes<VAR, 1, 3>(a, tm, om, s, h);
+        case 2: return launch_modes<VAR, 2, 3>(a, tm, om, s, h);
+        case 3: return launch_modes<VAR, 3, 3>(a, tm, om, s, h);
+        case 4: return launch_modes<VAR, 4, 3>(a, tm, om, s, h);
+        case 5: return launch_modes<VAR, 5, 3>(a, tm, om, s, h);
+        case 6: return launch_modes<VAR, 6, 3>(a, tm, om, s, h);
+        case 7: return launch_modes<VAR, 7, 3>(a, tm, om, s, h);
+        default: return launch_modes<VAR, 0, 3>(a, tm, om, s, h);
+        }
+    }
+    switch (a.dim) {
+    case 1: return launch_modes<VAR, 0, 1>(a, tm, om, s, h);
+    case 2: return launch_modes<VAR, 0, 2>(a, tm, om, s, h);
+    default: return launch_modes<VAR, 0, 4>(a, tm, om, s, h);
+    }
+}
+
+}  // namespace bez

@@ -1,0 +1,9 @@
+// curve_horner_centred.cu -- instantiates the horner_centred register evaluator (see curve_eval.cuh).
+#include "curve_eval.cuh"
+
+namespace bez {
+LaunchResult launch_curve_horner_centred(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h)
+{
+    return launch_curve_variant<VAR_HORNER_CENTRED>(a, tm, om, s, h);
+}
+}  // namespace bez
