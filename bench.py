@@ -175,8 +175,11 @@ def run_ours(args, rank, world, local_rank):
 
     results = {}
     headline = args.variant
+    run_variants = [v for v in VARIANTS if v in args.variants.split(",")] if args.variants else list(VARIANTS)
+    if headline not in run_variants:
+        run_variants.append(headline)
     with ClockSampler(local_rank) as clocks:
-        for v in VARIANTS:
+        for v in run_variants:
             ms, st, wall = timed(v, args.steps, args.warmup)
             results[v] = {"ms": ms, "stats": st}
     clock_summary = clocks.summary()
@@ -212,7 +215,7 @@ def run_ours(args, rank, world, local_rank):
     peaks = load_peaks()
     peak, peak_note = alu_peak(peaks)
     variants = {}
-    for v in VARIANTS:
+    for v in run_variants:
         r = results[v]
         st = r["stats"]
         kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
@@ -220,9 +223,9 @@ def run_ours(args, rank, world, local_rank):
         variants[v] = {"points_per_s": pts_per_step * args.steps / (r["ms"] * 1e-3),
                        "ms_per_step": r["ms"] / args.steps, "kernel_ms": kern_ms,
                        "alu_frac": ops / (kern_ms * 1e-3) / peak, "ops_per_point": T_OPS + EVAL_OPS[v] + LEN_OPS}
-    horner = variants["HORNER"]["points_per_s"]
-    for v in VARIANTS:
-        variants[v]["speedup_vs_horner"] = variants[v]["points_per_s"] / horner
+    horner = variants["HORNER"]["points_per_s"] if "HORNER" in variants else None
+    for v in run_variants:
+        variants[v]["speedup_vs_horner"] = variants[v]["points_per_s"] / horner if horner else None
 
     # accuracy on a sample of the same workload (points mode, same parameters)
     if not args.skip_accuracy:
@@ -232,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
         th = oracle.hash_t(seed, synth.PRECISION_T_STREAM, 0, ns, args.n_t)
         ref = oracle.bezier(ctrl_np[:ns], th)
         diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
-        for v in VARIANTS:
+        for v in run_variants:
             pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
                                seed=seed, stream_id=synth.PRECISION_T_STREAM, ctx=ctx)
             err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
@@ -335,6 +338,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", default="HORNER_CENTRED", choices=VARIANTS)
+    ap.add_argument("--variants", default="", help="comma-separated subset of evaluators to time")
     ap.add_argument("--n-curves", type=int, default=N_CURVES)
     ap.add_argument("--n-t", type=int, default=N_T)
     ap.add_argument("--accuracy-curves", type=int, default=4096)

@@ -128,7 +128,13 @@ bez_status bez_reset_stats(bez_ctx ctx);
  *   ctrl  [n_curves][degree+1][dim], element type opts->dtype
  *   t     per opts->t_mode (NULL for UNIFORM / HASH)
  *   out   POINTS: [n_curves][n_t][dim] FP32;  POLYLINE_LENGTH: [n_curves] FP32
- *   degree 1..15 for register variants; dim 1..4.
+ *   degree 1..15 (texture Seiler: 2..5); dim 1..4.
+ *
+ * Texture variants pack the control points into a cudaArray atlas owned by
+ * the context (one surface-write kernel), then evaluate with hardware linear
+ * filtering (one kernel).  dtype F32 gives float4 texels, F16 half4 texels;
+ * BF16 has no texture format (BEZ_ERR_UNSUPPORTED).  Calls of one context
+ * that use the atlases are ordered across streams by the library.
  *
  * BEZ_T_HASH draws t_(c,j) = (h >> 9) * 2^-23 with
  *   h = H(H(key ^ c) ^ j),  key = H(lo(seed) ^ H(hi(seed) ^ H(stream_id))),
@@ -137,6 +143,46 @@ bez_status bez_reset_stats(bez_ctx ctx);
  */
 bez_status bez_eval(bez_ctx ctx, const void* ctrl, int64_t n_curves, int degree, int dim,
                     const float* t, int64_t n_t, float* out, const bez_opts* opts, void* stream);
+
+/*
+ * bez_eval_piecewise -- C0 piecewise Bezier chains.
+ *
+ * Paper Sec. 2.1 (Eq. 1-2, Fig. 2): consecutive segments share end points;
+ * a quadratic chain of N segments fits an (N+1) x 2 texture because the two
+ * diagonal texels of each 2x2 window only need to average to the middle
+ * control point, and the texture is read along a zig-zag path.
+ *
+ *   ctrl  [n_chains][n_seg*degree+1][dim] logical control points (segment k
+ *         uses points k*degree .. k*degree+degree), element type opts->dtype
+ *   t     global parameters in [0, n_seg] per opts->t_mode; segment
+ *         k = min(floor(t), n_seg-1), local parameter t - k.  UNIFORM gives
+ *         t_j = fl32(n_seg * fl32(j)/fl32(n_t-1)); HASH gives
+ *         t = fl32(n_seg * u) with u the bez_eval draw.
+ *   out   POINTS [n_chains][n_t][dim] or POLYLINE_LENGTH [n_chains], FP32
+ *
+ * BEZ_VAR_TEX_DECASTELJAU evaluates quadratic chains (degree 2) from the
+ * zig-zag texture; the free texel of each chain is chosen per component to
+ * minimise the largest texel magnitude.  Register variants take any degree
+ * 1..15 with (n_seg*degree+1)*dim <= 3072; the chain is staged in shared
+ * memory.  Default (AUTO): register de Casteljau.
+ */
+bez_status bez_eval_piecewise(bez_ctx ctx, const void* ctrl, int64_t n_chains, int n_seg, int degree, int dim,
+                              const float* t, int64_t n_t, float* out, const bez_opts* opts, void* stream);
+
+/*
+ * bez_probe_filter -- characterise the texture unit's linear-filter weights.
+ *
+ * Paper Sec. 2.3: the hardware converts texture coordinates to a fixed-point
+ * format with 8 fractional bits before interpolating, which bounds the
+ * accuracy of every texture evaluator.  This call samples a 2x2x2 float4
+ * texture whose texel (x,y,z) holds (x, y, z) with linear filtering and clamp
+ * addressing, so the filtered value at unnormalised coordinates (X, Y, Z) is
+ * the weight the hardware applied along each axis.
+ *
+ *   xyz  [n][3] FP32 coordinates (texel centres at 0.5 and 1.5)
+ *   out  [n][3] FP32 filtered (x, y, z) values
+ */
+bez_status bez_probe_filter(bez_ctx ctx, const float* xyz, int64_t n, float* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -97,8 +97,11 @@ def lib():
             L.bez_get_stats.argtypes = [_VP, ctypes.POINTER(Stats)]
             L.bez_reset_stats.argtypes = [_VP]
             L.bez_eval.argtypes = [_VP, _VP, _I64, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts), _VP]
+            L.bez_probe_filter.argtypes = [_VP, _VP, _I64, _VP, _VP]
+            L.bez_eval_piecewise.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts),
+                                             _VP]
             for name in ("bez_create", "bez_destroy", "bez_set_timing", "bez_get_stats", "bez_reset_stats",
-                         "bez_eval"):
+                         "bez_eval", "bez_probe_filter", "bez_eval_piecewise"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -230,4 +233,39 @@ def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.P
     o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
     _check(lib().bez_eval(c.handle, _ptr(ctrl), n_curves, d1 - 1, dim, _ptr(t), n_t, _ptr(out), ctypes.byref(o),
                           _stream_handle(stream, dev)))
+    return out
+
+
+def bez_probe_filter(xyz, *, out=None, stream=None, ctx=None):
+    """Sample a 2x2x2 texture whose texel (x, y, z) holds (x, y, z) at the
+    unnormalised coordinates ``xyz`` [n][3]; returns the filtered values
+    [n][3], i.e. the hardware's interpolation weights along each axis."""
+    n = xyz.shape[0]
+    if out is None:
+        out = _empty_like_location(xyz, (n, 3))
+    dev = xyz.device.index if _is_cuda(xyz) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    _check(lib().bez_probe_filter(c.handle, _ptr(xyz), n, _ptr(out), _stream_handle(stream, dev)))
+    return out
+
+
+def bez_eval_piecewise(ctrl, n_seg, degree, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.POINTS,
+                       t_mode=None, seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None):
+    """Evaluate C0 chains ``ctrl`` [n_chains][n_seg*degree+1][dim] at global
+    parameters in [0, n_seg]."""
+    n_chains, n_pts, dim = ctrl.shape
+    assert n_pts == n_seg * degree + 1, "ctrl must hold n_seg*degree+1 points per chain"
+    if t_mode is None:
+        t_mode = TMode.SHARED if (t is not None and t.ndim == 1) else TMode.PER_CURVE
+    if t is not None:
+        n_t = t.shape[-1]
+    assert n_t is not None, "n_t is required when t is None"
+    shape = (n_chains, n_t, dim) if out_mode == OutMode.POINTS else (n_chains,)
+    if out is None:
+        out = _empty_like_location(ctrl, shape)
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
+    _check(lib().bez_eval_piecewise(c.handle, _ptr(ctrl), n_chains, n_seg, degree, dim, _ptr(t), n_t, _ptr(out),
+                                    ctypes.byref(o), _stream_handle(stream, dev)))
     return out

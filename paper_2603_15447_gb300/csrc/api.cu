@@ -64,6 +64,9 @@ struct bez_ctx_s {
     std::vector<cudaEvent_t> spare;
     cudaEvent_t cur_begin = nullptr;
     StageBuf stage[8];
+    TexState tex;
+    cudaEvent_t tex_done = nullptr;  // last use of the texture atlases
+    bool tex_used = false;
     std::mutex mu;
 };
 
@@ -81,10 +84,11 @@ cudaEvent_t take_event(bez_ctx c)
     return e;
 }
 
+void hook_count(void* self) { static_cast<bez_ctx>(self)->launches += 1; }
+
 void hook_begin(void* self, cudaStream_t s)
 {
     bez_ctx c = static_cast<bez_ctx>(self);
-    c->launches += 1;
     if (!c->timing) return;
     c->cur_begin = take_event(c);
     cudaEventRecord(c->cur_begin, s);
@@ -100,7 +104,7 @@ void hook_end(void* self, cudaStream_t s)
     c->cur_begin = nullptr;
 }
 
-LaunchHooks hooks_of(bez_ctx c) { return LaunchHooks{hook_begin, hook_end, c, c->sm_count}; }
+LaunchHooks hooks_of(bez_ctx c) { return LaunchHooks{hook_count, hook_begin, hook_end, c, c->sm_count}; }
 
 enum MemKind { MEM_NULL, MEM_DEVICE, MEM_HOST };
 
@@ -259,6 +263,10 @@ bez_status bez_create(bez_ctx* out, int device)
     bez_ctx c = new bez_ctx_s();
     c->device = device;
     c->sm_count = prop.multiProcessorCount;
+    c->tex.max3d = prop.maxTexture3D[0] < prop.maxTexture3D[1] ? prop.maxTexture3D[0] : prop.maxTexture3D[1];
+    c->tex.max2d_w = prop.maxTexture2D[0];
+    c->tex.max2d_h = prop.maxTexture2D[1];
+    BEZ_CUDA(cudaEventCreateWithFlags(&c->tex_done, cudaEventDisableTiming), "cudaEventCreate");
     *out = c;
     return BEZ_OK;
 }
@@ -275,6 +283,13 @@ bez_status bez_destroy(bez_ctx c)
     for (auto e : c->spare) cudaEventDestroy(e);
     for (auto& b : c->stage)
         if (b.p) cudaFree(b.p);
+    atlas_free(c->tex.dc3);
+    atlas_free(c->tex.strip2);
+    atlas_free(c->tex.seil2);
+    atlas_free(c->tex.seil3);
+    atlas_free(c->tex.chain);
+    atlas_free(c->tex.probe);
+    if (c->tex_done) cudaEventDestroy(c->tex_done);
     delete c;
     return BEZ_OK;
 }
@@ -328,8 +343,12 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
     if (degree < 1) return fail(BEZ_ERR_INVALID_ARG, "degree %d < 1", degree);
     int var = o->variant == BEZ_VAR_AUTO ? BEZ_VAR_SEILER : o->variant;
-    if (var > BEZ_VAR_SEILER) return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for bez_eval", var);
+    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER || var == BEZ_VAR_TEX_HYBRID;
+    if (var > BEZ_VAR_TEX_HYBRID) return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for bez_eval", var);
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
+    if (var == BEZ_VAR_TEX_SEILER && (degree < 2 || degree > 5))
+        return fail(BEZ_ERR_UNSUPPORTED, "Seiler textures are defined for degrees 2..5 (got %d)", degree);
+    if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     if (n_curves == 0 || (n_t == 0 && o->out_mode == BEZ_OUT_POINTS)) return BEZ_OK;
     if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");
     const bool t_array = o->t_mode == BEZ_T_SHARED || o->t_mode == BEZ_T_PER_CURVE;
@@ -369,6 +388,18 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
 
     LaunchHooks h = hooks_of(c);
     LaunchResult r{0, cudaSuccess};
+    if (tex) {
+        // the atlases are shared by all calls of this context: order their use
+        if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
+        r = launch_tex_curve(a, var, tm, om, c->tex, s, h);
+        if (r.err == cudaErrorInvalidValue && r.launches == 0)
+            return fail(BEZ_ERR_UNSUPPORTED, "batch of %lld curves does not fit one texture atlas",
+                        (long long)n_curves);
+        if (r.err != cudaSuccess) return cuda_fail(r.err, "texture evaluator");
+        BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
+        c->tex_used = true;
+        return stg.finish(o->sync);
+    }
     switch (var) {
     case BEZ_VAR_HORNER: r = launch_curve_horner(a, tm, om, s, h); break;
     case BEZ_VAR_HORNER_CENTRED: r = launch_curve_horner_centred(a, tm, om, s, h); break;
@@ -378,6 +409,112 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     }
     if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
     return stg.finish(o->sync);
+}
+
+bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int n_seg, int degree, int dim,
+                              const float* t, int64_t n_t, float* out, const bez_opts* o, void* stream)
+{
+    bez_status st = check_common(c, o);
+    if (st != BEZ_OK) return st;
+    if (n_chains < 0 || n_t < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n_t > 0x7fffffff) return fail(BEZ_ERR_INVALID_ARG, "n_t %lld exceeds 2^31-1", (long long)n_t);
+    if (o->t_mode == BEZ_T_HASH && n_chains > 0xffffffffLL)
+        return fail(BEZ_ERR_INVALID_ARG, "hash parameters index chains with 32 bits");
+    if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
+    if (degree < 1 || n_seg < 1) return fail(BEZ_ERR_INVALID_ARG, "degree %d / n_seg %d must be >= 1", degree, n_seg);
+    int var = o->variant == BEZ_VAR_AUTO ? BEZ_VAR_DECASTELJAU : o->variant;
+    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU;
+    if (var > BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TENSOR)
+        return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for chains", var);
+    if (tex && degree != 2)
+        return fail(BEZ_ERR_UNSUPPORTED, "zig-zag chain textures hold quadratic segments (degree %d)", degree);
+    if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
+    if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
+    const int64_t per = ((int64_t)n_seg * degree + 1) * dim;
+    if (!tex && per > kChainMaxFloats)
+        return fail(BEZ_ERR_UNSUPPORTED, "chain of %lld control values exceeds %d", (long long)per, kChainMaxFloats);
+    if (n_chains == 0 || (n_t == 0 && o->out_mode == BEZ_OUT_POINTS)) return BEZ_OK;
+    if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");
+    const bool t_array = o->t_mode == BEZ_T_SHARED || o->t_mode == BEZ_T_PER_CURVE;
+    if (t_array && n_t > 0 && !t) return fail(BEZ_ERR_INVALID_ARG, "null t for t_mode %d", o->t_mode);
+
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    CurveArgs a{};
+    st = stg.in(ctrl, (size_t)n_chains * per * dtype_size(o->dtype), 0, &a.ctrl);
+    if (st != BEZ_OK) return st;
+    if (t_array) {
+        const size_t tb = (size_t)n_t * sizeof(float) * (o->t_mode == BEZ_T_PER_CURVE ? (size_t)n_chains : 1);
+        const void* td = nullptr;
+        st = stg.in(t, tb, 1, &td);
+        if (st != BEZ_OK) return st;
+        a.t = static_cast<const float*>(td);
+        a.t_stride = o->t_mode == BEZ_T_PER_CURVE ? n_t : 0;
+    }
+    const size_t out_bytes =
+        o->out_mode == BEZ_OUT_POINTS ? (size_t)n_chains * n_t * dim * sizeof(float) : (size_t)n_chains * sizeof(float);
+    void* od = nullptr;
+    st = stg.out(out, out_bytes, 2, &od);
+    if (st != BEZ_OK) return st;
+    a.out = static_cast<float*>(od);
+    a.dtype = o->dtype;
+    a.degree = degree;
+    a.dim = dim;
+    a.n_t = (int32_t)n_t;
+    a.n_curves = n_chains;
+    a.n_seg = n_seg;
+    const uint32_t seed_lo = (uint32_t)(o->seed & 0xffffffffu), seed_hi = (uint32_t)(o->seed >> 32);
+    a.key = lowbias32(seed_lo ^ lowbias32(seed_hi ^ lowbias32(o->stream_id)));
+    const int tm = t_array ? TM_ARRAY : (o->t_mode == BEZ_T_UNIFORM ? TM_UNIFORM : TM_HASH);
+    const int om = o->out_mode == BEZ_OUT_POINTS ? OM_POINTS : OM_LENGTH;
+    LaunchHooks h = hooks_of(c);
+    LaunchResult r{0, cudaSuccess};
+    if (tex) {
+        if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
+        r = launch_tex_chain(a, tm, om, c->tex, s, h);
+        if (r.err == cudaErrorInvalidValue && r.launches == 0)
+            return fail(BEZ_ERR_UNSUPPORTED, "%lld chains of %d segments do not fit one texture atlas",
+                        (long long)n_chains, n_seg);
+        if (r.err != cudaSuccess) return cuda_fail(r.err, "zig-zag chain evaluator");
+        BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
+        c->tex_used = true;
+        return stg.finish(o->sync);
+    }
+    switch (var) {
+    case BEZ_VAR_HORNER: r = launch_chain_horner(a, tm, om, s, h); break;
+    case BEZ_VAR_HORNER_CENTRED: r = launch_chain_horner_centred(a, tm, om, s, h); break;
+    case BEZ_VAR_BERNSTEIN: r = launch_chain_bernstein(a, tm, om, s, h); break;
+    case BEZ_VAR_SEILER: r = launch_chain_seiler(a, tm, om, s, h); break;
+    default: r = launch_chain_decasteljau(a, tm, om, s, h); break;
+    }
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "chain evaluator launch");
+    return stg.finish(o->sync);
+}
+
+bez_status bez_probe_filter(bez_ctx c, const float* xyz, int64_t n, float* out, void* stream)
+{
+    if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
+    if (n < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n > 0 && (!xyz || !out)) return fail(BEZ_ERR_INVALID_ARG, "null coordinates or output");
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    const void* xd = nullptr;
+    void* od = nullptr;
+    bez_status st = stg.in(xyz, (size_t)n * 3 * sizeof(float), 0, &xd);
+    if (st != BEZ_OK) return st;
+    st = stg.out(out, (size_t)n * 3 * sizeof(float), 2, &od);
+    if (st != BEZ_OK) return st;
+    if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
+    LaunchResult r = launch_tex_probe(static_cast<const float*>(xd), n, static_cast<float*>(od), c->tex, s,
+                                      hooks_of(c));
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "filter probe");
+    BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
+    c->tex_used = true;
+    return stg.finish(1);
 }
 
 }  // extern "C"

@@ -36,7 +36,8 @@ __host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x)
 // 23 high bits of h as a uniform in [0,1): 1.m - 1 is exact in FP32.
 __device__ __forceinline__ float hash_unit(uint32_t h)
 {
-    return __uint_as_float(0x3f800000u | (h >> 9)) - 1.0f;
+    // (0x7f : h) >> 9 == 0x3f800000 | (h >> 9): one funnel shift builds 1.m
+    return __uint_as_float(__funnelshift_r(h, 0x7fu, 9)) - 1.0f;
 }
 
 // a + t (b - a) written as (a - t a) + t b: exact at t = 0 and t = 1, and
@@ -55,7 +56,7 @@ __device__ __forceinline__ float clamp01(float t)
 __device__ __forceinline__ float sqrt_approx(float x)
 {
     float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 

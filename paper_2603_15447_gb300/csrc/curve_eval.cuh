@@ -15,13 +15,19 @@
 //                   (Sec. 3.1); d_i from the closed forms for degree <= 5 and
 //                   by exact peeling of the s-power form above that.
 //
-// Setup runs in FP32 up to degree 7 and in FP64 from degree 8 on.
+// Setup runs in FP32 up to degree 7 and in FP64 from degree 8 on, except the
+// centred power basis, whose FP32 conversion alone costs more than 1e-6 of
+// the curve diagonal at degree 7 (1.4e-6 measured); it switches to FP64 at
+// degree 5.
 #pragma once
 
 #include "common.cuh"
 #include "internal.h"
 
 namespace bez {
+
+constexpr int kFp64Setup = 8;         // power basis about 0, Seiler peeling
+constexpr int kFp64SetupCentred = 5;  // power basis about 1/2
 
 template <int D>
 struct Deg {
@@ -80,7 +86,7 @@ struct Eval<VAR_HORNER, D, DIM> {
     __device__ __forceinline__ void setup(const float (&b)[N][DIM], int deg)
     {
         d = Deg<D>::get(deg);
-        if (D == 0 && d >= 8) setup_t<double>(b);
+        if (d >= kFp64Setup) setup_t<double>(b);
         else setup_t<float>(b);
     }
     __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
@@ -134,7 +140,7 @@ struct Eval<VAR_HORNER_CENTRED, D, DIM> {
     __device__ __forceinline__ void setup(const float (&b)[N][DIM], int deg)
     {
         d = Deg<D>::get(deg);
-        if (D == 0 && d >= 8) setup_t<double>(b);
+        if (d >= kFp64SetupCentred) setup_t<double>(b);
         else setup_t<float>(b);
     }
     __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
@@ -278,7 +284,7 @@ struct Eval<VAR_SEILER, D, DIM> {
                 for (int j = 0; j < N - 2; ++j) {
                     if (j <= m - 2) {
                         const S i1 = (S)(j + 1);
-                        const S q = c[j + 1] - (((S)1 - i1 / mm) * c0 + (i1 / mm) * cm);
+                        const S q = (c[j + 1] - c0) - (i1 / mm) * (cm - c0);
                         c[j] = q * (mm * (mm - (S)1)) / (i1 * (mm - (S)1 - (S)j));
                     }
                 }
@@ -291,7 +297,7 @@ struct Eval<VAR_SEILER, D, DIM> {
     {
         d = Deg<D>::get(deg);
         if (d <= 5) setup_closed(b);
-        else if (d >= 8) setup_peel<double>(b);
+        else if (d >= kFp64Setup) setup_peel<double>(b);
         else setup_peel<float>(b);
     }
 
@@ -370,7 +376,7 @@ struct EvalDyn {
                     const S c0 = w[0], cm = w[m], mm = (S)m;
                     for (int j = 0; j <= m - 2; ++j) {
                         const S i1 = (S)(j + 1);
-                        const S q = w[j + 1] - (((S)1 - i1 / mm) * c0 + (i1 / mm) * cm);
+                        const S q = (w[j + 1] - c0) - (i1 / mm) * (cm - c0);
                         w[j] = q * (mm * (mm - (S)1)) / (i1 * (mm - (S)1 - (S)j));
                     }
                     m -= 2;
@@ -389,7 +395,8 @@ struct EvalDyn {
     __device__ void setup(const float (&b)[N][DIM], int deg)
     {
         d = deg;
-        if (d >= 8 && VAR != VAR_DECASTELJAU && VAR != VAR_BERNSTEIN) setup_t<double>(b);
+        const int from = VAR == VAR_HORNER_CENTRED ? kFp64SetupCentred : kFp64Setup;
+        if (d >= from && VAR != VAR_DECASTELJAU && VAR != VAR_BERNSTEIN) setup_t<double>(b);
         else setup_t<float>(b);
     }
     __device__ void eval(float t, float (&P)[DIM]) const
@@ -462,90 +469,112 @@ __device__ __forceinline__ float seg_len(const float (&p)[DIM], const float (&q)
     return sqrt_approx(s);
 }
 
+// Warp-per-curve kernel.  Warps are independent (no block barrier): each
+// warp loads its curve's control points with one coalesced request (lane i
+// reads element i), broadcasts them with shuffles, and prefetches the next
+// curve's elements while it evaluates the current one.
+template <int N, int DIM>
+struct CtrlRegs {
+    static constexpr int kPer = N * DIM;                  // elements per curve (upper bound)
+    static constexpr int kLoads = (kPer + 31) / 32;       // elements per lane
+    float v[kLoads];
+
+    __device__ __forceinline__ void load(const CurveArgs& a, int64_t c, int per, int lane)
+    {
+#pragma unroll
+        for (int r = 0; r < kLoads; ++r) {
+            const int i = lane + 32 * r;
+            v[r] = (c < a.n_curves && i < per) ? load_elem(a.ctrl, a.dtype, c * per + i) : 0.f;
+        }
+    }
+    __device__ __forceinline__ void unpack(float (&b)[N][DIM], int deg) const
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const int e = i * DIM + k;
+                const float x = __shfl_sync(kFull, v[e / 32], e % 32);
+                b[i][k] = (i <= deg) ? x : 0.f;
+            }
+    }
+};
+
 template <int VAR, int D, int DIM, int TM, int OM>
-__global__ void __launch_bounds__(kWarps * 32) k_curve(const CurveArgs a)
+__global__ void __launch_bounds__(kWarps * 32, 6) k_curve(const CurveArgs a)
 {
     using E = typename Pick<VAR, D, DIM>::type;
     constexpr int N = E::N;
-    __shared__ float s_ctrl[kWarps * N * DIM];
     __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * DIM : 1];
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int deg = Deg<D>::get(a.degree);
     const int per = (deg + 1) * DIM;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
 
-    for (int64_t base = (int64_t)blockIdx.x * kWarps; base < a.n_curves; base += (int64_t)gridDim.x * kWarps) {
-        // coalesced load of this block's control points into shared memory
-        const int64_t n_here = min((int64_t)kWarps, a.n_curves - base);
-        const int count = (int)n_here * per;
-        for (int i = threadIdx.x; i < count; i += kWarps * 32) s_ctrl[i] = load_elem(a.ctrl, a.dtype, base * per + i);
-        __syncthreads();
+    int64_t c = (int64_t)blockIdx.x * kWarps + wib;
+    CtrlRegs<N, DIM> cur;
+    cur.load(a, c, per, lane);
+    for (; c < a.n_curves; c += n_warps) {
+        float b[N][DIM];
+        cur.unpack(b, deg);
+        cur.load(a, c + n_warps, per, lane);   // prefetch the next curve of this warp
+        E e;
+        e.setup(b, deg);
+        const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
+        const int n_t = a.n_t;
 
-        const int64_t c = base + wib;
-        if (c < a.n_curves) {
-            float b[N][DIM];
+        if (OM == OM_POINTS) {
+            float* stage = s_stage + wib * 32 * DIM;
+            for (int j0 = 0; j0 < n_t; j0 += 32) {
+                const int j = j0 + lane;
+                float P[DIM];
 #pragma unroll
-            for (int i = 0; i < N; ++i)
+                for (int k = 0; k < DIM; ++k) P[k] = 0.f;
+                if (j < n_t) e.eval(param<TM>(a, c, j, kc), P);
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) b[i][k] = (i <= deg) ? s_ctrl[wib * per + i * DIM + k] : 0.f;
-            E e;
-            e.setup(b, deg);
-            const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
-            const int n_t = a.n_t;
-
-            if (OM == OM_POINTS) {
-                float* stage = s_stage + wib * 32 * DIM;
-                for (int j0 = 0; j0 < n_t; j0 += 32) {
-                    const int j = j0 + lane;
-                    float P[DIM];
+                for (int k = 0; k < DIM; ++k) stage[lane * DIM + k] = P[k];
+                __syncwarp();
+                const int valid = min(32, n_t - j0) * DIM;
+                float* o = a.out + (c * n_t + j0) * DIM;
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) P[k] = 0.f;
-                    if (j < n_t) e.eval(param<TM>(a, c, j, kc), P);
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) stage[lane * DIM + k] = P[k];
-                    __syncwarp();
-                    const int valid = min(32, n_t - j0) * DIM;
-                    float* o = a.out + (c * n_t + j0) * DIM;
-#pragma unroll
-                    for (int m = 0; m < DIM; ++m) {
-                        const int idx = lane + 32 * m;
-                        if (idx < valid) o[idx] = stage[idx];
-                    }
-                    __syncwarp();
+                for (int m = 0; m < DIM; ++m) {
+                    const int idx = lane + 32 * m;
+                    if (idx < valid) o[idx] = stage[idx];
                 }
-            } else {
-                // each lane walks a contiguous run of samples; the segment
-                // joining two runs is closed with one shuffle
-                const int chunk = (n_t + 31) / 32;
-                const int jb = lane * chunk;
-                const int je = min(jb + chunk, n_t);
-                float acc = 0.f;
-                float first[DIM], prev[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) first[k] = prev[k] = 0.f;
-                if (jb < je) {
-                    e.eval(param<TM>(a, c, jb, kc), first);
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) prev[k] = first[k];
-#pragma unroll 4
-                    for (int j = jb + 1; j < je; ++j) {
-                        float P[DIM];
-                        e.eval(param<TM>(a, c, j, kc), P);
-                        acc += seg_len<DIM>(P, prev);
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) prev[k] = P[k];
-                    }
-                }
-                float pl[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) pl[k] = __shfl_up_sync(kFull, prev[k], 1);
-                if (lane > 0 && jb < je) acc += seg_len<DIM>(first, pl);
-                acc = warp_sum(acc);
-                if (lane == 0) a.out[c] = acc;
+                __syncwarp();
             }
+        } else {
+            // each lane walks a contiguous run of samples; the segment
+            // joining two runs is closed with one shuffle
+            const int chunk = (n_t + 31) / 32;
+            const int jb = lane * chunk;
+            const int je = min(jb + chunk, n_t);
+            float acc = 0.f;
+            float first[DIM], prev[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) first[k] = prev[k] = 0.f;
+            if (jb < je) {
+                e.eval(param<TM>(a, c, jb, kc), first);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) prev[k] = first[k];
+#pragma unroll 4
+                for (int j = jb + 1; j < je; ++j) {
+                    float P[DIM];
+                    e.eval(param<TM>(a, c, j, kc), P);
+                    acc += seg_len<DIM>(P, prev);
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) prev[k] = P[k];
+                }
+            }
+            float pl[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) pl[k] = __shfl_up_sync(kFull, prev[k], 1);
+            if (lane > 0 && jb < je) acc += seg_len<DIM>(first, pl);
+            acc = warp_sum(acc);
+            if (lane == 0) a.out[c] = acc;
         }
-        __syncthreads();
     }
 }
 
@@ -557,6 +586,7 @@ LaunchResult launch_one(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h
     auto kern = k_curve<VAR, D, DIM, TM, OM>;
     const int64_t work = (a.n_curves + kWarps - 1) / kWarps;
     const int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    h.count(h.self);
     h.begin(h.self, s);
     kern<<<grid, kWarps * 32, 0, s>>>(a);
     cudaError_t err = cudaGetLastError();

@@ -19,6 +19,7 @@ struct CurveArgs {
     int64_t t_stride;
     float* out;         // OM_POINTS [n_curves][n_t][dim]; OM_LENGTH [n_curves]
     uint32_t key;       // TM_HASH stream key
+    int32_t n_seg;      // chains: segments per chain (0 for single curves)
 };
 
 // Result of a launcher: how many kernels it launched and the CUDA status.
@@ -30,7 +31,8 @@ struct LaunchResult {
 // Hooks the runtime passes to launchers so that the main kernel of a call is
 // bracketed by timing events and counted.
 struct LaunchHooks {
-    void (*begin)(void* self, cudaStream_t s);
+    void (*count)(void* self);                  // every kernel launch
+    void (*begin)(void* self, cudaStream_t s);  // main kernel of a call
     void (*end)(void* self, cudaStream_t s);
     void* self;
     int sm_count;
@@ -42,6 +44,49 @@ LaunchResult launch_curve_horner_centred(const CurveArgs& a, int tm, int om, cud
 LaunchResult launch_curve_bernstein(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_curve_decasteljau(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_curve_seiler(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+
+// ---------------------------------------------------------------- textures
+
+// A cudaArray-backed atlas with a linear-filtering texture object for reads
+// and a surface object for the packers' writes.  fmt 0: float4 texels,
+// fmt 1: half4 texels.  depth 0 means a 2D array.
+struct Atlas {
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+    cudaSurfaceObject_t surf = 0;
+    int w = 0, h = 0, depth = 0, fmt = 0;
+};
+cudaError_t atlas_ensure(Atlas& at, int w, int h, int depth, int fmt);
+void atlas_free(Atlas& at);
+
+// Texture state owned by a context.
+struct TexState {
+    Atlas dc3;    // 3D de Casteljau tiles / strips: texel(x,y,z) = b_(x+y+z)
+    Atlas strip2; // 2D strips: texel(x,y) = b_(x+y)
+    Atlas seil2;  // 2D 2x2 Seiler tiles (degree 2, 3)
+    Atlas seil3;  // 3D 2x2x2 Seiler tiles (degree 4, 5)
+    Atlas chain;  // zig-zag C0 chain textures
+    Atlas probe;  // 2x2x2 weight probe
+    int max3d = 16384, max2d_w = 131072, max2d_h = 65536;
+};
+
+// Texture evaluators: pack the control points into the atlas of `variant`,
+// then evaluate.  `variant` is a bez_variant texture value.
+LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, TexState& ts, cudaStream_t s,
+                              const LaunchHooks& h);
+// Filter-weight probe: out[i] = filtered (x, y, z) texel index at coords xyz[i].
+LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState& ts, cudaStream_t s,
+                              const LaunchHooks& h);
+
+// C0 chains (chain_*.cu): register evaluators per segment.
+LaunchResult launch_chain_horner(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_chain_horner_centred(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_chain_bernstein(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_chain_decasteljau(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_chain_seiler(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+// Zig-zag texture for C0 quadratic chains (tex.cu).
+LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, cudaStream_t s, const LaunchHooks& h);
+constexpr int kChainMaxFloats = 3072;  // (n_seg*degree+1)*dim per chain staged in shared memory
 
 // Occupancy-sized persistent grid: a multiple of the SM count.
 int persistent_grid(const void* kernel, int block, size_t smem, int sm_count, int64_t work_blocks);

@@ -1,0 +1,120 @@
+// spline.cuh -- B-spline / NURBS support shared by the one-shot spline
+// evaluators and the mixed-batch kernel.
+//
+// Setup (paper Sec. 2.2: "B-splines can be converted to piecewise Bezier
+// curves using Boehm's algorithm"): every non-empty span [a, b) = [U_k,
+// U_(k+1)) of a degree-p spline gets its own Bezier control points by knot
+// insertion, in FP64, one thread per span.  Writing the de Boor points of the
+// span as blossom values D_i = f(s_(i+1), ..., s_(i+p)) over the local knots
+// s_1..s_2p = U_(k-p+1)..U_(k+p) (s_p = a, s_(p+1) = b):
+//   left pass, levels l = 1..p-1, i = 0..p-l ascending:
+//     Q_i <- lerp(Q_i, Q_(i+1), (a - s_(i+l)) / (s_(p+i+1) - s_(i+l)))
+//   inserts a until every point carries a^(p-i); then
+//   right pass, levels l = 1..p-1, i = p..l descending:
+//     Q_i <- lerp(Q_(i-1), Q_i, (b - a) / (s_(p+i-l+1) - a))
+//   inserts b, leaving Q_i = f(a^(p-i), b^i), the Bezier points of the span.
+// Each step is one single-knot insertion restricted to the span's p+1 points
+// (an affine combination of two blossom values that differ in one argument).
+// Rational curves run the same steps on homogeneous points (w P, w).
+//
+// Evaluation: t is clamped to [U_p, U_n]; the span is the last non-empty one
+// with U_k <= t (an interior knot starts the later span); tau = (t - a) /
+// (b - a) (clamped uniform knots: s = t * n_spans, k = floor(s), tau = s - k);
+// the span's Bezier points go through FP32 de Casteljau, and rational points
+// are divided by their weight.
+#pragma once
+
+#include "common.cuh"
+
+namespace bez {
+
+// knot U_i of the clamped uniform vector: p+1 zeros, (i-p)/(n-p), p+1 ones
+__host__ __device__ __forceinline__ double clamped_uniform_knot(int i, int n, int p)
+{
+    if (i <= p) return 0.0;
+    if (i >= n) return 1.0;
+    return (double)(i - p) / (double)(n - p);
+}
+
+// Bezier points of span k (p <= k < n) of one spline into q[(p+1)*comps]
+// (FP32).  ctrl [n][dim], w [n] or NULL, knots [n+p+1] or NULL.
+__device__ inline void extract_span(const float* ctrl, const float* w, const float* knots, int n, int p, int dim,
+                                    int k, float* q_out)
+{
+    const int comps = w ? dim + 1 : dim;
+    double s[2 * kMaxDegree + 1];   // s[1..2p]
+    for (int j = 1; j <= 2 * p; ++j) {
+        const int i = k - p + j;
+        s[j] = knots ? (double)knots[i] : clamped_uniform_knot(i, n, p);
+    }
+    const double a = s[p], b = s[p + 1];
+    double Q[kMaxDegree + 1][5];
+    for (int i = 0; i <= p; ++i) {
+        const int g = k - p + i;
+        const double wi = w ? (double)w[g] : 1.0;
+        for (int q = 0; q < dim; ++q) Q[i][q] = wi * (double)ctrl[g * dim + q];
+        if (w) Q[i][dim] = wi;
+    }
+    if (!(a < b)) {
+        for (int i = 0; i <= p; ++i)
+            for (int q = 0; q < comps; ++q) q_out[i * comps + q] = 0.f;
+        return;
+    }
+    for (int l = 1; l <= p - 1; ++l)
+        for (int i = 0; i <= p - l; ++i) {
+            const double lo = s[i + l], hi = s[p + i + 1];
+            if (lo == a) continue;                 // weight 0: already a
+            const double al = (a - lo) / (hi - lo);
+            for (int q = 0; q < comps; ++q) Q[i][q] += al * (Q[i + 1][q] - Q[i][q]);
+        }
+    for (int l = 1; l <= p - 1; ++l)
+        for (int i = p; i >= l; --i) {
+            const double T = s[p + i - l + 1];
+            if (T == b) continue;                  // weight 1: already b
+            const double al = (b - a) / (T - a);
+            for (int q = 0; q < comps; ++q) Q[i][q] = Q[i - 1][q] + al * (Q[i][q] - Q[i - 1][q]);
+        }
+    for (int i = 0; i <= p; ++i)
+        for (int q = 0; q < comps; ++q) q_out[i * comps + q] = (float)Q[i][q];
+}
+
+// FP32 de Casteljau on one span's Bezier points (compile-time degree P and
+// component count C), rational division by the last component if RAT.
+template <int P, int C, bool RAT>
+__device__ __forceinline__ void span_point_fixed(const float* q, float tau, float* out)
+{
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float w[P + 1];
+#pragma unroll
+        for (int i = 0; i <= P; ++i) w[i] = q[i * C + c];
+#pragma unroll
+        for (int r = 1; r <= P; ++r)
+#pragma unroll
+            for (int i = 0; i <= P - r; ++i) w[i] = lerp(w[i], w[i + 1], tau);
+        out[c] = w[0];
+    }
+    if (RAT) {
+        const float inv = 1.0f / out[C - 1];
+#pragma unroll
+        for (int c = 0; c < C - 1; ++c) out[c] *= inv;
+    }
+}
+
+// Runtime degree / component count (p <= kMaxDegree, comps <= 5).
+__device__ inline void span_point_dyn(const float* q, int p, int comps, bool rat, float tau, float* out)
+{
+    for (int c = 0; c < comps; ++c) {
+        float w[kMaxDegree + 1];
+        for (int i = 0; i <= p; ++i) w[i] = q[i * comps + c];
+        for (int r = 1; r <= p; ++r)
+            for (int i = 0; i <= p - r; ++i) w[i] = lerp(w[i], w[i + 1], tau);
+        out[c] = w[0];
+    }
+    if (rat) {
+        const float inv = 1.0f / out[comps - 1];
+        for (int c = 0; c < comps - 1; ++c) out[c] *= inv;
+    }
+}
+
+}  // namespace bez

@@ -1,0 +1,564 @@
+// tex.cu -- texture-path curve evaluators (paper Sec. 2 and Sec. 4).
+//
+// Control points are packed by a surface-write kernel into cudaArray atlases
+// owned by the context, then read with hardware linear filtering:
+//
+//   DC3   cubic, one 2x2x2 tile, texel(x,y,z) = b_(x+y+z), one trilinear read
+//         at (t, t, t): front slice is the quadratic (b0,b1,b2), back slice
+//         (b1,b2,b3) (Sec. 2).
+//   DCN   any other degree: strip texel(x,y,z) = b_(x+y+z), x in [0, d-2];
+//         window i read at (i+t, t, t) gives the level-3 de Casteljau point
+//         of b_i..b_(i+3); the remaining d-3 levels are FP32 lerps (Sec. 2:
+//         "further interpolation levels can be done in the shader").
+//         Degrees 1, 2 read one tile with the unused axes at texel centres.
+//   HYB3  cubic hybrid (Fig. 3): 2D strip texel(x,y) = b_(x+y); two bilinear
+//         reads give the quadratics (b0,b1,b2), (b1,b2,b3); final lerp in FP32.
+//   HYBN  the same 2D strip for other degrees: d-1 bilinear reads, d-2 lerps.
+//   SEIL2 degrees 2, 3: 2x2 tile [[b0, bd], [b0+d1, bd+d_(d-1)]] read at
+//         (t, st) (Sec. 4, Eq. 6 and the layout table).
+//   SEIL3 degrees 4, 5: 2x2x2 tile, z=0 [[b0,bd],[b0,bd]],
+//         z=1 [[b0+d1, bd+d_(d-1)], [b0+d1+d2, bd+d_(d-1)+d_(d-2)]] read at
+//         (t, st, st) (Sec. 4, Eq. 7 and the layout table).
+//
+// Coordinates are unnormalised with texel centres at i + 0.5, so the paper's
+// [0.25, 0.75] remap of a 2-texel axis becomes x = x0 + 0.5 + t; for the st
+// axis the offset is added after the product (Sec. 4).  Addressing clamps.
+#include "curve_eval.cuh"
+
+namespace bez {
+
+enum { TK_DC3 = 0, TK_DCN = 1, TK_HYB3 = 2, TK_HYBN = 3, TK_SEIL2 = 4, TK_SEIL3 = 5 };
+
+struct TexArgs {
+    cudaTextureObject_t tex;
+    int tw;   // tiles per atlas row
+    int wt;   // tile width in texels
+    int deg;
+};
+
+// ---------------------------------------------------------------- atlases (host)
+
+void atlas_free(Atlas& at)
+{
+    if (at.tex) cudaDestroyTextureObject(at.tex);
+    if (at.surf) cudaDestroySurfaceObject(at.surf);
+    if (at.arr) cudaFreeArray(at.arr);
+    at = Atlas{};
+}
+
+cudaError_t atlas_ensure(Atlas& at, int w, int h, int depth, int fmt)
+{
+    if (at.arr && at.depth == depth && at.fmt == fmt && at.w >= w && at.h >= h) return cudaSuccess;
+    if (at.arr && at.depth == depth && at.fmt == fmt) {
+        w = w > at.w ? w : at.w;
+        h = h > at.h ? h : at.h;
+    }
+    if (at.arr) {
+        cudaError_t e = cudaDeviceSynchronize();  // the old atlas may still be read
+        if (e != cudaSuccess) return e;
+        atlas_free(at);
+    }
+    cudaChannelFormatDesc cd = fmt == 0 ? cudaCreateChannelDesc<float4>() : cudaCreateChannelDescHalf4();
+    cudaError_t e;
+    if (depth > 0) e = cudaMalloc3DArray(&at.arr, &cd, make_cudaExtent(w, h, depth), cudaArraySurfaceLoadStore);
+    else e = cudaMallocArray(&at.arr, &cd, w, h, cudaArraySurfaceLoadStore);
+    if (e != cudaSuccess) {
+        at.arr = nullptr;
+        return e;
+    }
+    cudaResourceDesc rd = {};
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = at.arr;
+    cudaTextureDesc td = {};
+    td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModeLinear;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    e = cudaCreateTextureObject(&at.tex, &rd, &td, nullptr);
+    if (e == cudaSuccess) e = cudaCreateSurfaceObject(&at.surf, &rd);
+    if (e != cudaSuccess) {
+        atlas_free(at);
+        return e;
+    }
+    at.w = w;
+    at.h = h;
+    at.depth = depth;
+    at.fmt = fmt;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- packers
+
+__device__ __forceinline__ void put(cudaSurfaceObject_t s, int fmt, int x, int y, int z, bool is3d, float4 v)
+{
+    if (fmt == 0) {
+        if (is3d) surf3Dwrite(v, s, x * 16, y, z);
+        else surf2Dwrite(v, s, x * 16, y);
+    } else {
+        const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+        const uint2 bits = make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+        if (is3d) surf3Dwrite(bits, s, x * 8, y, z);
+        else surf2Dwrite(bits, s, x * 8, y);
+    }
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+
+// Seiler difference terms by the closed forms of Sec. 3.1 (degree 2..5):
+// d1 = d(b1-b0) - (bd-b0), d_(d-1) = d(b_(d-1)-bd) - (b0-bd), and for d = 4, 5
+// d2 = C(d,2)(b2-b1) - C(d-2,2)(b1-b0) - (d-3)(b_(d-1)-bd) - 3(b_(d-1)-b1),
+// d_(d-2) mirrored.
+__device__ void seiler_terms(const float4* b, int d, float4& d1, float4& dl, float4& d2, float4& dl2)
+{
+    const float fd = (float)d;
+    d1 = sub4(scale4(fd, sub4(b[1], b[0])), sub4(b[d], b[0]));
+    dl = sub4(scale4(fd, sub4(b[d - 1], b[d])), sub4(b[0], b[d]));
+    d2 = dl2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (d >= 4) {
+        const float c2 = (float)(d * (d - 1) / 2), c2m = (float)((d - 2) * (d - 3) / 2), e = (float)(d - 3);
+        d2 = sub4(sub4(sub4(scale4(c2, sub4(b[2], b[1])), scale4(c2m, sub4(b[1], b[0]))),
+                       scale4(e, sub4(b[d - 1], b[d]))),
+                  scale4(3.f, sub4(b[d - 1], b[1])));
+        dl2 = sub4(sub4(sub4(scale4(c2, sub4(b[d - 2], b[d - 1])), scale4(c2m, sub4(b[d - 1], b[d]))),
+                        scale4(e, sub4(b[1], b[0]))),
+                   scale4(3.f, sub4(b[1], b[d - 1])));
+    }
+}
+
+template <int KIND>
+__global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, int fmt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_curves) return;
+    const int d = a.degree, dim = a.dim;
+    float4 b[kMaxDegree + 1];
+    for (int i = 0; i <= d; ++i) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < dim; ++k) v[k] = load_elem(a.ctrl, a.dtype, (c * (d + 1) + i) * dim + k);
+        b[i] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    const int x0 = (int)(c % ta.tw) * ta.wt, y0 = (int)(c / ta.tw) * 2;
+    if (KIND == TK_DC3 || KIND == TK_DCN) {
+        for (int z = 0; z < 2; ++z)
+            for (int y = 0; y < 2; ++y)
+                for (int x = 0; x < ta.wt; ++x) put(surf, fmt, x0 + x, y0 + y, z, true, b[min(x + y + z, d)]);
+    } else if (KIND == TK_HYB3 || KIND == TK_HYBN) {
+        for (int y = 0; y < 2; ++y)
+            for (int x = 0; x < ta.wt; ++x) put(surf, fmt, x0 + x, y0 + y, 0, false, b[min(x + y, d)]);
+    } else {
+        float4 d1, dl, d2, dl2;
+        seiler_terms(b, d, d1, dl, d2, dl2);
+        if (KIND == TK_SEIL2) {
+            put(surf, fmt, x0, y0, 0, false, b[0]);
+            put(surf, fmt, x0 + 1, y0, 0, false, b[d]);
+            put(surf, fmt, x0, y0 + 1, 0, false, add4(b[0], d1));
+            put(surf, fmt, x0 + 1, y0 + 1, 0, false, add4(b[d], dl));
+        } else {
+            put(surf, fmt, x0, y0, 0, true, b[0]);
+            put(surf, fmt, x0 + 1, y0, 0, true, b[d]);
+            put(surf, fmt, x0, y0 + 1, 0, true, b[0]);
+            put(surf, fmt, x0 + 1, y0 + 1, 0, true, b[d]);
+            const float4 s1 = add4(b[0], d1), s2 = add4(b[d], dl);
+            put(surf, fmt, x0, y0, 1, true, s1);
+            put(surf, fmt, x0 + 1, y0, 1, true, s2);
+            put(surf, fmt, x0, y0 + 1, 1, true, add4(s1, d2));
+            put(surf, fmt, x0 + 1, y0 + 1, 1, true, add4(s2, dl2));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- evaluators
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t)
+{
+    return make_float4(lerp(a.x, b.x, t), lerp(a.y, b.y, t), lerp(a.z, b.z, t), lerp(a.w, b.w, t));
+}
+
+template <int KIND>
+__device__ __forceinline__ float4 tex_point(const TexArgs& ta, float xb, float yb, float t)
+{
+    if (KIND == TK_DC3) return tex3D<float4>(ta.tex, xb + t, yb + t, 0.5f + t);
+    if (KIND == TK_HYB3) {
+        const float y = yb + t;
+        const float4 q0 = tex2D<float4>(ta.tex, xb + t, y);
+        const float4 q1 = tex2D<float4>(ta.tex, (xb + 1.f) + t, y);
+        return lerp4(q0, q1, t);
+    }
+    if (KIND == TK_SEIL2) {
+        const float st = fmaf(-t, t, t);
+        return tex2D<float4>(ta.tex, xb + t, yb + st);
+    }
+    if (KIND == TK_SEIL3) {
+        const float st = fmaf(-t, t, t);
+        return tex3D<float4>(ta.tex, xb + t, yb + st, 0.5f + st);
+    }
+    const int d = ta.deg;
+    if (KIND == TK_DCN) {
+        if (d == 1) return tex3D<float4>(ta.tex, xb + t, yb, 0.5f);
+        if (d == 2) return tex3D<float4>(ta.tex, xb + t, yb + t, 0.5f);
+        float4 q[kMaxDegree - 2];
+        const float y = yb + t, z = 0.5f + t;
+        for (int i = 0; i <= d - 3; ++i) q[i] = tex3D<float4>(ta.tex, (xb + (float)i) + t, y, z);
+        for (int r = 1; r <= d - 3; ++r)
+            for (int i = 0; i <= d - 3 - r; ++i) q[i] = lerp4(q[i], q[i + 1], t);
+        return q[0];
+    }
+    // TK_HYBN
+    if (d == 1) return tex2D<float4>(ta.tex, xb + t, yb);
+    float4 q[kMaxDegree - 1];
+    const float y = yb + t;
+    for (int i = 0; i <= d - 2; ++i) q[i] = tex2D<float4>(ta.tex, (xb + (float)i) + t, y);
+    for (int r = 1; r <= d - 2; ++r)
+        for (int i = 0; i <= d - 2 - r; ++i) q[i] = lerp4(q[i], q[i + 1], t);
+    return q[0];
+}
+
+__device__ __forceinline__ float seg_len4(float4 p, float4 q)
+{
+    const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z, ew = p.w - q.w;
+    return sqrt_approx(fmaf(ew, ew, fmaf(ez, ez, fmaf(ey, ey, ex * ex))));
+}
+
+template <int KIND, int TM>
+__device__ __forceinline__ float4 tex_eval(const CurveArgs& a, const TexArgs& ta, int64_t c, int j, uint32_t kc,
+                                           float xb, float yb)
+{
+    const float t = param<TM>(a, c, j, kc);
+    float4 P = tex_point<KIND>(ta, xb, yb, t);
+    if (TM == TM_ARRAY && t != t) P = make_float4(t, t, t, t);  // NaN parameter -> NaN point
+    return P;
+}
+
+template <int KIND, int TM, int OM>
+__global__ void __launch_bounds__(kWarps * 32) k_tex(const CurveArgs a, const TexArgs ta)
+{
+    __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * 4 : 1];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    const int dim = a.dim;
+    for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
+        const float xb = (float)((int)(c % ta.tw) * ta.wt) + 0.5f;
+        const float yb = (float)((int)(c / ta.tw) * 2) + 0.5f;
+        const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
+        const int n_t = a.n_t;
+        if (OM == OM_POINTS) {
+            float* stage = s_stage + wib * 32 * 4;
+            for (int j0 = 0; j0 < n_t; j0 += 32) {
+                const int j = j0 + lane;
+                float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < n_t) P = tex_eval<KIND, TM>(a, ta, c, j, kc, xb, yb);
+                const float pv[4] = {P.x, P.y, P.z, P.w};
+                for (int k = 0; k < dim; ++k) stage[lane * dim + k] = pv[k];
+                __syncwarp();
+                const int valid = min(32, n_t - j0) * dim;
+                float* o = a.out + (c * n_t + j0) * dim;
+                for (int idx = lane; idx < valid; idx += 32) o[idx] = stage[idx];
+                __syncwarp();
+            }
+        } else {
+            const int chunk = (n_t + 31) / 32;
+            const int jb = lane * chunk;
+            const int je = min(jb + chunk, n_t);
+            float acc = 0.f;
+            float4 first = make_float4(0.f, 0.f, 0.f, 0.f), prev = first;
+            if (jb < je) {
+                first = prev = tex_eval<KIND, TM>(a, ta, c, jb, kc, xb, yb);
+#pragma unroll 4
+                for (int j = jb + 1; j < je; ++j) {
+                    const float4 P = tex_eval<KIND, TM>(a, ta, c, j, kc, xb, yb);
+                    acc += seg_len4(P, prev);
+                    prev = P;
+                }
+            }
+            float4 pl;
+            pl.x = __shfl_up_sync(kFull, prev.x, 1);
+            pl.y = __shfl_up_sync(kFull, prev.y, 1);
+            pl.z = __shfl_up_sync(kFull, prev.z, 1);
+            pl.w = __shfl_up_sync(kFull, prev.w, 1);
+            if (lane > 0 && jb < je) acc += seg_len4(first, pl);
+            acc = warp_sum(acc);
+            if (lane == 0) a.out[c] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- dispatch
+
+template <int KIND>
+LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, int wt, cudaStream_t s,
+                         const LaunchHooks& h)
+{
+    TexArgs ta{at.tex, tw, wt, a.degree};
+    h.count(h.self);
+    k_pack<KIND><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, at.surf, at.fmt);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return {1, err};
+    const void* kern;
+    auto pick = [&](auto k) { kern = (const void*)k; };
+    if (om == OM_POINTS) {
+        if (tm == TM_ARRAY) pick(k_tex<KIND, TM_ARRAY, OM_POINTS>);
+        else if (tm == TM_UNIFORM) pick(k_tex<KIND, TM_UNIFORM, OM_POINTS>);
+        else pick(k_tex<KIND, TM_HASH, OM_POINTS>);
+    } else {
+        if (tm == TM_ARRAY) pick(k_tex<KIND, TM_ARRAY, OM_LENGTH>);
+        else if (tm == TM_UNIFORM) pick(k_tex<KIND, TM_UNIFORM, OM_LENGTH>);
+        else pick(k_tex<KIND, TM_HASH, OM_LENGTH>);
+    }
+    const int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, (a.n_curves + kWarps - 1) / kWarps);
+    void* args[] = {(void*)&a, (void*)&ta};
+    h.count(h.self);
+    h.begin(h.self, s);
+    err = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);
+    h.end(h.self, s);
+    return {2, err};
+}
+
+// Tiles per atlas row: a power of two near sqrt(n * 2 / wt) so that the
+// atlas is roughly square (small coordinates keep more fractional bits).
+static int tiles_per_row(int64_t n, int wt, int max_w)
+{
+    int tw = 1;
+    while ((int64_t)tw * tw * wt < n * 2 && tw * 2 * wt <= max_w) tw *= 2;
+    return tw;
+}
+
+LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, TexState& ts, cudaStream_t s,
+                              const LaunchHooks& h)
+{
+    const int d = a.degree;
+    const int fmt = a.dtype == 1 ? 1 : 0;
+    int kind, wt;
+    bool is3d;
+    if (variant == 6) {  // BEZ_VAR_TEX_DECASTELJAU
+        kind = d == 3 ? TK_DC3 : TK_DCN;
+        wt = d >= 3 ? d - 1 : 2;
+        is3d = true;
+    } else if (variant == 8) {  // BEZ_VAR_TEX_HYBRID
+        kind = d == 3 ? TK_HYB3 : TK_HYBN;
+        wt = d >= 2 ? d : 2;
+        is3d = false;
+    } else {  // BEZ_VAR_TEX_SEILER
+        kind = d <= 3 ? TK_SEIL2 : TK_SEIL3;
+        wt = 2;
+        is3d = d > 3;
+    }
+    const int max_w = is3d ? ts.max3d : ts.max2d_w;
+    const int tw = tiles_per_row(a.n_curves, wt, max_w);
+    const int64_t rows = (a.n_curves + tw - 1) / tw;
+    const int64_t h_needed = rows * 2;
+    if (h_needed > (is3d ? ts.max3d : ts.max2d_h)) return {0, cudaErrorInvalidValue};
+    Atlas& at = kind == TK_DC3 || kind == TK_DCN ? ts.dc3
+                : kind == TK_HYB3 || kind == TK_HYBN ? ts.strip2
+                : kind == TK_SEIL2 ? ts.seil2 : ts.seil3;
+    cudaError_t e = atlas_ensure(at, tw * wt, (int)h_needed, is3d ? 2 : 0, fmt);
+    if (e != cudaSuccess) return {0, e};
+    switch (kind) {
+    case TK_DC3: return launch_kind<TK_DC3>(a, tm, om, at, tw, wt, s, h);
+    case TK_DCN: return launch_kind<TK_DCN>(a, tm, om, at, tw, wt, s, h);
+    case TK_HYB3: return launch_kind<TK_HYB3>(a, tm, om, at, tw, wt, s, h);
+    case TK_HYBN: return launch_kind<TK_HYBN>(a, tm, om, at, tw, wt, s, h);
+    case TK_SEIL2: return launch_kind<TK_SEIL2>(a, tm, om, at, tw, wt, s, h);
+    default: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, s, h);
+    }
+}
+
+// ---------------------------------------------------------------- zig-zag C0 chains
+
+// Sec. 2.1 (Eq. 1-2, Fig. 2): N quadratic segments with shared end points in
+// an (N+1) x 2 texture.  Column k holds P_(2k) in row k mod 2 and a free
+// texel F_k in the other row.  Segment k is read between (k, k mod 2) and
+// (k+1, 1 - k mod 2); bilinear filtering there gives
+//   (1-tau)^2 P_2k + tau (1-tau) (F_k + F_(k+1)) + tau^2 P_(2k+2),
+// the quadratic with middle point (F_k + F_(k+1)) / 2, so the N constraints
+// are F_k + F_(k+1) = 2 P_(2k+1) on N+1 unknowns.  The free choice of F_0
+// (per component) minimises max_k |F_k|: with F_k = (-1)^k F_0 + G_k,
+// F_0 = -(max_k H_k + min_k H_k) / 2 for H_k = (-1)^k G_k.  Each F_(k+1) is
+// formed from the stored F_k, so every constraint holds to one rounding.
+__global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf, int fmt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_curves) return;
+    const int N = a.n_seg, dim = a.dim;
+    const int64_t base = c * (int64_t)(2 * N + 1) * dim;
+    auto P = [&](int i, int k) { return load_elem(a.ctrl, a.dtype, base + (int64_t)i * dim + k); };
+    float f0[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < dim; ++k) {
+        float g = 0.f, hmax = 0.f, hmin = 0.f;  // G_0 = 0
+        for (int s = 0; s < N; ++s) {
+            g = 2.f * P(2 * s + 1, k) - g;      // G_(s+1)
+            const float h = (s & 1) ? g : -g;   // H_(s+1) = (-1)^(s+1) G_(s+1)
+            hmax = fmaxf(hmax, h);
+            hmin = fminf(hmin, h);
+        }
+        f0[k] = -0.5f * (hmax + hmin);
+    }
+    const int x0 = (int)(c % cw) * (N + 1), y0 = (int)(c / cw) * 2;
+    float4 F = make_float4(f0[0], f0[1], f0[2], f0[3]);
+    for (int s = 0; s <= N; ++s) {
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < dim; ++k) p[k] = P(2 * s, k);
+        const float4 Pe = make_float4(p[0], p[1], p[2], p[3]);
+        const bool hw = fmt == 1;
+        if (hw) {  // store what the half texture holds, so the next constraint uses it
+            F = make_float4(__half2float(__float2half_rn(F.x)), __half2float(__float2half_rn(F.y)),
+                            __half2float(__float2half_rn(F.z)), __half2float(__float2half_rn(F.w)));
+        }
+        put(surf, fmt, x0 + s, y0 + (s & 1), 0, false, Pe);
+        put(surf, fmt, x0 + s, y0 + 1 - (s & 1), 0, false, F);
+        if (s < N) {
+            float m[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < dim; ++k) m[k] = P(2 * s + 1, k);
+            F = make_float4(2.f * m[0] - F.x, 2.f * m[1] - F.y, 2.f * m[2] - F.z, 2.f * m[3] - F.w);
+        }
+    }
+}
+
+template <int TM>
+__device__ __forceinline__ float4 zigzag_eval(const CurveArgs& a, cudaTextureObject_t tex, int64_t c, int j,
+                                              uint32_t kc, float xb, float yb)
+{
+    const float ns = (float)a.n_seg;
+    float t;
+    if (TM == TM_ARRAY) {
+        t = __ldg(a.t + c * a.t_stride + j);
+        t = t < 0.f ? 0.f : (t > ns ? ns : t);
+    } else if (TM == TM_UNIFORM) {
+        t = ns * (a.n_t > 1 ? __fdiv_rn((float)j, (float)(a.n_t - 1)) : 0.f);
+    } else {
+        t = ns * hash_unit(lowbias32(kc ^ (uint32_t)j));
+    }
+    int k = (int)floorf(t);
+    k = k < 0 ? 0 : (k > a.n_seg - 1 ? a.n_seg - 1 : k);
+    const float tau = t - (float)k;
+    const float y = (k & 1) ? 1.f - tau : tau;
+    float4 P = tex2D<float4>(tex, (xb + (float)k) + tau, yb + y);
+    if (TM == TM_ARRAY && t != t) P = make_float4(t, t, t, t);
+    return P;
+}
+
+template <int TM, int OM>
+__global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cudaTextureObject_t tex, int cw)
+{
+    __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * 4 : 1];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    const int dim = a.dim;
+    for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
+        const float xb = (float)((int)(c % cw) * (a.n_seg + 1)) + 0.5f;
+        const float yb = (float)((int)(c / cw) * 2) + 0.5f;
+        const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
+        const int n_t = a.n_t;
+        if (OM == OM_POINTS) {
+            float* stage = s_stage + wib * 32 * 4;
+            for (int j0 = 0; j0 < n_t; j0 += 32) {
+                const int j = j0 + lane;
+                float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < n_t) P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb);
+                const float pv[4] = {P.x, P.y, P.z, P.w};
+                for (int k = 0; k < dim; ++k) stage[lane * dim + k] = pv[k];
+                __syncwarp();
+                const int valid = min(32, n_t - j0) * dim;
+                float* o = a.out + (c * n_t + j0) * dim;
+                for (int idx = lane; idx < valid; idx += 32) o[idx] = stage[idx];
+                __syncwarp();
+            }
+        } else {
+            const int chunk = (n_t + 31) / 32;
+            const int jb = lane * chunk;
+            const int je = min(jb + chunk, n_t);
+            float acc = 0.f;
+            float4 first = make_float4(0.f, 0.f, 0.f, 0.f), prev = first;
+            if (jb < je) {
+                first = prev = zigzag_eval<TM>(a, tex, c, jb, kc, xb, yb);
+#pragma unroll 4
+                for (int j = jb + 1; j < je; ++j) {
+                    const float4 P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb);
+                    acc += seg_len4(P, prev);
+                    prev = P;
+                }
+            }
+            float4 pl;
+            pl.x = __shfl_up_sync(kFull, prev.x, 1);
+            pl.y = __shfl_up_sync(kFull, prev.y, 1);
+            pl.z = __shfl_up_sync(kFull, prev.z, 1);
+            pl.w = __shfl_up_sync(kFull, prev.w, 1);
+            if (lane > 0 && jb < je) acc += seg_len4(first, pl);
+            acc = warp_sum(acc);
+            if (lane == 0) a.out[c] = acc;
+        }
+    }
+}
+
+LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, cudaStream_t s, const LaunchHooks& h)
+{
+    const int wt = a.n_seg + 1;
+    const int fmt = a.dtype == 1 ? 1 : 0;
+    const int cw = tiles_per_row(a.n_curves, wt, ts.max2d_w);
+    const int64_t h_needed = (a.n_curves + cw - 1) / cw * 2;
+    if (h_needed > ts.max2d_h || (int64_t)cw * wt > ts.max2d_w) return {0, cudaErrorInvalidValue};
+    cudaError_t e = atlas_ensure(ts.chain, cw * wt, (int)h_needed, 0, fmt);
+    if (e != cudaSuccess) return {0, e};
+    h.count(h.self);
+    k_chain_pack<<<(unsigned)((a.n_curves + 127) / 128), 128, 0, s>>>(a, cw, ts.chain.surf, fmt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return {1, e};
+    const void* kern;
+    if (om == OM_POINTS)
+        kern = tm == TM_ARRAY ? (const void*)k_chain_tex<TM_ARRAY, OM_POINTS>
+               : tm == TM_UNIFORM ? (const void*)k_chain_tex<TM_UNIFORM, OM_POINTS>
+                                  : (const void*)k_chain_tex<TM_HASH, OM_POINTS>;
+    else
+        kern = tm == TM_ARRAY ? (const void*)k_chain_tex<TM_ARRAY, OM_LENGTH>
+               : tm == TM_UNIFORM ? (const void*)k_chain_tex<TM_UNIFORM, OM_LENGTH>
+                                  : (const void*)k_chain_tex<TM_HASH, OM_LENGTH>;
+    const int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, (a.n_curves + kWarps - 1) / kWarps);
+    cudaTextureObject_t tex = ts.chain.tex;
+    int cw_arg = cw;
+    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg};
+    h.count(h.self);
+    h.begin(h.self, s);
+    e = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);
+    h.end(h.self, s);
+    return {2, e};
+}
+
+// ---------------------------------------------------------------- weight probe
+
+__global__ void k_probe_pack(cudaSurfaceObject_t surf)
+{
+    const int x = threadIdx.x & 1, y = (threadIdx.x >> 1) & 1, z = threadIdx.x >> 2;
+    surf3Dwrite(make_float4((float)x, (float)y, (float)z, 0.f), surf, x * 16, y, z);
+}
+
+__global__ void k_probe(cudaTextureObject_t tex, const float* xyz, int64_t n, float* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = tex3D<float4>(tex, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+    out[3 * i] = v.x;
+    out[3 * i + 1] = v.y;
+    out[3 * i + 2] = v.z;
+}
+
+LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState& ts, cudaStream_t s,
+                              const LaunchHooks& h)
+{
+    cudaError_t e = atlas_ensure(ts.probe, 2, 2, 2, 0);
+    if (e != cudaSuccess) return {0, e};
+    h.count(h.self);
+    k_probe_pack<<<1, 8, 0, s>>>(ts.probe.surf);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || n == 0) return {1, e};
+    h.count(h.self);
+    h.begin(h.self, s);
+    k_probe<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ts.probe.tex, xyz, n, out);
+    e = cudaGetLastError();
+    h.end(h.self, s);
+    return {2, e};
+}
+
+}  // namespace bez

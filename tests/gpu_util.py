@@ -63,3 +63,16 @@ def horner_bound(ctrl, t):
     conv_k = np.array([comb(d, k) * (gamma(k + 1) * 2 ** k + U32) for k in range(d + 1)])
     conv = np.einsum("bnk,k,bc->bnc", powk, conv_k, M) * 2
     return horner + conv + 1e-30
+
+
+def normalised_error_ctrl(got, ref, ctrl):
+    """Secondary normaliser: per-curve max point error over the diagonal of
+    the control polygon's bounding box (floor 2^-4).  Used for point
+    dimensions other than 3, where a curve's sampled range can be far
+    smaller than its control values (a scalar polynomial with a flat stretch)
+    and the primary normaliser becomes ill-conditioned."""
+    got = np.asarray(got, np.float64)
+    err = np.linalg.norm(got - ref, axis=-1)
+    c = np.asarray(ctrl, np.float64)
+    diag = np.linalg.norm(c.max(axis=1) - c.min(axis=1), axis=-1)
+    return err.max(axis=1) / np.maximum(diag, DELTA)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import horner_bound, need_gpu, normalised_error
+from gpu_util import horner_bound, need_gpu, normalised_error, normalised_error_ctrl
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,7 @@ def test_points_other_dims_per_curve_t(variant, dim):
     if variant == "HORNER":
         assert np.all(np.abs(got - ref) <= horner_bound(ctrl.astype(np.float64), t.astype(np.float64)))
     else:
-        assert normalised_error(got, ref).max() <= FP32_BAR
+        assert normalised_error_ctrl(got, ref, ctrl).max() <= FP32_BAR
 
 
 @pytest.mark.parametrize("variant", ALL)
