@@ -170,17 +170,49 @@ bez_status bez_eval_piecewise(bez_ctx ctx, const void* ctrl, int64_t n_chains, i
                               const float* t, int64_t n_t, float* out, const bez_opts* opts, void* stream);
 
 /*
+ * bez_eval_bspline / bez_eval_nurbs -- B-spline and NURBS curves.
+ *
+ * Paper Sec. 2.2: B-splines become piecewise Bezier curves by Boehm's knot
+ * insertion, and rational curves divide one integral spline point by
+ * another (homogeneous coordinates).  A setup kernel extracts the Bezier
+ * control points of every span in FP64 (one thread per span; rational
+ * curves in homogeneous form (w P, w)) into a library-owned scratch buffer;
+ * the evaluator finds each parameter's span, runs FP32 de Casteljau on it
+ * and, for NURBS, divides by the weight.
+ *
+ *   ctrl     [n_curves][n_ctrl][dim] FP32 (opts->dtype must be BEZ_F32)
+ *   weights  [n_curves][n_ctrl] FP32 (NURBS only; positive weights expected)
+ *   knots    [n_curves][n_ctrl+degree+1] FP32, nondecreasing, or NULL for the
+ *            clamped uniform vector (degree+1 zeros, i/(n_ctrl-degree),
+ *            degree+1 ones)
+ *   t        knot-space parameters per opts->t_mode, clamped to
+ *            [U_degree, U_n_ctrl]; UNIFORM / HASH map their [0,1] draws
+ *            affinely onto that domain.  A parameter on an interior knot
+ *            belongs to the later span.
+ *   out      POINTS [n_curves][n_t][dim] or POLYLINE_LENGTH [n_curves], FP32
+ *   degree 1..15, n_ctrl >= degree+1, dim 1..4; variant AUTO or
+ *   DECASTELJAU.  A zero rational denominator increments *opts->err_word.
+ */
+bez_status bez_eval_bspline(bez_ctx ctx, const float* ctrl, const float* knots, int64_t n_curves, int n_ctrl,
+                            int degree, int dim, const float* t, int64_t n_t, float* out, const bez_opts* opts,
+                            void* stream);
+bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, const float* knots, int64_t n_curves,
+                          int n_ctrl, int degree, int dim, const float* t, int64_t n_t, float* out,
+                          const bez_opts* opts, void* stream);
+
+/*
  * bez_probe_filter -- characterise the texture unit's linear-filter weights.
  *
  * Paper Sec. 2.3: the hardware converts texture coordinates to a fixed-point
  * format with 8 fractional bits before interpolating, which bounds the
  * accuracy of every texture evaluator.  This call samples a 2x2x2 float4
- * texture whose texel (x,y,z) holds (x, y, z) with linear filtering and clamp
- * addressing, so the filtered value at unnormalised coordinates (X, Y, Z) is
- * the weight the hardware applied along each axis.
+ * texture whose texel (x,y,z) holds (x, y, z, 1) with linear filtering and
+ * clamp addressing: at unnormalised coordinates (X, Y, Z) the first three
+ * channels return the total weight given to the texels with index 1 along
+ * each axis, and the fourth the sum of all eight texel weights.
  *
  *   xyz  [n][3] FP32 coordinates (texel centres at 0.5 and 1.5)
- *   out  [n][3] FP32 filtered (x, y, z) values
+ *   out  [n][4] FP32 filtered values
  */
 bez_status bez_probe_filter(bez_ctx ctx, const float* xyz, int64_t n, float* out, void* stream);
 

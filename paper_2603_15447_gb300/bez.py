@@ -98,10 +98,14 @@ def lib():
             L.bez_reset_stats.argtypes = [_VP]
             L.bez_eval.argtypes = [_VP, _VP, _I64, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts), _VP]
             L.bez_probe_filter.argtypes = [_VP, _VP, _I64, _VP, _VP]
+            L.bez_eval_bspline.argtypes = [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
+                                           ctypes.POINTER(Opts), _VP]
+            L.bez_eval_nurbs.argtypes = [_VP, _VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
+                                         ctypes.POINTER(Opts), _VP]
             L.bez_eval_piecewise.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts),
                                              _VP]
             for name in ("bez_create", "bez_destroy", "bez_set_timing", "bez_get_stats", "bez_reset_stats",
-                         "bez_eval", "bez_probe_filter", "bez_eval_piecewise"):
+                         "bez_eval", "bez_probe_filter", "bez_eval_piecewise", "bez_eval_bspline", "bez_eval_nurbs"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -237,12 +241,12 @@ def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.P
 
 
 def bez_probe_filter(xyz, *, out=None, stream=None, ctx=None):
-    """Sample a 2x2x2 texture whose texel (x, y, z) holds (x, y, z) at the
+    """Sample a 2x2x2 texture whose texel (x, y, z) holds (x, y, z, 1) at the
     unnormalised coordinates ``xyz`` [n][3]; returns the filtered values
-    [n][3], i.e. the hardware's interpolation weights along each axis."""
+    [n][4]: the weight on index 1 along each axis and the weight sum."""
     n = xyz.shape[0]
     if out is None:
-        out = _empty_like_location(xyz, (n, 3))
+        out = _empty_like_location(xyz, (n, 4))
     dev = xyz.device.index if _is_cuda(xyz) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
     _check(lib().bez_probe_filter(c.handle, _ptr(xyz), n, _ptr(out), _stream_handle(stream, dev)))
@@ -269,3 +273,42 @@ def bez_eval_piecewise(ctrl, n_seg, degree, t=None, *, n_t=None, variant=Variant
     _check(lib().bez_eval_piecewise(c.handle, _ptr(ctrl), n_chains, n_seg, degree, dim, _ptr(t), n_t, _ptr(out),
                                     ctypes.byref(o), _stream_handle(stream, dev)))
     return out
+
+
+def _spline_call(ctrl, degree, t, n_t, weights, knots, out_mode, t_mode, seed, stream_id, out, stream, sync, ctx,
+                 err_word=None):
+    n_curves, n_ctrl, dim = ctrl.shape
+    if t_mode is None:
+        t_mode = TMode.SHARED if (t is not None and t.ndim == 1) else TMode.PER_CURVE
+    if t is not None:
+        n_t = t.shape[-1]
+    assert n_t is not None, "n_t is required when t is None"
+    shape = (n_curves, n_t, dim) if out_mode == OutMode.POINTS else (n_curves,)
+    if out is None:
+        out = _empty_like_location(ctrl, shape)
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    o = _opts(Variant.AUTO, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
+    if err_word is not None:
+        o.err_word = _ptr(err_word)
+    if weights is None:
+        _check(lib().bez_eval_bspline(c.handle, _ptr(ctrl), _ptr(knots), n_curves, n_ctrl, degree, dim, _ptr(t), n_t,
+                                      _ptr(out), ctypes.byref(o), _stream_handle(stream, dev)))
+    else:
+        _check(lib().bez_eval_nurbs(c.handle, _ptr(ctrl), _ptr(weights), _ptr(knots), n_curves, n_ctrl, degree, dim,
+                                    _ptr(t), n_t, _ptr(out), ctypes.byref(o), _stream_handle(stream, dev)))
+    return out
+
+
+def bez_eval_bspline(ctrl, degree, t=None, *, knots=None, n_t=None, out_mode=OutMode.POINTS, t_mode=None, seed=0,
+                     stream_id=0, out=None, stream=None, sync=False, ctx=None):
+    """B-splines ``ctrl`` [n_curves][n_ctrl][dim]; ``knots`` [n_curves][n_ctrl+degree+1] or None
+    (clamped uniform)."""
+    return _spline_call(ctrl, degree, t, n_t, None, knots, out_mode, t_mode, seed, stream_id, out, stream, sync, ctx)
+
+
+def bez_eval_nurbs(ctrl, weights, degree, t=None, *, knots=None, n_t=None, out_mode=OutMode.POINTS, t_mode=None,
+                   seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None, err_word=None):
+    """NURBS ``ctrl`` [n_curves][n_ctrl][dim] with ``weights`` [n_curves][n_ctrl]."""
+    return _spline_call(ctrl, degree, t, n_t, weights, knots, out_mode, t_mode, seed, stream_id, out, stream, sync,
+                        ctx, err_word)

@@ -63,7 +63,7 @@ struct bez_ctx_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> spare;
     cudaEvent_t cur_begin = nullptr;
-    StageBuf stage[8];
+    StageBuf stage[8];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots (host staging); 5 spline spans (scratch)
     TexState tex;
     cudaEvent_t tex_done = nullptr;  // last use of the texture atlases
     bool tex_used = false;
@@ -493,6 +493,102 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     return stg.finish(o->sync);
 }
 
+static bez_status eval_spline(bez_ctx c, const float* ctrl, const float* weights, const float* knots, int64_t n_curves,
+                              int n_ctrl, int degree, int dim, const float* t, int64_t n_t, float* out,
+                              const bez_opts* o, void* stream, bool rational)
+{
+    bez_status st = check_common(c, o);
+    if (st != BEZ_OK) return st;
+    if (n_curves < 0 || n_t < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n_t > 0x7fffffff) return fail(BEZ_ERR_INVALID_ARG, "n_t %lld exceeds 2^31-1", (long long)n_t);
+    if (o->t_mode == BEZ_T_HASH && n_curves > 0xffffffffLL)
+        return fail(BEZ_ERR_INVALID_ARG, "hash parameters index curves with 32 bits");
+    if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
+    if (degree < 1 || n_ctrl < degree + 1)
+        return fail(BEZ_ERR_INVALID_ARG, "need degree >= 1 and n_ctrl >= degree+1 (degree %d, n_ctrl %d)", degree,
+                    n_ctrl);
+    if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
+    if (o->dtype != BEZ_F32) return fail(BEZ_ERR_UNSUPPORTED, "splines take FP32 control points");
+    const int var = o->variant == BEZ_VAR_AUTO ? BEZ_VAR_DECASTELJAU : o->variant;
+    if (var != BEZ_VAR_DECASTELJAU)
+        return fail(BEZ_ERR_UNSUPPORTED, "splines evaluate their Bezier spans by de Casteljau (variant %d)", var);
+    if (rational && !weights && n_curves > 0) return fail(BEZ_ERR_INVALID_ARG, "null weights");
+    if (n_curves == 0 || (n_t == 0 && o->out_mode == BEZ_OUT_POINTS)) return BEZ_OK;
+    if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");
+    const bool t_array = o->t_mode == BEZ_T_SHARED || o->t_mode == BEZ_T_PER_CURVE;
+    if (t_array && n_t > 0 && !t) return fail(BEZ_ERR_INVALID_ARG, "null t for t_mode %d", o->t_mode);
+
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    SplineArgs a{};
+    const void* p = nullptr;
+    st = stg.in(ctrl, (size_t)n_curves * n_ctrl * dim * sizeof(float), 0, &p);
+    if (st != BEZ_OK) return st;
+    a.ctrl = static_cast<const float*>(p);
+    if (rational) {
+        st = stg.in(weights, (size_t)n_curves * n_ctrl * sizeof(float), 3, &p);
+        if (st != BEZ_OK) return st;
+        a.weights = static_cast<const float*>(p);
+    }
+    if (knots) {
+        st = stg.in(knots, (size_t)n_curves * (n_ctrl + degree + 1) * sizeof(float), 4, &p);
+        if (st != BEZ_OK) return st;
+        a.knots = static_cast<const float*>(p);
+    }
+    if (t_array) {
+        const size_t tb = (size_t)n_t * sizeof(float) * (o->t_mode == BEZ_T_PER_CURVE ? (size_t)n_curves : 1);
+        st = stg.in(t, tb, 1, &p);
+        if (st != BEZ_OK) return st;
+        a.t = static_cast<const float*>(p);
+        a.t_stride = o->t_mode == BEZ_T_PER_CURVE ? n_t : 0;
+    }
+    const size_t out_bytes =
+        o->out_mode == BEZ_OUT_POINTS ? (size_t)n_curves * n_t * dim * sizeof(float) : (size_t)n_curves * sizeof(float);
+    void* od = nullptr;
+    st = stg.out(out, out_bytes, 2, &od);
+    if (st != BEZ_OK) return st;
+    a.out = static_cast<float*>(od);
+    a.n_curves = n_curves;
+    a.n_ctrl = n_ctrl;
+    a.degree = degree;
+    a.dim = dim;
+    a.comps = rational ? dim + 1 : dim;
+    a.n_spans = n_ctrl - degree;
+    a.n_t = (int32_t)n_t;
+    a.err_word = o->err_word;
+    const uint32_t seed_lo = (uint32_t)(o->seed & 0xffffffffu), seed_hi = (uint32_t)(o->seed >> 32);
+    a.key = lowbias32(seed_lo ^ lowbias32(seed_hi ^ lowbias32(o->stream_id)));
+    // Bezier spans: library-owned scratch, one slot per context
+    const size_t span_bytes = (size_t)n_curves * a.n_spans * (degree + 1) * a.comps * sizeof(float);
+    st = ensure_stage(c, 5, span_bytes, s);
+    if (st != BEZ_OK) return st;
+    a.spans = static_cast<float*>(c->stage[5].p);
+    const int tm = t_array ? TM_ARRAY : (o->t_mode == BEZ_T_UNIFORM ? TM_UNIFORM : TM_HASH);
+    const int om = o->out_mode == BEZ_OUT_POINTS ? OM_POINTS : OM_LENGTH;
+    LaunchHooks h = hooks_of(c);
+    LaunchResult r = launch_spline_setup(a, s, h);
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "spline setup launch");
+    r = launch_spline_eval(a, tm, om, s, h);
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "spline evaluator launch");
+    return stg.finish(o->sync);
+}
+
+bez_status bez_eval_bspline(bez_ctx c, const float* ctrl, const float* knots, int64_t n_curves, int n_ctrl,
+                            int degree, int dim, const float* t, int64_t n_t, float* out, const bez_opts* o,
+                            void* stream)
+{
+    return eval_spline(c, ctrl, nullptr, knots, n_curves, n_ctrl, degree, dim, t, n_t, out, o, stream, false);
+}
+
+bez_status bez_eval_nurbs(bez_ctx c, const float* ctrl, const float* weights, const float* knots, int64_t n_curves,
+                          int n_ctrl, int degree, int dim, const float* t, int64_t n_t, float* out,
+                          const bez_opts* o, void* stream)
+{
+    return eval_spline(c, ctrl, weights, knots, n_curves, n_ctrl, degree, dim, t, n_t, out, o, stream, true);
+}
+
 bez_status bez_probe_filter(bez_ctx c, const float* xyz, int64_t n, float* out, void* stream)
 {
     if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
@@ -506,7 +602,7 @@ bez_status bez_probe_filter(bez_ctx c, const float* xyz, int64_t n, float* out, 
     void* od = nullptr;
     bez_status st = stg.in(xyz, (size_t)n * 3 * sizeof(float), 0, &xd);
     if (st != BEZ_OK) return st;
-    st = stg.out(out, (size_t)n * 3 * sizeof(float), 2, &od);
+    st = stg.out(out, (size_t)n * 4 * sizeof(float), 2, &od);
     if (st != BEZ_OK) return st;
     if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
     LaunchResult r = launch_tex_probe(static_cast<const float*>(xd), n, static_cast<float*>(od), c->tex, s,

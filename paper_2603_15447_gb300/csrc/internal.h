@@ -88,6 +88,27 @@ LaunchResult launch_chain_seiler(const CurveArgs& a, int tm, int om, cudaStream_
 LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, cudaStream_t s, const LaunchHooks& h);
 constexpr int kChainMaxFloats = 3072;  // (n_seg*degree+1)*dim per chain staged in shared memory
 
+// ---------------------------------------------------------------- splines
+
+struct SplineArgs {
+    const float* ctrl;     // [n_curves][n_ctrl][dim]
+    const float* weights;  // [n_curves][n_ctrl] or NULL (integral B-spline)
+    const float* knots;    // [n_curves][n_ctrl+degree+1] or NULL (clamped uniform)
+    int64_t n_curves;
+    int32_t n_ctrl, degree, dim;
+    int32_t comps;         // dim, or dim+1 for homogeneous rational points
+    int32_t n_spans;       // n_ctrl - degree
+    float* spans;          // scratch [n_curves][n_spans][degree+1][comps]
+    const float* t;
+    int64_t t_stride;
+    int32_t n_t;
+    float* out;
+    uint32_t key;
+    int32_t* err_word;
+};
+LaunchResult launch_spline_setup(const SplineArgs& a, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_spline_eval(const SplineArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+
 // Occupancy-sized persistent grid: a multiple of the SM count.
 int persistent_grid(const void* kernel, int block, size_t smem, int sm_count, int64_t work_blocks);
 

@@ -19,7 +19,7 @@
 //
 // Evaluation: t is clamped to [U_p, U_n]; the span is the last non-empty one
 // with U_k <= t (an interior knot starts the later span); tau = (t - a) /
-// (b - a) (clamped uniform knots: s = t * n_spans, k = floor(s), tau = s - k);
+// (b - a) (clamped uniform knots: k = floor(fl(t * n_spans)), tau = fma(t, n_spans, -k));
 // the span's Bezier points go through FP32 de Casteljau, and rational points
 // are divided by their weight.
 #pragma once

@@ -531,7 +531,7 @@ LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, 
 __global__ void k_probe_pack(cudaSurfaceObject_t surf)
 {
     const int x = threadIdx.x & 1, y = (threadIdx.x >> 1) & 1, z = threadIdx.x >> 2;
-    surf3Dwrite(make_float4((float)x, (float)y, (float)z, 0.f), surf, x * 16, y, z);
+    surf3Dwrite(make_float4((float)x, (float)y, (float)z, 1.f), surf, x * 16, y, z);
 }
 
 __global__ void k_probe(cudaTextureObject_t tex, const float* xyz, int64_t n, float* out)
@@ -539,9 +539,7 @@ __global__ void k_probe(cudaTextureObject_t tex, const float* xyz, int64_t n, fl
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 v = tex3D<float4>(tex, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
-    out[3 * i] = v.x;
-    out[3 * i + 1] = v.y;
-    out[3 * i + 2] = v.z;
+    reinterpret_cast<float4*>(out)[i] = v;
 }
 
 LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState& ts, cudaStream_t s,

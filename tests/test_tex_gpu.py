@@ -1,14 +1,21 @@
 """GPU parity of the texture-path evaluators (paper Sec. 2, 2.3, 4 and Fig. 3).
 
-Linear filtering converts each coordinate to a weight with 8 fractional bits
-(Sec. 2.3), so a texture evaluator does not reach the oracle to FP32
-accuracy.  Its tolerance is derived here from the texel layout the paper
-gives: along each filtered axis the point moves by at most (weight error) x
-(largest texel difference along that axis), and FP32 lerps done afterwards
-in registers are convex and do not enlarge an error.  The weight error per
-axis is bounded by 2^-8 (quantisation, either rounding or truncation) plus
-2^-12 (rounding of the unnormalised coordinate in the atlases used here).
-The probe test measures the weights themselves."""
+Linear filtering works with weights of 8 fractional bits (Sec. 2.3), so a
+texture evaluator does not reach the oracle to FP32 accuracy.  The tolerance
+of one filtered fetch is taken as
+
+    (number of filtered axes) x (2^-8 + 2^-11) x |range of the tile's texels|
+
+per point: the filtered value is a weighted mean of the tile's texels whose
+weights still sum to one (measured exactly by the probe below), so moving
+weight between texels moves the result by at most the moved weight times the
+texel range; each filtered axis moves at most 2^-8 (8-bit weights; the probe
+sees up to 1.5 x 2^-8 on one marginal when three axes are off-centre, within
+3 x 2^-8) plus 2^-11 for the FP32 rounding of the unnormalised coordinate in
+atlases up to 4096 texels wide.  FP32 lerps done afterwards in registers are
+convex and do not enlarge the error.  The tiles are rebuilt here from the
+paper's layouts.  This is a hardware-model tolerance: the paper fixes the
+weight format, not the filter's internal rounding."""
 import numpy as np
 import pytest
 
@@ -18,7 +25,7 @@ from gpu_util import need_gpu, normalised_error
 pytestmark = pytest.mark.gpu
 
 U = 2.0 ** -24
-WERR = 2.0 ** -8 + 2.0 ** -12
+WERR = 2.0 ** -8 + 2.0 ** -11
 
 
 def _run(torch, ctrl, t=None, n_t=None, variant="TEX_DECASTELJAU", out_mode="POINTS", t_mode=None, seed=0,
@@ -34,9 +41,9 @@ def _run(torch, ctrl, t=None, n_t=None, variant="TEX_DECASTELJAU", out_mode="POI
     return out.cpu().numpy()
 
 
-def _edge_max(b):
-    """max_k |b_(k+1) - b_k|_2 per curve."""
-    return np.linalg.norm(np.diff(b, axis=1), axis=-1).max(axis=1)
+def _range(tiles):
+    """|max - min|_2 over the texels of each tile: tiles [B][n_texels][dim]."""
+    return np.linalg.norm(tiles.max(axis=1) - tiles.min(axis=1), axis=-1)
 
 
 def _seiler_terms(b):
@@ -55,58 +62,65 @@ def _seiler_terms(b):
 
 
 def texture_bound(variant, ctrl, texel_eps=U):
-    """Per-curve bound on |P_tex - C| from the texel layout (see module doc).
-    texel_eps: relative rounding of a stored texel (2^-24 float, 2^-11 half)."""
+    """Per-curve bound on |P_tex - C| (see module doc).  texel_eps: relative
+    rounding of a stored texel (2^-24 float, 2^-11 half)."""
     b = ctrl.astype(np.float64)
     B, d1_, dim = b.shape
     d = d1_ - 1
-    n = lambda x: np.linalg.norm(x, axis=-1)
-    M = np.abs(b).max(axis=(1, 2))
     if variant == "TEX_DECASTELJAU":
-        axes = min(d, 3)
-        bound = axes * WERR * _edge_max(b)
-        tex_mag = M
+        # tile of window i holds b_i..b_(i+3) (degree <= 2: b_0..b_d)
+        w = min(d, 3)
+        bound = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0) * w * WERR
+        tex_mag = np.abs(b).max(axis=(1, 2))
     elif variant == "TEX_HYBRID":
-        axes = min(d, 2)
-        bound = axes * WERR * _edge_max(b)
-        tex_mag = M
+        w = min(d, 2)
+        bound = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0) * w * WERR
+        tex_mag = np.abs(b).max(axis=(1, 2))
     else:
         d1, dl, d2, dl2 = _seiler_terms(b)
         b0, bd = b[:, 0], b[:, d]
         s1, s2 = b0 + d1, bd + dl
         if d <= 3:
-            ex = np.maximum(n(bd - b0), n(s2 - s1))
-            ey = np.maximum(n(d1), n(dl))
-            bound = WERR * (ex + ey)
-            tex_mag = np.maximum(M, np.abs(np.stack([s1, s2], 1)).max(axis=(1, 2)))
+            tiles = np.stack([b0, bd, s1, s2], 1)
+            axes = 2
         else:
-            ex = np.max(np.stack([n(bd - b0), n(s2 - s1), n((s2 + dl2) - (s1 + d2))]), axis=0)
-            ey = np.maximum(n(d2), n(dl2))
-            ez = np.max(np.stack([n(d1), n(dl), n(d1 + d2), n(dl + dl2)]), axis=0)
-            bound = WERR * (ex + ey + ez)
-            tex_mag = np.abs(np.stack([b0, bd, s1, s2, s1 + d2, s2 + dl2], 1)).max(axis=(1, 2))
-    # texel rounding (Seiler sums), filter and register-lerp rounding
+            tiles = np.stack([b0, bd, s1, s2, s1 + d2, s2 + dl2], 1)
+            axes = 3
+        bound = axes * WERR * _range(tiles)
+        tex_mag = np.abs(tiles).max(axis=(1, 2))
+    # texel rounding (Seiler sums, half texels), filter and register-lerp rounding
     slack = (4 * texel_eps + (d + 12) * U) * tex_mag * np.sqrt(dim)
     return bound + slack
 
 
-def test_filter_weight_probe_characterisation():
+def test_filter_weight_probe_single_axis():
+    # Along one axis (the others at texel centres) the weight is the
+    # fractional coordinate on 8 fractional bits (Sec. 2.3), within 2^-8 of
+    # exact and exact at texel centres; weights sum to one.
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
     k = np.arange(0, 4097)
     frac = k / 4096.0
-    xyz = np.stack([0.5 + frac, 0.5 + frac[::-1], np.full_like(frac, 1.0)], 1).astype(np.float32)
+    xyz = np.stack([0.5 + frac, np.full_like(frac, 0.5), np.full_like(frac, 1.5)], 1).astype(np.float32)
     got = bez.bez_probe_filter(torch.from_numpy(xyz).cuda()).cpu().numpy().astype(np.float64)
-    # every weight is a multiple of 2^-8 (8 fractional bits, Sec. 2.3) ...
-    np.testing.assert_array_equal(got * 256, np.round(got * 256))
-    # ... within 2^-8 of the exact weight, exact at texel centres
+    np.testing.assert_array_equal(got[:, 0] * 256, np.round(got[:, 0] * 256))
     assert np.abs(got[:, 0] - frac).max() <= 2.0 ** -8
-    assert np.abs(got[:, 1] - frac[::-1]).max() <= 2.0 ** -8
-    np.testing.assert_array_equal(got[:, 2], 0.5)
+    np.testing.assert_array_equal(got[:, 1], 0.0)
+    np.testing.assert_array_equal(got[:, 2], 1.0)
+    np.testing.assert_array_equal(got[:, 3], 1.0)
     assert got[0, 0] == 0.0 and got[-1, 0] == 1.0
+    # three axes off-centre: weights still sum to one, every marginal within
+    # the 3 x 2^-8 the tolerance above allows for a trilinear fetch
+    g = np.arange(0, 33) / 32.0
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    xyz = np.stack([0.5 + X.ravel(), 0.5 + Y.ravel(), 0.5 + Z.ravel()], 1).astype(np.float32)
+    got3 = bez.bez_probe_filter(torch.from_numpy(xyz).cuda()).cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(got3[:, 3], 1.0)
+    for ax, E in enumerate((X, Y, Z)):
+        assert np.abs(got3[:, ax] - E.ravel()).max() <= 3 * 2.0 ** -8
     err = got[:, 0] - frac
-    mode = "round-to-nearest" if err.max() > 2.0 ** -10 and err.min() < -2.0 ** -10 else "truncate"
-    print(f"\nfilter weights: 8 fractional bits, {mode}; max |w - t| = {np.abs(err).max():.6f}")
+    mode = "round-to-nearest" if err.min() < -2.0 ** -10 else "truncate"
+    print(f"\nsingle-axis filter weight: 8 fractional bits, {mode}; max |w - t| = {np.abs(err).max():.6f}")
 
 
 @pytest.mark.parametrize("variant,d", [("TEX_DECASTELJAU", d) for d in (1, 2, 3, 4, 5, 7)]
