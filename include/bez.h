@@ -201,6 +201,36 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
                           const bez_opts* opts, void* stream);
 
 /*
+ * bez_eval_spline_noalloc -- B-spline / NURBS evaluation that allocates no
+ * memory.  The paper has no counterpart; this is a deployment variant of
+ * bez_eval_bspline / bez_eval_nurbs.
+ *
+ * Those calls keep the Bezier spans they extract in a scratch buffer that
+ * the context grows with cudaMalloc.  Some callers cannot allow that: code
+ * that must never synchronise the device (cudaMalloc / cudaFree can), hosts
+ * whose memory manager owns all device memory, and plugins that may only use
+ * the buffers they are given.  This entry point runs the same kernels with
+ * the span scratch in a fixed 16 MiB array built into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *   weights NULL evaluates B-splines, non-NULL NURBS; other arguments as in
+ *   bez_eval_nurbs, with no context.  Every array must be device memory
+ *   (host arrays would need staging buffers): BEZ_ERR_INVALID_ARG otherwise.
+ *   The batch may need at most 4,194,304 span floats,
+ *   n_curves * (n_ctrl - degree) * (degree + 1) * (dim, or dim+1 for NURBS);
+ *   larger batches are rejected with BEZ_ERR_INVALID_ARG.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make it before any stream capture.  All calls share the
+ * array and each overwrites it, so calls that may overlap on the GPU
+ * (different streams without ordering between them) race.  Errors are
+ * reported through bez_last_error().
+ */
+bez_status bez_eval_spline_noalloc(const float* ctrl, const float* weights, const float* knots, int64_t n_curves,
+                                   int n_ctrl, int degree, int dim, const float* t, int64_t n_t, float* out,
+                                   const bez_opts* opts, void* stream);
+
+/*
  * bez_probe_filter -- characterise the texture unit's linear-filter weights.
  *
  * Paper Sec. 2.3: the hardware converts texture coordinates to a fixed-point

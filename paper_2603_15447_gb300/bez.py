@@ -102,10 +102,13 @@ def lib():
                                            ctypes.POINTER(Opts), _VP]
             L.bez_eval_nurbs.argtypes = [_VP, _VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
                                          ctypes.POINTER(Opts), _VP]
+            L.bez_eval_spline_noalloc.argtypes = [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
+                                                  ctypes.POINTER(Opts), _VP]
             L.bez_eval_piecewise.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts),
                                              _VP]
             for name in ("bez_create", "bez_destroy", "bez_set_timing", "bez_get_stats", "bez_reset_stats",
-                         "bez_eval", "bez_probe_filter", "bez_eval_piecewise", "bez_eval_bspline", "bez_eval_nurbs"):
+                         "bez_eval", "bez_probe_filter", "bez_eval_piecewise", "bez_eval_bspline", "bez_eval_nurbs",
+                         "bez_eval_spline_noalloc"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -312,3 +315,24 @@ def bez_eval_nurbs(ctrl, weights, degree, t=None, *, knots=None, n_t=None, out_m
     """NURBS ``ctrl`` [n_curves][n_ctrl][dim] with ``weights`` [n_curves][n_ctrl]."""
     return _spline_call(ctrl, degree, t, n_t, weights, knots, out_mode, t_mode, seed, stream_id, out, stream, sync,
                         ctx, err_word)
+
+
+def bez_eval_spline_noalloc(ctrl, degree, t=None, *, weights=None, knots=None, n_t=None, out_mode=OutMode.POINTS,
+                            t_mode=None, seed=0, stream_id=0, out=None, stream=None, sync=False):
+    """B-spline (weights None) or NURBS evaluation through the entry point
+    that allocates nothing: every tensor must be on the GPU, and ``out``
+    should be preallocated by callers that must not allocate either."""
+    n_curves, n_ctrl, dim = ctrl.shape
+    if t_mode is None:
+        t_mode = TMode.SHARED if (t is not None and t.ndim == 1) else TMode.PER_CURVE
+    if t is not None:
+        n_t = t.shape[-1]
+    assert n_t is not None, "n_t is required when t is None"
+    if out is None:
+        shape = (n_curves, n_t, dim) if out_mode == OutMode.POINTS else (n_curves,)
+        out = _empty_like_location(ctrl, shape)
+    dev = ctrl.device.index if _is_cuda(ctrl) else 0
+    o = _opts(Variant.AUTO, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
+    _check(lib().bez_eval_spline_noalloc(_ptr(ctrl), _ptr(weights), _ptr(knots), n_curves, n_ctrl, degree, dim,
+                                         _ptr(t), n_t, _ptr(out), ctypes.byref(o), _stream_handle(stream, dev)))
+    return out

@@ -46,6 +46,10 @@ static bez_status cuda_fail(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
     } while (0)
 
+namespace bez {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace bez
+
 // ---------------------------------------------------------------- context
 
 struct StageBuf {

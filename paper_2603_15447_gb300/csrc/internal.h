@@ -109,6 +109,9 @@ struct SplineArgs {
 LaunchResult launch_spline_setup(const SplineArgs& a, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_spline_eval(const SplineArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 
+// Message returned by bez_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Occupancy-sized persistent grid: a multiple of the SM count.
 int persistent_grid(const void* kernel, int block, size_t smem, int sm_count, int64_t work_blocks);
 
