@@ -201,6 +201,49 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
                           const bez_opts* opts, void* stream);
 
 /*
+ * bez_eval_surface / bez_eval_volume -- tensor-product Bezier surfaces and
+ * volumes on uniform parameter grids.
+ *
+ * Paper Sec. 2.2: a surface splits its order between u and v (a bicubic
+ * patch evaluates its four column curves at u, giving the control points of
+ * the isoline cubic in v); a volume splits it between u, v and w.  The
+ * kernels contract separably (columns at u, then v, then w) with Bernstein
+ * tables of the grid values fl32(a)/fl32(n-1), one block per patch, and
+ * write the output with coalesced (float4 where aligned) stores.
+ *
+ *   surface ctrl [n][du+1][dv+1][dim]        -> out [n][nu][nv][dim]
+ *   volume  ctrl [n][du+1][dv+1][dw+1][dim]  -> out [n][nu][nv][nw][dim]
+ *   degrees 1..7, grid sizes 1..256 per axis, dim 1..4; ctrl element type
+ *   opts->dtype (FP32, FP16 or BF16 storage, FP32 math); variant AUTO or
+ *   BERNSTEIN; out_mode POINTS; t_mode and t are not used.
+ */
+bez_status bez_eval_surface(bez_ctx ctx, const void* ctrl, int64_t n, int du, int dv, int dim, int nu, int nv,
+                            float* out, const bez_opts* opts, void* stream);
+bez_status bez_eval_volume(bez_ctx ctx, const void* ctrl, int64_t n, int du, int dv, int dw, int dim, int nu, int nv,
+                           int nw, float* out, const bez_opts* opts, void* stream);
+
+/*
+ * bez_eval_backward -- adjoint of (rational) Bezier curve evaluation.
+ *
+ * Differentiates C(t) = sum_i B_i(t) w_i P_i / sum_i B_i(t) w_i (w = 1 when
+ * weights is NULL; the rational form is Sec. 2.2's quotient of two integral
+ * curves) for an upstream gradient grad_out = dL/dC(t_j):
+ *   grad_ctrl[c][i]    = sum_j (w_i B_i(t_j) / W_j) grad_out[c][j]
+ *   grad_weights[c][i] = sum_j B_i(t_j) (P_i - C(t_j)) . grad_out[c][j] / W_j
+ *   grad_t[c][j]       = grad_out[c][j] . C'(t_j), 0 where t_j was clamped
+ *                        (shared t: summed over curves, grad_t [n_t])
+ *
+ *   ctrl [n_curves][degree+1][dim] FP32, weights [n_curves][degree+1] or NULL
+ *   t    SHARED [n_t] or PER_CURVE [n_curves][n_t] (opts->t_mode)
+ *   grad_out [n_curves][n_t][dim]
+ *   Outputs are overwritten; any of grad_ctrl, grad_weights, grad_t may be
+ *   NULL (grad_weights needs weights).  degree 1..15, dim 1..4.
+ */
+bez_status bez_eval_backward(bez_ctx ctx, const float* ctrl, const float* weights, int64_t n_curves, int degree,
+                             int dim, const float* t, int64_t n_t, const float* grad_out, float* grad_ctrl,
+                             float* grad_weights, float* grad_t, const bez_opts* opts, void* stream);
+
+/*
  * bez_eval_spline_noalloc -- B-spline / NURBS evaluation that allocates no
  * memory.  The paper has no counterpart; this is a deployment variant of
  * bez_eval_bspline / bez_eval_nurbs.

@@ -102,13 +102,20 @@ def lib():
                                            ctypes.POINTER(Opts), _VP]
             L.bez_eval_nurbs.argtypes = [_VP, _VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
                                          ctypes.POINTER(Opts), _VP]
+            L.bez_eval_surface.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _INT, _VP, ctypes.POINTER(Opts),
+                                           _VP]
+            L.bez_eval_volume.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _INT, _INT, _INT, _VP,
+                                          ctypes.POINTER(Opts), _VP]
+            L.bez_eval_backward.argtypes = [_VP, _VP, _VP, _I64, _INT, _INT, _VP, _I64, _VP, _VP, _VP, _VP,
+                                            ctypes.POINTER(Opts), _VP]
             L.bez_eval_spline_noalloc.argtypes = [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
                                                   ctypes.POINTER(Opts), _VP]
             L.bez_eval_piecewise.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts),
                                              _VP]
             for name in ("bez_create", "bez_destroy", "bez_set_timing", "bez_get_stats", "bez_reset_stats",
                          "bez_eval", "bez_probe_filter", "bez_eval_piecewise", "bez_eval_bspline", "bez_eval_nurbs",
-                         "bez_eval_spline_noalloc"):
+                         "bez_eval_spline_noalloc", "bez_eval_surface", "bez_eval_volume",
+                         "bez_eval_backward"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -336,3 +343,52 @@ def bez_eval_spline_noalloc(ctrl, degree, t=None, *, weights=None, knots=None, n
     _check(lib().bez_eval_spline_noalloc(_ptr(ctrl), _ptr(weights), _ptr(knots), n_curves, n_ctrl, degree, dim,
                                          _ptr(t), n_t, _ptr(out), ctypes.byref(o), _stream_handle(stream, dev)))
     return out
+
+
+def bez_eval_surface(ctrl, nu, nv, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None):
+    """Tensor-product surfaces ``ctrl`` [n][du+1][dv+1][dim] on an nu x nv
+    uniform grid -> [n][nu][nv][dim]."""
+    n, du1, dv1, dim = ctrl.shape
+    if out is None:
+        out = _empty_like_location(ctrl, (n, nu, nv, dim))
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync)
+    _check(lib().bez_eval_surface(c.handle, _ptr(ctrl), n, du1 - 1, dv1 - 1, dim, nu, nv, _ptr(out),
+                                  ctypes.byref(o), _stream_handle(stream, dev)))
+    return out
+
+
+def bez_eval_volume(ctrl, nu, nv, nw, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None):
+    """Tensor-product volumes ``ctrl`` [n][du+1][dv+1][dw+1][dim] on an
+    nu x nv x nw uniform grid -> [n][nu][nv][nw][dim]."""
+    n, du1, dv1, dw1, dim = ctrl.shape
+    if out is None:
+        out = _empty_like_location(ctrl, (n, nu, nv, nw, dim))
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync)
+    _check(lib().bez_eval_volume(c.handle, _ptr(ctrl), n, du1 - 1, dv1 - 1, dw1 - 1, dim, nu, nv, nw, _ptr(out),
+                                 ctypes.byref(o), _stream_handle(stream, dev)))
+    return out
+
+
+def bez_eval_backward(ctrl, t, grad_out, *, weights=None, need_ctrl=True, need_weights=None, need_t=True,
+                      stream=None, sync=False, ctx=None):
+    """Adjoint of Bezier (or rational Bezier) evaluation.  Returns
+    (grad_ctrl, grad_weights, grad_t); entries not requested are None."""
+    n_curves, d1, dim = ctrl.shape
+    n_t = t.shape[-1]
+    t_mode = TMode.SHARED if t.ndim == 1 else TMode.PER_CURVE
+    if need_weights is None:
+        need_weights = weights is not None
+    gc = _empty_like_location(ctrl, (n_curves, d1, dim)) if need_ctrl else None
+    gw = _empty_like_location(ctrl, (n_curves, d1)) if need_weights else None
+    gt = _empty_like_location(ctrl, tuple(t.shape)) if need_t else None
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    o = _opts(Variant.AUTO, _dtype_code(ctrl), OutMode.POINTS, t_mode, 0, 0, sync)
+    _check(lib().bez_eval_backward(c.handle, _ptr(ctrl), _ptr(weights), n_curves, d1 - 1, dim, _ptr(t), n_t,
+                                   _ptr(grad_out), _ptr(gc), _ptr(gw), _ptr(gt), ctypes.byref(o),
+                                   _stream_handle(stream, dev)))
+    return gc, gw, gt

@@ -67,7 +67,8 @@ struct bez_ctx_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> spare;
     cudaEvent_t cur_begin = nullptr;
-    StageBuf stage[8];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots (host staging); 5 spline spans (scratch)
+    StageBuf stage[8];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots / grad_out, 6-7 extra outputs (host staging);
+                        // 5 spline spans (scratch)
     TexState tex;
     cudaEvent_t tex_done = nullptr;  // last use of the texture atlases
     bool tex_used = false;
@@ -591,6 +592,132 @@ bez_status bez_eval_nurbs(bez_ctx c, const float* ctrl, const float* weights, co
                           const bez_opts* o, void* stream)
 {
     return eval_spline(c, ctrl, weights, knots, n_curves, n_ctrl, degree, dim, t, n_t, out, o, stream, true);
+}
+
+static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, int dv, int dw, int dim, int nu, int nv,
+                              int nw, float* out, const bez_opts* o, void* stream)
+{
+    bez_status st = check_common(c, o);
+    if (st != BEZ_OK) return st;
+    const bool vol = dw >= 0;
+    if (n < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
+    if (du < 1 || dv < 1 || (vol && dw < 1)) return fail(BEZ_ERR_INVALID_ARG, "degrees must be >= 1");
+    if (nu < 1 || nv < 1 || (vol && nw < 1)) return fail(BEZ_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (du > 7 || dv > 7 || dw > 7) return fail(BEZ_ERR_UNSUPPORTED, "tensor-product degrees above 7");
+    if (nu > 256 || nv > 256 || nw > 256) return fail(BEZ_ERR_UNSUPPORTED, "grids above 256 per axis");
+    if (o->out_mode != BEZ_OUT_POINTS) return fail(BEZ_ERR_UNSUPPORTED, "surfaces and volumes output points");
+    const int var = o->variant;
+    if (var != BEZ_VAR_AUTO && var != BEZ_VAR_BERNSTEIN)
+        return fail(BEZ_ERR_UNSUPPORTED,
+                    "variant %d: the store-bound grid contraction runs on CUDA cores (AUTO / BERNSTEIN)", var);
+    TensorLaunch t{};
+    t.dtype = o->dtype;
+    t.n = n;
+    t.du = du;
+    t.dv = dv;
+    t.dw = vol ? dw : -1;
+    t.dim = dim;
+    t.nu = nu;
+    t.nv = nv;
+    t.nw = vol ? nw : 1;
+    if (tensor_product_smem(t) > 200 * 1024) return fail(BEZ_ERR_UNSUPPORTED, "grid too large for one block");
+    if (n == 0) return BEZ_OK;
+    if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    const int64_t per = (int64_t)(du + 1) * (dv + 1) * (vol ? dw + 1 : 1) * dim;
+    st = stg.in(ctrl, (size_t)n * per * dtype_size(o->dtype), 0, &t.ctrl);
+    if (st != BEZ_OK) return st;
+    void* od = nullptr;
+    st = stg.out(out, (size_t)n * nu * nv * (vol ? nw : 1) * dim * sizeof(float), 2, &od);
+    if (st != BEZ_OK) return st;
+    t.out = static_cast<float*>(od);
+    LaunchResult r = launch_tensor_product(t, s, hooks_of(c));
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "tensor-product launch");
+    return stg.finish(o->sync);
+}
+
+bez_status bez_eval_surface(bez_ctx c, const void* ctrl, int64_t n, int du, int dv, int dim, int nu, int nv,
+                            float* out, const bez_opts* o, void* stream)
+{
+    return eval_tensor(c, ctrl, n, du, dv, -1, dim, nu, nv, 1, out, o, stream);
+}
+
+bez_status bez_eval_volume(bez_ctx c, const void* ctrl, int64_t n, int du, int dv, int dw, int dim, int nu, int nv,
+                           int nw, float* out, const bez_opts* o, void* stream)
+{
+    if (dw < 0) return fail(BEZ_ERR_INVALID_ARG, "degree %d < 1", dw);
+    return eval_tensor(c, ctrl, n, du, dv, dw, dim, nu, nv, nw, out, o, stream);
+}
+
+bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights, int64_t n_curves, int degree, int dim,
+                             const float* t, int64_t n_t, const float* grad_out, float* grad_ctrl,
+                             float* grad_weights, float* grad_t, const bez_opts* o, void* stream)
+{
+    bez_status st = check_common(c, o);
+    if (st != BEZ_OK) return st;
+    if (n_curves < 0 || n_t < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n_t > 0x7fffffff) return fail(BEZ_ERR_INVALID_ARG, "n_t %lld exceeds 2^31-1", (long long)n_t);
+    if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
+    if (degree < 1) return fail(BEZ_ERR_INVALID_ARG, "degree %d < 1", degree);
+    if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
+    if (o->dtype != BEZ_F32) return fail(BEZ_ERR_UNSUPPORTED, "the adjoint takes FP32 control points");
+    if (o->t_mode != BEZ_T_SHARED && o->t_mode != BEZ_T_PER_CURVE)
+        return fail(BEZ_ERR_UNSUPPORTED, "the adjoint needs the parameters as an array (SHARED / PER_CURVE)");
+    if (grad_weights && !weights) return fail(BEZ_ERR_INVALID_ARG, "grad_weights requested without weights");
+    if (n_curves == 0) return BEZ_OK;
+    if (!ctrl || (n_t > 0 && (!t || !grad_out))) return fail(BEZ_ERR_INVALID_ARG, "null ctrl, t or grad_out");
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    GradArgs a{};
+    const bool per_curve = o->t_mode == BEZ_T_PER_CURVE;
+    const void* p = nullptr;
+    st = stg.in(ctrl, (size_t)n_curves * (degree + 1) * dim * sizeof(float), 0, &p);
+    if (st != BEZ_OK) return st;
+    a.ctrl = static_cast<const float*>(p);
+    if (weights) {
+        st = stg.in(weights, (size_t)n_curves * (degree + 1) * sizeof(float), 3, &p);
+        if (st != BEZ_OK) return st;
+        a.weights = static_cast<const float*>(p);
+    }
+    st = stg.in(t, (size_t)n_t * sizeof(float) * (per_curve ? (size_t)n_curves : 1), 1, &p);
+    if (st != BEZ_OK) return st;
+    a.t = static_cast<const float*>(p);
+    st = stg.in(grad_out, (size_t)n_curves * n_t * dim * sizeof(float), 4, &p);
+    if (st != BEZ_OK) return st;
+    a.g = static_cast<const float*>(p);
+    void* od = nullptr;
+    if (grad_ctrl) {
+        st = stg.out(grad_ctrl, (size_t)n_curves * (degree + 1) * dim * sizeof(float), 2, &od);
+        if (st != BEZ_OK) return st;
+        a.grad_ctrl = static_cast<float*>(od);
+    }
+    if (grad_weights) {
+        st = stg.out(grad_weights, (size_t)n_curves * (degree + 1) * sizeof(float), 6, &od);
+        if (st != BEZ_OK) return st;
+        a.grad_w = static_cast<float*>(od);
+    }
+    if (grad_t) {
+        const size_t gb = (size_t)n_t * sizeof(float) * (per_curve ? (size_t)n_curves : 1);
+        st = stg.out(grad_t, gb, 7, &od);
+        if (st != BEZ_OK) return st;
+        a.grad_t = static_cast<float*>(od);
+        if (!per_curve) BEZ_CUDA(cudaMemsetAsync(a.grad_t, 0, gb, s), "cudaMemsetAsync");
+    }
+    a.n_curves = n_curves;
+    a.degree = degree;
+    a.dim = dim;
+    a.n_t = (int32_t)n_t;
+    a.t_stride = per_curve ? n_t : 0;
+    a.shared_gt = (!per_curve && n_t <= 8192) ? 1 : 0;
+    LaunchResult r = launch_grad(a, s, hooks_of(c));
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "adjoint launch");
+    return stg.finish(o->sync);
 }
 
 bez_status bez_probe_filter(bez_ctx c, const float* xyz, int64_t n, float* out, void* stream)

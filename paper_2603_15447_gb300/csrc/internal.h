@@ -109,6 +109,39 @@ struct SplineArgs {
 LaunchResult launch_spline_setup(const SplineArgs& a, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_spline_eval(const SplineArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 
+// ---------------------------------------------------------------- surfaces / volumes
+
+struct TensorArgs;
+struct TensorLaunch {
+    const void* ctrl;
+    int32_t dtype;
+    int64_t n;
+    int32_t du, dv, dw;  // dw < 0: surface
+    int32_t dim;
+    int32_t nu, nv, nw;
+    float* out;
+};
+LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const LaunchHooks& h);
+size_t tensor_product_smem(const TensorLaunch& t);
+
+// ---------------------------------------------------------------- adjoint
+
+struct GradArgs {
+    const float* ctrl;     // [n][d+1][dim]
+    const float* weights;  // [n][d+1] or NULL
+    int64_t n_curves;
+    int32_t degree, dim, n_t;
+    const float* t;        // t[c * t_stride + j]
+    int64_t t_stride;
+    const float* g;        // [n][n_t][dim]
+    float* grad_ctrl;      // [n][d+1][dim] or NULL
+    float* grad_w;         // [n][d+1] or NULL
+    float* grad_t;         // [n][n_t] (per-curve t) or [n_t] (shared t) or NULL
+    int32_t shared_gt;     // shared-t sums staged in shared memory (n_t small enough)
+};
+
+LaunchResult launch_grad(const GradArgs& a, cudaStream_t s, const LaunchHooks& h);
+
 // Message returned by bez_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
