@@ -223,6 +223,70 @@ bez_status bez_eval_volume(bez_ctx ctx, const void* ctrl, int64_t n, int du, int
                            int nw, float* out, const bez_opts* opts, void* stream);
 
 /*
+ * Mixed batches -- curves of different type, degree and sample count in one
+ * persistent launch (the batching pattern the paper's evaluators need when a
+ * scene mixes curve kinds; the curve types are those of Sec. 2.2).
+ *
+ * Each curve has a descriptor.  Control points of curve c are
+ * ctrl_pool[ctrl_off .. ctrl_off + n_ctrl*dim); NURBS weights
+ * weight_pool[weight_off .. + n_ctrl); its points go to
+ * out_pool[out_off .. out_off + n_samples*dim), evaluated at
+ * t_j = fl32(j) / fl32(n_samples - 1) over the curve's domain [0, 1].
+ *   BEZ_CURVE_BEZIER  n_ctrl == degree + 1
+ *   BEZ_CURVE_BSPLINE clamped uniform knots, n_ctrl >= degree + 1
+ *   BEZ_CURVE_NURBS   clamped uniform knots and weights
+ *   degree 1..7, dim 1..4; pools are FP32 device arrays of the stated
+ *   lengths (in floats); descriptors are host or device arrays.
+ *
+ * bez_batch_create validates every descriptor on the host (offsets against
+ * the pool lengths), builds the work-item table (curve, chunk of samples),
+ * allocates the plan's device buffers (descriptors, items, the FP64-extracted
+ * Bezier span pool of the splines), optionally autotunes chunk size,
+ * scheduler (static round-robin or atomic work queue) and block size by
+ * timing candidates on the real batch (results cached in memory and, when
+ * the environment variable BEZ_AUTOTUNE_CACHE names a file, in that JSON
+ * file), and captures span setup + evaluation in a CUDA graph.
+ * bez_batch_launch replays it on `stream`; with setup_each_launch = 0 the
+ * spans are extracted once at creation (control points must then not
+ * change).  bez_eval_batch is create + launch + destroy without graph or
+ * tuning, synchronous on `stream`.
+ */
+typedef enum bez_curve_type { BEZ_CURVE_BEZIER = 0, BEZ_CURVE_BSPLINE = 1, BEZ_CURVE_NURBS = 2 } bez_curve_type;
+
+typedef struct bez_curve_desc {
+    int32_t type;       /* bez_curve_type */
+    int32_t degree;
+    int32_t n_ctrl;
+    int32_t n_samples;
+    int64_t ctrl_off;   /* floats into ctrl_pool   */
+    int64_t weight_off; /* floats into weight_pool */
+    int64_t out_off;    /* floats into out_pool    */
+} bez_curve_desc;
+
+typedef struct bez_batch_opts {
+    int32_t autotune;          /* time candidate launch shapes at creation      */
+    int32_t setup_each_launch; /* re-extract spline spans on every launch        */
+    int32_t use_graph;         /* capture setup + evaluation in a CUDA graph     */
+    int32_t chunk;             /* samples per work item, 0 = default / tuned     */
+    int32_t schedule;          /* -1 default / tuned, 0 static, 1 atomic queue   */
+    int32_t threads;           /* threads per block, 0 = default / tuned         */
+} bez_batch_opts;
+
+typedef struct bez_batch_s* bez_batch;
+
+bez_status bez_batch_create(bez_ctx ctx, const bez_curve_desc* desc, int64_t n_curves, int dim,
+                            const float* ctrl_pool, int64_t ctrl_len, const float* weight_pool, int64_t weight_len,
+                            float* out_pool, int64_t out_len, const bez_batch_opts* bopts, void* stream,
+                            bez_batch* batch);
+bez_status bez_batch_launch(bez_batch batch, void* stream);
+/* chosen launch shape: chunk, schedule (0 static, 1 atomic), threads */
+bez_status bez_batch_config(bez_batch batch, int32_t* chunk, int32_t* schedule, int32_t* threads);
+bez_status bez_batch_destroy(bez_batch batch);
+bez_status bez_eval_batch(bez_ctx ctx, const bez_curve_desc* desc, int64_t n_curves, int dim, const float* ctrl_pool,
+                          int64_t ctrl_len, const float* weight_pool, int64_t weight_len, float* out_pool,
+                          int64_t out_len, void* stream);
+
+/*
  * bez_eval_backward -- adjoint of (rational) Bezier curve evaluation.
  *
  * Differentiates C(t) = sum_i B_i(t) w_i P_i / sum_i B_i(t) w_i (w = 1 when

@@ -392,3 +392,92 @@ def bez_eval_backward(ctrl, t, grad_out, *, weights=None, need_ctrl=True, need_w
                                    _ptr(grad_out), _ptr(gc), _ptr(gw), _ptr(gt), ctypes.byref(o),
                                    _stream_handle(stream, dev)))
     return gc, gw, gt
+
+
+# ---------------------------------------------------------------- mixed batches
+
+DESC_DTYPE = np.dtype([("type", "<i4"), ("degree", "<i4"), ("n_ctrl", "<i4"), ("n_samples", "<i4"),
+                       ("ctrl_off", "<i8"), ("weight_off", "<i8"), ("out_off", "<i8")])
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int32), ("setup_each_launch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("schedule", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+def descriptors(type, degree, n_ctrl, n_samples, ctrl_off, weight_off, out_off):
+    """Pack per-curve arrays into the C descriptor layout (NumPy, host)."""
+    d = np.zeros(len(type), DESC_DTYPE)
+    d["type"], d["degree"], d["n_ctrl"], d["n_samples"] = type, degree, n_ctrl, n_samples
+    d["ctrl_off"], d["weight_off"], d["out_off"] = ctrl_off, weight_off, out_off
+    return d
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.bez_batch_create.argtypes = [_VP, _VP, _I64, _INT, _VP, _I64, _VP, _I64, _VP, _I64,
+                                       ctypes.POINTER(BatchOpts), _VP, ctypes.POINTER(_VP)]
+        L.bez_batch_launch.argtypes = [_VP, _VP]
+        L.bez_batch_config.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]
+        L.bez_batch_destroy.argtypes = [_VP]
+        L.bez_eval_batch.argtypes = [_VP, _VP, _I64, _INT, _VP, _I64, _VP, _I64, _VP, _I64, _VP]
+        for n in ("bez_batch_create", "bez_batch_launch", "bez_batch_config", "bez_batch_destroy", "bez_eval_batch"):
+            getattr(L, n).restype = ctypes.c_int
+        L._batch_ready = True
+    return L
+
+
+def _numel(x):
+    return 0 if x is None else int(x.numel() if not isinstance(x, np.ndarray) else x.size)
+
+
+class Batch:
+    """A mixed-batch plan (bez_batch_create); ``launch()`` replays it."""
+
+    def __init__(self, desc, dim, ctrl_pool, weight_pool, out_pool, *, autotune=False, setup_each_launch=True,
+                 use_graph=True, chunk=0, schedule=-1, threads=0, stream=None, ctx=None):
+        L = _batch_lib()
+        desc = np.ascontiguousarray(desc, dtype=DESC_DTYPE)
+        self.dev = ctrl_pool.device.index
+        self.ctx = ctx or context(self.dev)
+        self._keep = (ctrl_pool, weight_pool, out_pool)
+        bo = BatchOpts(int(autotune), int(setup_each_launch), int(use_graph), chunk, schedule, threads)
+        h = _VP()
+        _check(L.bez_batch_create(self.ctx.handle, desc.ctypes.data, len(desc), dim, _ptr(ctrl_pool),
+                                  _numel(ctrl_pool), _ptr(weight_pool), _numel(weight_pool), _ptr(out_pool),
+                                  _numel(out_pool), ctypes.byref(bo), _stream_handle(stream, self.dev),
+                                  ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(_batch_lib().bez_batch_launch(self.handle, _stream_handle(stream, self.dev)))
+
+    def config(self):
+        c, s, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_batch_lib().bez_batch_config(self.handle, ctypes.byref(c), ctypes.byref(s), ctypes.byref(t)))
+        return {"chunk": c.value, "schedule": s.value, "threads": t.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _batch_lib().bez_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bez_eval_batch(desc, dim, ctrl_pool, weight_pool, out_pool, *, stream=None, ctx=None):
+    """One-shot mixed batch (no graph, no tuning), synchronous on the stream."""
+    L = _batch_lib()
+    desc = np.ascontiguousarray(desc, dtype=DESC_DTYPE)
+    dev = ctrl_pool.device.index
+    c = ctx or context(dev)
+    _check(L.bez_eval_batch(c.handle, desc.ctypes.data, len(desc), dim, _ptr(ctrl_pool), _numel(ctrl_pool),
+                            _ptr(weight_pool), _numel(weight_pool), _ptr(out_pool), _numel(out_pool),
+                            _stream_handle(stream, dev)))
+    return out_pool

@@ -8,11 +8,13 @@
 #include <cstring>
 #include <mutex>
 #include <string>
-#include <unordered_map>
+#include <map>
+#include <tuple>
 #include <utility>
 #include <vector>
 
 #include "../../include/bez.h"
+#include "context.h"
 #include "internal.h"
 
 using namespace bez;
@@ -23,7 +25,7 @@ using namespace bez;
 
 static thread_local std::string g_last_error;
 
-static bez_status fail(bez_status st, const char* fmt, ...)
+bez_status bez::fail(bez_status st, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -34,46 +36,17 @@ static bez_status fail(bez_status st, const char* fmt, ...)
     return st;
 }
 
-static bez_status cuda_fail(cudaError_t e, const char* what)
+bez_status bez::cuda_fail(cudaError_t e, const char* what)
 {
     if (e == cudaErrorMemoryAllocation) return fail(BEZ_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
     return fail(BEZ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-#define BEZ_CUDA(call, what)                                  \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
-    } while (0)
 
 namespace bez {
 void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace bez
 
 // ---------------------------------------------------------------- context
-
-struct StageBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-};
-
-struct bez_ctx_s {
-    int device = 0;
-    int sm_count = 0;
-    bool timing = false;
-    int64_t launches = 0;
-    int64_t timed_launches = 0;
-    double timed_ms = 0.0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
-    std::vector<cudaEvent_t> spare;
-    cudaEvent_t cur_begin = nullptr;
-    StageBuf stage[8];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots / grad_out, 6-7 extra outputs (host staging);
-                        // 5 spline spans (scratch)
-    TexState tex;
-    cudaEvent_t tex_done = nullptr;  // last use of the texture atlases
-    bool tex_used = false;
-    std::mutex mu;
-};
 
 namespace {
 
@@ -109,11 +82,11 @@ void hook_end(void* self, cudaStream_t s)
     c->cur_begin = nullptr;
 }
 
-LaunchHooks hooks_of(bez_ctx c) { return LaunchHooks{hook_count, hook_begin, hook_end, c, c->sm_count}; }
+}  // namespace
 
-enum MemKind { MEM_NULL, MEM_DEVICE, MEM_HOST };
+LaunchHooks bez::hooks_of(bez_ctx c) { return LaunchHooks{hook_count, hook_begin, hook_end, c, c->sm_count}; }
 
-MemKind classify(const void* p)
+bez::MemKind bez::classify(const void* p)
 {
     if (!p) return MEM_NULL;
     cudaPointerAttributes at;
@@ -124,6 +97,8 @@ MemKind classify(const void* p)
     }
     return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? MEM_DEVICE : MEM_HOST;
 }
+
+namespace {
 
 bez_status ensure_stage(bez_ctx c, int slot, size_t bytes, cudaStream_t s)
 {
@@ -223,11 +198,12 @@ namespace bez {
 int persistent_grid(const void* kernel, int block, size_t smem, int sm_count, int64_t work_blocks)
 {
     static std::mutex mu;
-    static std::unordered_map<const void*, int> cache;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    const auto key = std::make_tuple(kernel, block, smem);
     int per_sm = 0;
     {
         std::lock_guard<std::mutex> g(mu);
-        auto it = cache.find(kernel);
+        auto it = cache.find(key);
         if (it != cache.end()) per_sm = it->second;
     }
     if (per_sm == 0) {
@@ -236,7 +212,7 @@ int persistent_grid(const void* kernel, int block, size_t smem, int sm_count, in
             per_sm = 1;
         }
         std::lock_guard<std::mutex> g(mu);
-        cache[kernel] = per_sm;
+        cache[key] = per_sm;
     }
     int64_t full = (int64_t)per_sm * sm_count;
     if (work_blocks < 1) work_blocks = 1;

@@ -1,0 +1,429 @@
+// batch_plan.cu -- host side of mixed batches: descriptor validation, work
+// items, plan-owned device buffers, the autotuner and CUDA-graph capture.
+// Kernels are in batch.cu; the ABI is declared in include/bez.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "context.h"
+
+using namespace bez;
+
+namespace {
+
+struct Shape {
+    int chunk = 512;
+    int schedule = 0;
+    int threads = 256;
+};
+
+void no_count(void*) {}
+void no_event(void*, cudaStream_t) {}
+
+std::mutex g_tune_mu;
+std::map<std::string, Shape> g_tune_cache;
+
+// ---- the JSON autotune cache: {"key": {"chunk": c, "schedule": s, "threads": t}, ...}
+
+void load_cache_file(const char* path)
+{
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    std::string s;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, n);
+    fclose(f);
+    size_t pos = 0;
+    for (;;) {
+        const size_t k0 = s.find('"', pos);
+        if (k0 == std::string::npos) break;
+        const size_t k1 = s.find('"', k0 + 1);
+        if (k1 == std::string::npos) break;
+        const std::string key = s.substr(k0 + 1, k1 - k0 - 1);
+        const size_t b0 = s.find('{', k1), b1 = s.find('}', k1);
+        if (b0 == std::string::npos || b1 == std::string::npos || b0 > b1) {
+            pos = k1 + 1;
+            continue;
+        }
+        const std::string body = s.substr(b0, b1 - b0);
+        Shape sh;
+        auto field = [&](const char* name, int* out) {
+            const size_t p = body.find(name);
+            if (p != std::string::npos) *out = atoi(body.c_str() + body.find(':', p) + 1);
+        };
+        field("\"chunk\"", &sh.chunk);
+        field("\"schedule\"", &sh.schedule);
+        field("\"threads\"", &sh.threads);
+        if (sh.chunk > 0 && (sh.schedule == 0 || sh.schedule == 1) && (sh.threads == 128 || sh.threads == 256))
+            g_tune_cache[key] = sh;
+        pos = b1 + 1;
+    }
+}
+
+void save_cache_file(const char* path)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (auto& kv : g_tune_cache) {
+        fprintf(f, "  \"%s\": {\"chunk\": %d, \"schedule\": %d, \"threads\": %d}%s\n", kv.first.c_str(),
+                kv.second.chunk, kv.second.schedule, kv.second.threads, ++i < g_tune_cache.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+int log2_bucket(double x) { return x < 1 ? 0 : (int)std::lround(std::log2(x)); }
+
+}  // namespace
+
+struct bez_batch_s {
+    bez_ctx ctx = nullptr;
+    BatchArgs a{};
+    std::vector<bez_curve_desc> hdesc;
+    bez_curve_desc* d_desc = nullptr;
+    int64_t* d_span_off = nullptr;
+    int64_t* d_spline_ids = nullptr;
+    int2* d_items = nullptr;
+    size_t items_cap = 0;
+    float* d_spans = nullptr;
+    void* d_counter = nullptr;
+    Shape shape;
+    bool setup_each = true;
+    bool use_graph = false;
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_launch = 0;
+    std::string key;
+};
+
+namespace {
+
+bez_status build_items(bez_batch b, int chunk, cudaStream_t s)
+{
+    std::vector<int2> items;
+    for (size_t c = 0; c < b->hdesc.size(); ++c) {
+        const int n = b->hdesc[c].n_samples;
+        for (int k = 0; (int64_t)k * chunk < n; ++k) items.push_back(make_int2((int)c, k));
+    }
+    if (items.size() > b->items_cap) {
+        if (b->d_items) {
+            cudaError_t e = cudaStreamSynchronize(s);  // the old table may still be read
+            if (e != cudaSuccess) return cuda_fail(e, "batch items resize");
+            cudaFree(b->d_items);
+            b->d_items = nullptr;
+        }
+        cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(int2));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc batch items");
+        b->items_cap = items.size();
+    }
+    if (!items.empty()) {
+        cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy batch items");
+        e = cudaStreamSynchronize(s);  // `items` is a host temporary
+        if (e != cudaSuccess) return cuda_fail(e, "copy batch items");
+    }
+    b->a.items = b->d_items;
+    b->a.n_items = (int64_t)items.size();
+    b->a.chunk = chunk;
+    return BEZ_OK;
+}
+
+bez_status apply_shape(bez_batch b, const Shape& sh, cudaStream_t s)
+{
+    if (b->a.chunk != sh.chunk || !b->a.items) {
+        bez_status st = build_items(b, sh.chunk, s);
+        if (st != BEZ_OK) return st;
+    }
+    b->a.schedule = sh.schedule;
+    b->a.grab = 4;
+    b->shape = sh;
+    return BEZ_OK;
+}
+
+// time the evaluator (no setup) for one shape: median of 3 after a warm-up
+bez_status time_shape(bez_batch b, const Shape& sh, cudaStream_t s, float* ms_out)
+{
+    bez_status st = apply_shape(b, sh, s);
+    if (st != BEZ_OK) return st;
+    const LaunchHooks h{no_count, no_event, no_event, nullptr, b->ctx->sm_count};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float t[3];
+    int k = 0;
+    cudaError_t e = launch_batch(b->a, sh.threads, b->ctx->sm_count, false, s, h, &k);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+        cudaEventRecord(e0, s);
+        e = launch_batch(b->a, sh.threads, b->ctx->sm_count, false, s, h, &k);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+    std::sort(t, t + 3);
+    *ms_out = t[1];
+    return BEZ_OK;
+}
+
+bez_status autotune(bez_batch b, cudaStream_t s)
+{
+    const char* path = getenv("BEZ_AUTOTUNE_CACHE");
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        if (path) load_cache_file(path);
+        auto it = g_tune_cache.find(b->key);
+        if (it != g_tune_cache.end()) return apply_shape(b, it->second, s);
+    }
+    Shape best;
+    float best_ms = 1e30f;
+    for (int chunk : {256, 512, 1024, 2048})
+        for (int sched : {0, 1})
+            for (int threads : {128, 256}) {
+                Shape sh{chunk, sched, threads};
+                float ms = 0.f;
+                bez_status st = time_shape(b, sh, s, &ms);
+                if (st != BEZ_OK) return st;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = sh;
+                }
+            }
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[b->key] = best;
+        if (path) save_cache_file(path);
+    }
+    return apply_shape(b, best, s);
+}
+
+void free_batch(bez_batch b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_span_off);
+    cudaFree(b->d_spline_ids);
+    cudaFree(b->d_items);
+    cudaFree(b->d_spans);
+    cudaFree(b->d_counter);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_curves, int dim, const float* ctrl_pool,
+                            int64_t ctrl_len, const float* weight_pool, int64_t weight_len, float* out_pool,
+                            int64_t out_len, const bez_batch_opts* bo, void* stream, bez_batch* out)
+{
+    if (!out) return fail(BEZ_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
+    if (n_curves < 0 || ctrl_len < 0 || weight_len < 0 || out_len < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n_curves > 0x7fffffff) return fail(BEZ_ERR_INVALID_ARG, "more than 2^31-1 curves");
+    if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
+    if (n_curves > 0 && !desc) return fail(BEZ_ERR_INVALID_ARG, "null descriptors");
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((ctrl_len > 0 && classify(ctrl_pool) != MEM_DEVICE) || (out_len > 0 && classify(out_pool) != MEM_DEVICE) ||
+        (weight_len > 0 && classify(weight_pool) != MEM_DEVICE))
+        return fail(BEZ_ERR_INVALID_ARG, "batch pools must be device arrays");
+    bez_batch b = new bez_batch_s();
+    b->ctx = c;
+    b->hdesc.resize((size_t)n_curves);
+    if (n_curves > 0) {
+        const cudaMemcpyKind kind = classify(desc) == MEM_DEVICE ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        cudaError_t e = cudaMemcpy(b->hdesc.data(), desc, (size_t)n_curves * sizeof(bez_curve_desc), kind);
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "copy descriptors");
+        }
+    }
+    // validate every descriptor against the pools
+    std::vector<int64_t> span_off((size_t)n_curves, 0);
+    std::vector<int64_t> spline_ids;
+    int64_t spans = 0, total_samples = 0, n_type[3] = {0, 0, 0}, deg_sum = 0;
+    for (int64_t i = 0; i < n_curves; ++i) {
+        const bez_curve_desc& d = b->hdesc[(size_t)i];
+        const char* why = nullptr;
+        if (d.type < BEZ_CURVE_BEZIER || d.type > BEZ_CURVE_NURBS) why = "unknown curve type";
+        else if (d.degree < 1 || d.degree > 7) why = "degree outside 1..7";
+        else if (d.type == BEZ_CURVE_BEZIER && d.n_ctrl != d.degree + 1) why = "a Bezier curve has degree+1 points";
+        else if (d.n_ctrl < d.degree + 1) why = "fewer than degree+1 control points";
+        else if (d.n_samples < 0) why = "negative sample count";
+        else if (d.ctrl_off < 0 || d.ctrl_off + (int64_t)d.n_ctrl * dim > ctrl_len) why = "control points outside ctrl_pool";
+        else if (d.out_off < 0 || d.out_off + (int64_t)d.n_samples * dim > out_len) why = "samples outside out_pool";
+        else if (d.type == BEZ_CURVE_NURBS && (!weight_pool || d.weight_off < 0 || d.weight_off + d.n_ctrl > weight_len))
+            why = "weights outside weight_pool";
+        if (why) {
+            delete b;
+            return fail(BEZ_ERR_INVALID_ARG, "curve %lld: %s", (long long)i, why);
+        }
+        n_type[d.type] += 1;
+        deg_sum += d.degree;
+        total_samples += d.n_samples;
+        if (d.type != BEZ_CURVE_BEZIER) {
+            const int comps = d.type == BEZ_CURVE_NURBS ? dim + 1 : dim;
+            span_off[(size_t)i] = spans;
+            spans += (int64_t)(d.n_ctrl - d.degree) * (d.degree + 1) * comps;
+            spline_ids.push_back(i);
+        }
+    }
+    // plan-owned device buffers
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    };
+    alloc((void**)&b->d_desc, (size_t)n_curves * sizeof(bez_curve_desc));
+    alloc((void**)&b->d_span_off, (size_t)n_curves * sizeof(int64_t));
+    alloc((void**)&b->d_spline_ids, spline_ids.size() * sizeof(int64_t));
+    alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
+    alloc(&b->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess && n_curves > 0)
+        e = cudaMemcpy(b->d_desc, b->hdesc.data(), (size_t)n_curves * sizeof(bez_curve_desc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_curves > 0)
+        e = cudaMemcpy(b->d_span_off, span_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !spline_ids.empty())
+        e = cudaMemcpy(b->d_spline_ids, spline_ids.data(), spline_ids.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "batch buffers");
+    }
+    BatchArgs& a = b->a;
+    a.desc = b->d_desc;
+    a.n_curves = n_curves;
+    a.dim = dim;
+    a.ctrl_pool = ctrl_pool;
+    a.weight_pool = weight_pool;
+    a.out_pool = out_pool;
+    a.span_pool = b->d_spans;
+    a.span_off = b->d_span_off;
+    a.spline_ids = b->d_spline_ids;
+    a.n_splines = (int64_t)spline_ids.size();
+    a.counter = b->d_counter;
+    b->setup_each = bo ? bo->setup_each_launch != 0 : true;
+    b->use_graph = bo ? bo->use_graph != 0 : false;
+    char key[160];
+    snprintf(key, sizeof(key), "batch-v1:n%d:dim%d:mix%lld/%lld/%lld:deg%d:s%d", log2_bucket((double)n_curves), dim,
+             (long long)(n_curves ? 100 * n_type[0] / n_curves : 0), (long long)(n_curves ? 100 * n_type[1] / n_curves : 0),
+             (long long)(n_curves ? 100 * n_type[2] / n_curves : 0), n_curves ? (int)std::lround((double)deg_sum / n_curves) : 0,
+             log2_bucket(n_curves ? (double)total_samples / n_curves : 0.0));
+    b->key = key;
+    // launch shape: explicit, tuned or default
+    Shape sh;
+    if (bo && bo->chunk > 0) sh.chunk = bo->chunk;
+    if (bo && (bo->schedule == 0 || bo->schedule == 1)) sh.schedule = bo->schedule;
+    if (bo && (bo->threads == 128 || bo->threads == 256)) sh.threads = bo->threads;
+    if (bo && bo->threads != 0 && bo->threads != 128 && bo->threads != 256) {
+        free_batch(b);
+        return fail(BEZ_ERR_INVALID_ARG, "threads must be 128 or 256");
+    }
+    bez_status st = BEZ_OK;
+    // spans must exist before the evaluator runs (autotuning included)
+    if (a.n_splines > 0) {
+        const LaunchHooks h0{no_count, no_event, no_event, nullptr, c->sm_count};
+        int k = 0;
+        st = apply_shape(b, sh, s);
+        if (st == BEZ_OK) {
+            e = launch_batch(a, sh.threads, c->sm_count, true, s, h0, &k);
+            if (e != cudaSuccess) st = cuda_fail(e, "batch setup");
+        }
+    }
+    if (st == BEZ_OK) st = (bo && bo->autotune) ? autotune(b, s) : apply_shape(b, sh, s);
+    if (st == BEZ_OK && b->use_graph) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const LaunchHooks h0{no_count, no_event, no_event, nullptr, c->sm_count};
+            int k = 0;
+            cudaError_t le = launch_batch(a, b->shape.threads, c->sm_count, b->setup_each, cs, h0, &k);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (le != cudaSuccess) e = le;
+            b->kernels_per_launch = k;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch graph capture");
+    }
+    if (st != BEZ_OK) {
+        cudaStreamSynchronize(s);
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return BEZ_OK;
+}
+
+bez_status bez_batch_launch(bez_batch b, void* stream)
+{
+    if (!b) return fail(BEZ_ERR_INVALID_ARG, "null batch");
+    bez_ctx c = b->ctx;
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LaunchHooks h = hooks_of(c);
+    if (b->exec) {
+        for (int i = 0; i < b->kernels_per_launch; ++i) h.count(h.self);
+        h.begin(h.self, s);
+        cudaError_t e = cudaGraphLaunch(b->exec, s);
+        h.end(h.self, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        return BEZ_OK;
+    }
+    int k = 0;
+    cudaError_t e = launch_batch(b->a, b->shape.threads, c->sm_count, b->setup_each, s, h, &k);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return BEZ_OK;
+}
+
+bez_status bez_batch_config(bez_batch b, int32_t* chunk, int32_t* schedule, int32_t* threads)
+{
+    if (!b) return fail(BEZ_ERR_INVALID_ARG, "null batch");
+    if (chunk) *chunk = b->shape.chunk;
+    if (schedule) *schedule = b->shape.schedule;
+    if (threads) *threads = b->shape.threads;
+    return BEZ_OK;
+}
+
+bez_status bez_batch_destroy(bez_batch b)
+{
+    if (!b) return BEZ_OK;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return BEZ_OK;
+}
+
+bez_status bez_eval_batch(bez_ctx c, const bez_curve_desc* desc, int64_t n_curves, int dim, const float* ctrl_pool,
+                          int64_t ctrl_len, const float* weight_pool, int64_t weight_len, float* out_pool,
+                          int64_t out_len, void* stream)
+{
+    bez_batch_opts bo{0, 1, 0, 0, -1, 0};
+    bez_batch b = nullptr;
+    bez_status st = bez_batch_create(c, desc, n_curves, dim, ctrl_pool, ctrl_len, weight_pool, weight_len, out_pool,
+                                     out_len, &bo, stream, &b);
+    if (st != BEZ_OK) return st;
+    st = bez_batch_launch(b, stream);
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    bez_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"

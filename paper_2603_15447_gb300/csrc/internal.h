@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/bez.h"
+
 namespace bez {
 
 // Arguments of the register curve evaluators (one warp per curve).
@@ -141,6 +143,29 @@ struct GradArgs {
 };
 
 LaunchResult launch_grad(const GradArgs& a, cudaStream_t s, const LaunchHooks& h);
+
+// ---------------------------------------------------------------- mixed batches
+
+struct BatchArgs {
+    const bez_curve_desc* desc;  // device copy
+    int64_t n_curves;
+    int32_t dim;
+    const float* ctrl_pool;
+    const float* weight_pool;
+    float* out_pool;
+    float* span_pool;            // Bezier spans of the spline curves
+    const int64_t* span_off;     // per curve, floats into span_pool
+    const int64_t* spline_ids;   // indices of the spline curves
+    int64_t n_splines;
+    const int2* items;           // (curve, chunk index)
+    int64_t n_items;
+    int32_t chunk;
+    int32_t schedule;            // 0 static round-robin, 1 atomic queue
+    int32_t grab;                // items taken per atomic
+    void* counter;               // 8-byte work counter (atomic schedule)
+};
+cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
+                         const LaunchHooks& h, int* launches);
 
 // Message returned by bez_last_error() on the calling thread.
 void set_last_error(const char* msg);

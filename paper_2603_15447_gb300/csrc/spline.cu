@@ -49,11 +49,7 @@ __device__ __forceinline__ int spline_span(const SplineArgs& a, int64_t c, float
 {
     const int ns = a.n_spans;
     if (!a.knots) {
-        const float x = t * (float)ns;
-        int s = (int)floorf(x);
-        s = s < 0 ? 0 : (s > ns - 1 ? ns - 1 : s);
-        tau = fmaf(t, (float)ns, -(float)s);  // t*ns - s rounded once, not twice
-        return s;
+        return uniform_span(t, ns, tau);
     }
     const float* B = a.knots + c * (int64_t)(a.n_ctrl + a.degree + 1) + a.degree;  // breakpoints B[0..ns]
     int lo = 0, hi = ns;  // count of B[i] <= t over i < ns, by bisection

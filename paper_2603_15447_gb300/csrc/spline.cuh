@@ -19,7 +19,7 @@
 //
 // Evaluation: t is clamped to [U_p, U_n]; the span is the last non-empty one
 // with U_k <= t (an interior knot starts the later span); tau = (t - a) /
-// (b - a) (clamped uniform knots: k = floor(fl(t * n_spans)), tau = fma(t, n_spans, -k));
+// (b - a) (clamped uniform knots: see uniform_span);
 // the span's Bezier points go through FP32 de Casteljau, and rational points
 // are divided by their weight.
 #pragma once
@@ -76,6 +76,29 @@ __device__ inline void extract_span(const float* ctrl, const float* w, const flo
         }
     for (int i = 0; i <= p; ++i)
         for (int q = 0; q < comps; ++q) q_out[i * comps + q] = (float)Q[i][q];
+}
+
+// Span of t on the clamped uniform knots k / ns: the largest k with
+// t * ns >= k exactly.  fl(t * ns) can round across an integer when t lies
+// within an ulp of a knot, which would evaluate the neighbouring span just
+// outside its interval (a first-order error at the kinks of degree-1
+// splines); the residual fma(t, ns, -k) has the exact sign of t * ns - k, so
+// it corrects k, and the same residual is tau, rounded once.
+__device__ __forceinline__ int uniform_span(float t, int ns, float& tau)
+{
+    const float fn = (float)ns;
+    int s = (int)floorf(t * fn);
+    s = s < 0 ? 0 : (s > ns - 1 ? ns - 1 : s);
+    float r = fmaf(t, fn, -(float)s);
+    if (r < 0.f && s > 0) {
+        --s;
+        r = fmaf(t, fn, -(float)s);
+    } else if (r >= 1.f && s < ns - 1) {
+        ++s;
+        r = fmaf(t, fn, -(float)s);
+    }
+    tau = r;
+    return s;
 }
 
 // FP32 de Casteljau on one span's Bezier points (compile-time degree P and

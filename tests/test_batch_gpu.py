@@ -1,0 +1,141 @@
+"""GPU parity of mixed batches (bez_batch_*, bez_eval_batch): Bezier curves,
+clamped uniform B-splines and NURBS of degrees 1..7 with log-uniform sample
+counts, evaluated in one persistent launch (graph-captured, autotuned) and
+compared curve by curve with the oracle at the FP32 bar."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import need_gpu, normalised_error
+
+pytestmark = pytest.mark.gpu
+FP32_BAR = 1e-6
+
+
+def _reference(w):
+    """Oracle points of every curve of a synth.batch workload, as one flat
+    array laid out like out_pool."""
+    dim = w["dim"]
+    out = np.zeros(w["out_len"], np.float64)
+    groups = {}
+    for c in range(len(w["type"])):
+        groups.setdefault((int(w["type"][c]), int(w["degree"][c]), int(w["n_ctrl"][c]), int(w["n_samples"][c])),
+                          []).append(c)
+    for (ty, p, n, ns), ids in groups.items():
+        if ns == 0:
+            continue
+        ids = np.array(ids)
+        ctrl = np.stack([w["ctrl_pool"][w["ctrl_off"][c]: w["ctrl_off"][c] + n * dim].reshape(n, dim) for c in ids])
+        t = oracle.grid(ns)
+        if ty == 0:
+            pts = oracle.bezier(ctrl, t)
+        elif ty == 1:
+            pts = oracle.bspline(ctrl, p, t)
+        else:
+            wts = np.stack([w["weight_pool"][w["weight_off"][c]: w["weight_off"][c] + n] for c in ids])
+            pts = oracle.bspline(ctrl, p, t, weights=wts)
+        for k, c in enumerate(ids):
+            out[w["out_off"][c]: w["out_off"][c] + ns * dim] = pts[k].ravel()
+    return out
+
+
+def _check_all(got, ref, w):
+    dim = w["dim"]
+    worst = 0.0
+    for c in range(len(w["type"])):
+        ns = int(w["n_samples"][c])
+        if ns == 0:
+            continue
+        g = got[w["out_off"][c]: w["out_off"][c] + ns * dim].reshape(1, ns, dim)
+        r = ref[w["out_off"][c]: w["out_off"][c] + ns * dim].reshape(1, ns, dim)
+        worst = max(worst, float(normalised_error(g, r)[0]))
+    return worst
+
+
+@pytest.fixture(scope="module")
+def workload():
+    from paper_2603_15447_gb300 import synth
+    w = synth.batch(n_curves=3000, max_samples=600)
+    return w, _reference(w)
+
+
+def _pools(torch, w):
+    ctrl = torch.from_numpy(w["ctrl_pool"]).cuda()
+    wts = torch.from_numpy(w["weight_pool"]).cuda()
+    out = torch.full((w["out_len"],), float("nan"), device="cuda")
+    return ctrl, wts, out
+
+
+def _desc(w):
+    from paper_2603_15447_gb300 import bez
+    return bez.descriptors(w["type"], w["degree"], w["n_ctrl"], w["n_samples"], w["ctrl_off"], w["weight_off"],
+                           w["out_off"])
+
+
+@pytest.mark.parametrize("schedule,chunk,threads", [(0, 256, 256), (1, 512, 128), (0, 2048, 128)])
+def test_batch_plan_graph_replay(workload, schedule, chunk, threads):
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    w, ref = workload
+    ctrl, wts, out = _pools(torch, w)
+    b = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, chunk=chunk, schedule=schedule, threads=threads)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        b.launch()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert _check_all(got, ref, w) <= FP32_BAR
+    assert b.config() == {"chunk": chunk, "schedule": schedule, "threads": threads}
+    b.close()
+
+
+def test_batch_autotune_and_static_spans(workload, tmp_path, monkeypatch):
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    w, ref = workload
+    monkeypatch.setenv("BEZ_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    ctrl, wts, out = _pools(torch, w)
+    b = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, autotune=True, setup_each_launch=False)
+    cfg = b.config()
+    assert cfg["chunk"] in (256, 512, 1024, 2048) and cfg["schedule"] in (0, 1) and cfg["threads"] in (128, 256)
+    out.fill_(float("nan"))
+    b.launch()
+    torch.cuda.synchronize()
+    assert _check_all(out.cpu().numpy(), ref, w) <= FP32_BAR
+    b.close()
+    text = (tmp_path / "tune.json").read_text()
+    assert '"chunk"' in text and "batch-v1" in text
+    # a second plan of the same shape takes the cached choice
+    b2 = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, autotune=True)
+    assert b2.config() == cfg
+    b2.close()
+
+
+def test_one_shot_and_empty_curves(workload):
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    w, ref = workload
+    ctrl, wts, out = _pools(torch, w)
+    bez.bez_eval_batch(_desc(w), w["dim"], ctrl, wts, out)
+    assert _check_all(out.cpu().numpy(), ref, w) <= FP32_BAR
+    d = _desc(w)[:10].copy()
+    d["n_samples"][3] = 0
+    d["n_samples"][4] = 1
+    bez.bez_eval_batch(d, w["dim"], ctrl, wts, out)
+
+
+def test_batch_rejects_bad_descriptors(workload):
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    w, _ = workload
+    ctrl, wts, out = _pools(torch, w)
+    for field, value in (("degree", 9), ("ctrl_off", 10 ** 12), ("out_off", -1), ("type", 5)):
+        d = _desc(w)[:5].copy()
+        d[field][2] = value
+        with pytest.raises(bez.BezError) as e:
+            bez.bez_eval_batch(d, w["dim"], ctrl, wts, out)
+        assert e.value.status == bez.Status.INVALID_ARG and "curve 2" in str(e.value)
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_batch(_desc(w)[:5], w["dim"], ctrl.cpu(), wts, out)
+    assert e.value.status == bez.Status.INVALID_ARG

@@ -155,3 +155,21 @@ def test_spline_argument_errors():
         bez.bez_eval_bspline(torch.zeros((2, 8, 3), device="cuda", dtype=torch.float16), 3,
                              torch.zeros(4, device="cuda"))
     assert e.value.status == bez.Status.UNSUPPORTED
+
+
+@pytest.mark.parametrize("rational", [False, True])
+def test_parameters_next_to_knots_pick_their_span(rational):
+    # Degree-1 splines have kinks at every knot: evaluating the neighbouring
+    # span a hair outside its interval costs a first-order error there.
+    # Sample at the FP32 neighbours of every knot k / (n - p).
+    torch = need_gpu()
+    rng = np.random.default_rng(700 + rational)
+    n, p = 61, 1
+    ctrl = rng.uniform(-1, 1, size=(64, n, 3)).astype(np.float32)
+    w = rng.uniform(0.5, 2, size=(64, n)).astype(np.float32) if rational else None
+    knots = np.array([k / (n - p) for k in range(n - p + 1)], np.float32)
+    t = np.unique(np.concatenate([knots, np.nextafter(knots, np.float32(0)), np.nextafter(knots, np.float32(1))]))
+    t = t[(t >= 0) & (t <= 1)].astype(np.float32)
+    got = _bspline(torch, ctrl, p, t, weights=w)
+    ref = oracle.bspline(ctrl, p, t, weights=w)
+    assert normalised_error(got, ref).max() <= FP32_BAR
