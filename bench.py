@@ -1,19 +1,24 @@
-"""Benchmark: curve points evaluated per second on the fused
-evaluate-and-measure workload, per evaluator, against FP32 Horner on the same
-GPU, with the max normalised error against the FP64 oracle.
+"""Benchmark: curve points evaluated per second per evaluator, as a speed-up
+over FP32 Horner on the same GPU, with the max normalised error against the
+FP64 oracle.
 
-Workload (one step): 1,048,576 cubic 3D Bezier curves (control points
-U[-1,1]^3, FP32), each at 1024 parameters drawn U[0,1) inside the kernel,
-evaluated and reduced to one polyline length per curve; no points are
-stored.  A step is one bez_eval call: per-curve setup, parameter draw,
-evaluation and the warp-shuffle length reduction, all in one kernel.
+Default workload (precision/texture), one step = one bez_eval call over
+1,048,576 cubic 3D Bezier curves (control points U[-1,1]^3 FP32), each at
+1024 parameters drawn U[0,1) inside the kernel, reduced to one polyline
+length per curve (no point stores): per-curve setup, parameter draw,
+evaluation and warp-shuffle reduction in one kernel (texture variants add
+the atlas packing kernel).  The same line reports the C0 chain part of the
+workload (16,384 chains x 64 quadratic segments, 65,536 parameters each,
+register de Casteljau vs the zig-zag texture).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload precision|plain|chains|batch|tensor|fit]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank evaluates its own
-batch of the same size (weak scaling, different seeds); the only
-cross-rank traffic is the timing barrier and a max over ranks of the timed
-duration.
+batch of the same size (weak scaling, different seeds); the only cross-rank
+traffic is the timing barrier and a max over ranks of the timed duration.
+Workloads other than the default print their own line (measurement of the
+other configurations; the default line is the headline).
 """
 from __future__ import annotations
 
@@ -34,25 +39,22 @@ sys.path.insert(0, ROOT)
 METRIC = "curve points evaluated/sec vs FP32 Horner on same GB300, at max err vs FP64 oracle"
 N_CURVES = 1 << 20
 N_T = 1024
-DEGREE = 3
-DIM = 3
 WORKLOAD = ("precision/texture: 1,048,576 cubic 3D Bezier curves (U[-1,1]^3 FP32), 1024 parameters per curve "
             "drawn U[0,1) in-kernel, fused per-curve polyline length (no point stores)")
 
-# Algorithmic lane operations per point (cubic, 3D), see the design doc:
-# parameter draw 12 (xor, lowbias32 = 3 shift + 3 xor + 2 mul, shift-or,
+# Algorithmic lane operations per point (cubic, 3D):
+# parameter draw 12 (xor, lowbias32 = 3 shift + 3 xor + 2 mul, funnel shift,
 # subtract) + evaluation + polyline step 8 (3 sub, mul + 2 fma, sqrt, add).
 T_OPS, LEN_OPS = 12, 8
-EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 10, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36}
-VARIANTS = ["HORNER", "HORNER_CENTRED", "BERNSTEIN", "SEILER", "DECASTELJAU"]
-FP32_BAR = 1e-6
-
-
-def alu_peak(peaks):
-    """FP32/INT32 lane-operation issue peak: 152 SMs x 128 lanes x max clock."""
-    sms, lanes = 152, 128
-    mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
-    return sms * lanes * mhz * 1e6, f"152 SMs x 128 lanes x {mhz:.0f} MHz (derived from unit counts and max clock)"
+EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 10, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
+            "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
+# filtered fetches per point and the peak they are held to
+TEX_FETCHES = {"TEX_DECASTELJAU": (1, "tex3d_f32"), "TEX_SEILER": (1, "tex2d_f32"), "TEX_HYBRID": (2, "tex2d_f32")}
+REG_VARIANTS = ["HORNER", "HORNER_CENTRED", "BERNSTEIN", "SEILER", "DECASTELJAU"]
+TEX_VARIANTS = ["TEX_DECASTELJAU", "TEX_SEILER", "TEX_HYBRID"]
+VARIANTS = REG_VARIANTS + TEX_VARIANTS
+FP32_BAR, TEX_BAR = 1e-6, 2e-3
+SMS, LANES = 152, 128
 
 
 def load_peaks():
@@ -61,6 +63,18 @@ def load_peaks():
         with open(p) as f:
             return json.load(f)
     return None
+
+
+def alu_peak(peaks):
+    """FP32/INT32 lane-operation issue peak: 152 SMs x 128 lanes x max clock."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
+    return SMS * LANES * mhz * 1e6, f"derived: {SMS} SMs x {LANES} lanes x {mhz:.0f} MHz"
+
+
+def hbm_peak(peaks):
+    if peaks and "hbm_gbs" in peaks:
+        return float(peaks["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    return 6800.0, "of fallback (6.8 TB/s)"
 
 
 class ClockSampler:
@@ -118,87 +132,122 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ ours
+class Timer:
+    """Times K steps with CUDA events on the current stream, flushing L2
+    (256 MiB device write) before each step outside the timed region; the
+    library's own events bracket its main kernels."""
 
-def run_ours(args, rank, world, local_rank):
+    def __init__(self, torch, ctx, dev, world):
+        self.torch, self.ctx, self.dev, self.world = torch, ctx, dev, world
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+
+    def run(self, step, steps, warmup):
+        torch = self.torch
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        self.ctx.reset_stats()
+        self.ctx.set_timing(True)
+        evs = []
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            self.flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            step()
+            b.record(self.stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        self.ctx.set_timing(False)
+        st = self.ctx.stats()
+        return sum(a.elapsed_time(b) for a, b in evs), st
+
+
+def max_over_ranks(torch, dev, world, ms):
+    if world == 1:
+        return ms
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measure_peaks(bez, ctx):
+    out = {}
+    for k in ("fma", "tex2d_f32", "tex2d_f16", "tex3d_f32", "tex3d_f16"):
+        out[k] = bez.bez_measure_peak(k, ctx=ctx)
+    return out
+
+
+# ------------------------------------------------------------------ default workload
+
+def run_precision(args, rank, world, local_rank):
     import torch
 
     from paper_2603_15447_gb300 import bez, synth
-    from paper_2603_15447_gb300 import build as _build
 
-    if rank == 0 or world == 1:
-        _build.build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     seed = synth.BASE_SEED + 1 + 1000 * rank
     ctrl_np = synth.precision(seed=seed, n_curves=args.n_curves)
     ctrl = torch.from_numpy(ctrl_np).to(dev)
     out = torch.empty(args.n_curves, dtype=torch.float32, device=dev)
     ctx = bez.context(local_rank)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MiB > 129 MB L2
+    timer = Timer(torch, ctx, dev, world)
+    ts = synth.PRECISION_T_STREAM
 
-    def step(variant):
-        bez.bez_eval(ctrl, None, n_t=args.n_t, variant=bez.Variant[variant], out_mode=bez.OutMode.POLYLINE_LENGTH,
-                     t_mode=bez.TMode.HASH, seed=seed, stream_id=synth.PRECISION_T_STREAM, out=out, ctx=ctx)
+    def step_for(v):
+        def step():
+            bez.bez_eval(ctrl, None, n_t=args.n_t, variant=bez.Variant[v], out_mode=bez.OutMode.POLYLINE_LENGTH,
+                         t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, out=out, ctx=ctx)
+        return step
 
-    def timed(variant, steps, warmup, sampler=None):
-        for _ in range(warmup):
-            step(variant)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        ctx.reset_stats()
-        ctx.set_timing(True)
-        evs = []
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter()
-        for _ in range(steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step(variant)
-            b.record(stream)
-            evs.append((a, b))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall
-        if world > 1:
-            dist.barrier()
-        ctx.set_timing(False)
-        st = ctx.stats()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        return ms, st, wall
-
-    results = {}
-    headline = args.variant
     run_variants = [v for v in VARIANTS if v in args.variants.split(",")] if args.variants else list(VARIANTS)
-    if headline not in run_variants:
-        run_variants.append(headline)
+    for must in ("HORNER", args.variant):
+        if must not in run_variants:
+            run_variants.append(must)
+    results = {}
     with ClockSampler(local_rank) as clocks:
         for v in run_variants:
-            ms, st, wall = timed(v, args.steps, args.warmup)
+            ms, st = timer.run(step_for(v), args.steps, args.warmup)
             results[v] = {"ms": ms, "stats": st}
     clock_summary = clocks.summary()
 
-    # max over ranks of the device time of the headline variant
-    ms_head = results[headline]["ms"]
-    if world > 1:
-        t = torch.tensor([ms_head], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_head = float(t.item())
+    # chain part of the workload: register de Casteljau vs zig-zag texture
+    chains = None
+    if not args.skip_chains:
+        cctrl_np, _ = synth.chains(n_chains=args.n_chains, n_t=1)
+        cctrl = torch.from_numpy(cctrl_np).to(dev)
+        cout = torch.empty(args.n_chains, dtype=torch.float32, device=dev)
+        chains = {}
+        csteps = max(args.steps // 4, 3)
+        for v in ("DECASTELJAU", "TEX_DECASTELJAU"):
+            def cstep(v=v):
+                bez.bez_eval_piecewise(cctrl, 64, 2, None, n_t=args.chain_t, variant=bez.Variant[v],
+                                       out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed,
+                                       stream_id=12, out=cout, ctx=ctx)
+            ms, st = timer.run(cstep, csteps, 2)
+            n_pts = args.n_chains * args.chain_t * csteps
+            chains[v] = {"points_per_s": n_pts / (ms * 1e-3),
+                         "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
+
+    ms_head = max_over_ranks(torch, dev, world, results[args.variant]["ms"])
 
     # end to end through the public API with pinned host buffers
     ctrl_host = torch.from_numpy(ctrl_np).pin_memory()
     out_host = torch.empty(args.n_curves, dtype=torch.float32).pin_memory()
 
     def e2e_step():
-        bez.bez_eval(ctrl_host, None, n_t=args.n_t, variant=bez.Variant[headline],
-                     out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed,
-                     stream_id=synth.PRECISION_T_STREAM, out=out_host, ctx=ctx)
+        bez.bez_eval(ctrl_host, None, n_t=args.n_t, variant=bez.Variant[args.variant],
+                     out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed, stream_id=ts,
+                     out=out_host, ctx=ctx)
 
     for _ in range(max(args.warmup, 1)):
         e2e_step()
@@ -210,45 +259,51 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return None
-
-    pts_per_step = args.n_curves * args.n_t
-    peaks = load_peaks()
-    peak, peak_note = alu_peak(peaks)
+    peak_alu, peak_note = alu_peak(load_peaks())
+    peaks = measure_peaks(bez, ctx)
+    pts_step = args.n_curves * args.n_t
     variants = {}
     for v in run_variants:
         r = results[v]
         st = r["stats"]
         kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
-        ops = (T_OPS + EVAL_OPS[v] + LEN_OPS) * pts_per_step
-        variants[v] = {"points_per_s": pts_per_step * args.steps / (r["ms"] * 1e-3),
-                       "ms_per_step": r["ms"] / args.steps, "kernel_ms": kern_ms,
-                       "alu_frac": ops / (kern_ms * 1e-3) / peak, "ops_per_point": T_OPS + EVAL_OPS[v] + LEN_OPS}
-    horner = variants["HORNER"]["points_per_s"] if "HORNER" in variants else None
+        ops = (T_OPS + EVAL_OPS[v] + LEN_OPS) * pts_step
+        row = {"points_per_s": pts_step * args.steps / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / args.steps,
+               "kernel_ms": kern_ms, "ops_per_point": T_OPS + EVAL_OPS[v] + LEN_OPS,
+               "alu_frac": ops / (kern_ms * 1e-3) / peak_alu}
+        if v in TEX_FETCHES:
+            nf, kind = TEX_FETCHES[v]
+            row["fetches_per_s"] = nf * pts_step / (kern_ms * 1e-3)
+            row["tex_frac"] = row["fetches_per_s"] / peaks[kind]
+            row["tex_peak"] = kind
+        variants[v] = row
+    horner = variants["HORNER"]["points_per_s"]
     for v in run_variants:
-        variants[v]["speedup_vs_horner"] = variants[v]["points_per_s"] / horner if horner else None
+        variants[v]["speedup_vs_horner"] = variants[v]["points_per_s"] / horner
 
-    # accuracy on a sample of the same workload (points mode, same parameters)
     if not args.skip_accuracy:
         import oracle
         ns = args.accuracy_curves
         sample = ctrl[:ns].contiguous()
-        th = oracle.hash_t(seed, synth.PRECISION_T_STREAM, 0, ns, args.n_t)
+        th = oracle.hash_t(seed, ts, 0, ns, args.n_t)
         ref = oracle.bezier(ctrl_np[:ns], th)
         diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
         for v in run_variants:
             pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
-                               seed=seed, stream_id=synth.PRECISION_T_STREAM, ctx=ctx)
+                               seed=seed, stream_id=ts, ctx=ctx)
             err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
+            bar = TEX_BAR if v in TEX_FETCHES else FP32_BAR
             variants[v]["max_norm_err"] = float(err.max())
-            variants[v]["meets_1e-6"] = bool(err.max() <= FP32_BAR)
+            variants[v]["bar"] = bar
+            variants[v]["meets_bar"] = bool(err.max() <= bar)
 
-    head = variants[headline]
+    head = variants[args.variant]
     kern_ms = head["kernel_ms"]
-    ops_launch = head["ops_per_point"] * pts_per_step
+    ops_launch = head["ops_per_point"] * pts_step
     achieved = ops_launch / (kern_ms * 1e-3)
     line = {
         "metric": METRIC,
-        "value": pts_per_step * world * args.steps / (ms_head * 1e-3),
+        "value": pts_step * world * args.steps / (ms_head * 1e-3),
         "unit": "points/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -259,18 +314,26 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": headline, "n_curves": args.n_curves, "n_t": args.n_t,
-                   "degree": DEGREE, "dim": DIM, "l2": "flushed between timed steps (256 MiB device write)",
-                   "speedup_vs_horner": head["speedup_vs_horner"]},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": args.traffic, "peak_source": peak_note,
-                     "ops_per_launch": ops_launch, "kernel": "k_curve (fused hash + eval + polyline length)"},
-        "e2e": {"value": pts_per_step / e2e_s, "unit": "points/s",
+        "config": {"workload": WORKLOAD, "variant": args.variant, "n_curves": args.n_curves, "n_t": args.n_t,
+                   "degree": 3, "dim": 3, "l2": "flushed between timed steps (256 MiB device write)",
+                   "speedup_vs_horner": head["speedup_vs_horner"],
+                   "max_norm_err": head.get("max_norm_err")},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_alu / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak_alu, "traffic": args.traffic, "peak_source": peak_note,
+                     "ops_per_launch": ops_launch, "kernel": "k_curve (fused draw + eval + polyline length)",
+                     "measured_fma_peak_tops": peaks["fma"] / 1e12},
+        "e2e": {"value": pts_step / e2e_s, "unit": "points/s",
                 "h2d_bytes_per_step": int(ctrl_np.nbytes), "d2h_bytes_per_step": int(args.n_curves * 4)},
-        "gpu_launches": int(results[headline]["stats"]["launches"]),
+        "gpu_launches": int(results[args.variant]["stats"]["launches"]),
         "clocks": clock_summary,
         "variants": variants,
+        "peaks_measured": {"fma_tops": peaks["fma"] / 1e12,
+                           **{k + "_gfetch_s": peaks[k] / 1e9 for k in peaks if k.startswith("tex")}},
     }
+    if chains is not None:
+        line["chains"] = {"workload": f"{args.n_chains} C0 chains x 64 quadratic segments, {args.chain_t} "
+                                      "parameters per chain drawn U[0,64) in-kernel, fused polyline length",
+                          **chains}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ctrl_np, seed, args.n_t, args.cpu_seconds)
     return line
@@ -294,6 +357,132 @@ def cpu_baseline(ctrl_np, seed, n_t, seconds):
     return {"value": done * n_t / el, "unit": "points/s", "cores": threads, "kind": "oracle",
             "sample": f"first {done} of {ctrl_np.shape[0]} curves x {n_t} parameters (FP64 Bernstein sum + "
                       f"polyline length), {el:.1f} s wall"}
+
+
+# ------------------------------------------------------------------ other workloads
+
+def _hbm_line(name, value, unit, steps, warmup, ms, bytes_step, kern_ms, kernel, extra):
+    peak, note = hbm_peak(load_peaks())
+    achieved = bytes_step / (kern_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": name},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": note, "bytes_per_launch": bytes_step, "kernel": kernel}}
+    line.update(extra)
+    return line
+
+
+def run_plain(args):
+    import torch
+
+    from paper_2603_15447_gb300 import bez, synth
+    ctx = bez.context(0)
+    ctrl_np, t_np = synth.plain()
+    ctrl, t = torch.from_numpy(ctrl_np).cuda(), torch.from_numpy(t_np).cuda()
+    out = torch.empty((4096, 256, 3), device="cuda")
+    timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
+    res = {}
+    for v in ("HORNER", "DECASTELJAU", "SEILER", "HORNER_CENTRED"):
+        ms, st = timer.run(lambda v=v: bez.bez_eval(ctrl, t, variant=bez.Variant[v], out=out, ctx=ctx),
+                           args.steps, args.warmup)
+        res[v] = {"points_per_s": 4096 * 256 * args.steps / (ms * 1e-3),
+                  "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
+    head = res["DECASTELJAU"]
+    return _hbm_line("plain: 4,096 cubic 3D curves x 256 shared uniform t, points stored", head["points_per_s"],
+                     "points/s", args.steps, args.warmup, 4096 * 256 * args.steps / head["points_per_s"] * 1e3,
+                     4096 * 256 * 12 + 4096 * 48 + 1024, head["kernel_ms"], "k_curve (points)",
+                     {"variants": res, "note": "12.6 MB of output fits in L2; the launch is latency-bound"})
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2603_15447_gb300 import bez, synth
+    ctx = bez.context(0)
+    w = synth.batch()
+    ctrl, wts = torch.from_numpy(w["ctrl_pool"]).cuda(), torch.from_numpy(w["weight_pool"]).cuda()
+    out = torch.empty(w["out_len"], device="cuda")
+    desc = bez.descriptors(w["type"], w["degree"], w["n_ctrl"], w["n_samples"], w["ctrl_off"], w["weight_off"],
+                           w["out_off"])
+    timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
+    n_pts = int(w["n_samples"].sum())
+    full = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=True, use_graph=True, ctx=ctx)
+    ms_full, st_full = timer.run(full.launch, args.steps, args.warmup)
+    cfg = full.config()
+    full.close()
+    ev = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=False, use_graph=True, ctx=ctx)
+    ms_ev, st_ev = timer.run(ev.launch, args.steps, args.warmup)
+    ev.close()
+    bytes_step = n_pts * 12 + w["ctrl_pool"].nbytes + w["weight_pool"].nbytes
+    return _hbm_line(f"batch: {len(desc)} mixed curves (50% Bezier deg 1-7, 25% cubic B-spline, 25% NURBS), "
+                     f"{n_pts} points, one graph-captured persistent launch, autotuned",
+                     n_pts * args.steps / (ms_full * 1e-3), "points/s", args.steps, args.warmup, ms_full, bytes_step,
+                     ms_ev / args.steps, "k_batch_eval (graph replay, spans extracted once)",
+                     {"setup_each_launch_points_per_s": n_pts * args.steps / (ms_full * 1e-3),
+                      "eval_only_points_per_s": n_pts * args.steps / (ms_ev * 1e-3),
+                      "gpu_launches": int(st_full["launches"]), "autotuned": cfg, "n_points": n_pts})
+
+
+def run_tensor(args):
+    import torch
+
+    from paper_2603_15447_gb300 import bez, synth
+    ctx = bez.context(0)
+    s = torch.from_numpy(synth.surfaces()).cuda()
+    v = torch.from_numpy(synth.volumes()).cuda()
+    so = torch.empty((65536, 32, 32, 3), device="cuda")
+    vo = torch.empty((4096, 16, 16, 16, 1), device="cuda")
+    timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
+    ms_s, st_s = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, out=so, ctx=ctx), args.steps, args.warmup)
+    ms_v, st_v = timer.run(lambda: bez.bez_eval_volume(v, 16, 16, 16, out=vo, ctx=ctx), args.steps, args.warmup)
+    n_s, n_v = 65536 * 1024, 4096 * 4096
+    ks = st_s["timed_ms"] / st_s["timed_launches"]
+    kv = st_v["timed_ms"] / st_v["timed_launches"]
+    return _hbm_line("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
+                     (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
+                     ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3",
+                     {"surface_points_per_s": n_s * args.steps / (ms_s * 1e-3),
+                      "volume_values_per_s": n_v * args.steps / (ms_v * 1e-3), "volume_kernel_ms": kv,
+                      "volume_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9})
+
+
+def run_fit(args):
+    import torch
+
+    from paper_2603_15447_gb300 import bez, synth
+    from paper_2603_15447_gb300.autograd import bezier_curve
+    ctx = bez.context(0)
+    truth, t_true, noise, init = synth.fit()
+    target = bez.bez_eval(torch.from_numpy(truth).cuda(), torch.from_numpy(t_true).cuda(),
+                          variant=bez.Variant.DECASTELJAU) + torch.from_numpy(noise).cuda()
+    ctrl = torch.tensor(init, device="cuda", requires_grad=True)
+    t = torch.tensor(np.tile((np.arange(512) / 511.0).astype(np.float32), (65536, 1)), device="cuda",
+                     requires_grad=True)
+    opt = torch.optim.Adam([ctrl, t], lr=1e-2)
+
+    def step():
+        opt.zero_grad(set_to_none=False)
+        loss = ((bezier_curve(ctrl, t) - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            t.clamp_(0, 1)
+        return loss
+
+    timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
+    first = float(step())
+    ms, st = timer.run(step, args.steps, args.warmup)
+    for _ in range(max(0, 200 - args.steps - args.warmup - 2)):
+        step()
+    final = float(step())
+    n = 65536 * 512
+    kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
+    # forward + adjoint kernels per sample: t 4 B in, point 12 B out; t 4 B + grad_out 12 B in, grad_t 4 B out
+    return _hbm_line("fit: 65,536 cubic 3D curves x 512 samples, forward + MSE + adjoint + Adam per step",
+                     n * args.steps / (ms * 1e-3), "samples/s", args.steps, args.warmup, ms, n * 18, kern_ms,
+                     "k_curve (forward) and k_grad (adjoint), mean launch",
+                     {"loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5})
 
 
 # ------------------------------------------------------------------ reference arm
@@ -337,10 +526,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", default="HORNER_CENTRED", choices=VARIANTS)
+    ap.add_argument("--workload", choices=["precision", "plain", "chains", "batch", "tensor", "fit"],
+                    default="precision")
+    ap.add_argument("--variant", default="HORNER_CENTRED", choices=VARIANTS,
+                    help="headline evaluator (the fastest one meeting the FP32 bar)")
     ap.add_argument("--variants", default="", help="comma-separated subset of evaluators to time")
     ap.add_argument("--n-curves", type=int, default=N_CURVES)
     ap.add_argument("--n-t", type=int, default=N_T)
+    ap.add_argument("--n-chains", type=int, default=16384)
+    ap.add_argument("--chain-t", type=int, default=65536)
+    ap.add_argument("--skip-chains", action="store_true")
     ap.add_argument("--accuracy-curves", type=int, default=4096)
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -356,12 +551,27 @@ def main():
     if args.impl == "reference":
         line = run_reference(args, rank)
     else:
+        import torch
+
+        from paper_2603_15447_gb300 import build as _build
         if world > 1:
-            import torch
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-        line = run_ours(args, rank, world, local_rank)
+            if rank == 0:
+                _build.build()
+            dist.barrier()
+        else:
+            _build.build()
+            torch.cuda.set_device(0)
+        if args.workload == "precision":
+            line = run_precision(args, rank, world, local_rank)
+        elif args.workload == "chains":
+            args.variants = "HORNER"
+            args.skip_accuracy = True
+            line = run_precision(args, rank, world, local_rank)
+        else:
+            line = {"plain": run_plain, "batch": run_batch, "tensor": run_tensor, "fit": run_fit}[args.workload](args)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -338,6 +338,29 @@ bez_status bez_eval_spline_noalloc(const float* ctrl, const float* weights, cons
                                    const bez_opts* opts, void* stream);
 
 /*
+ * bez_measure_peak -- microbenchmarks giving the roofline denominators of the
+ * evaluators on this device (no counterpart in the paper, whose Sec. 5 times
+ * whole frames).  Synchronous; allocates and frees its own buffers.
+ *   BEZ_PEAK_FMA      FP32 FMA lane operations per second (8 independent
+ *                     chains per thread, every SM busy)
+ *   BEZ_PEAK_TEX2D_F32 / _F16  bilinear-filtered float4 / half4 fetches per
+ *                     second from an L1-resident 64x64 texture
+ *   BEZ_PEAK_TEX3D_F32 / _F16  trilinear-filtered fetches per second
+ *   BEZ_PEAK_STORE    device-memory store bandwidth, GB/s (2 GiB of float4)
+ *   BEZ_PEAK_COPY     device-memory copy bandwidth, GB/s counting read+write
+ */
+typedef enum bez_peak_kind {
+    BEZ_PEAK_FMA = 0,
+    BEZ_PEAK_TEX2D_F32 = 1,
+    BEZ_PEAK_TEX2D_F16 = 2,
+    BEZ_PEAK_TEX3D_F32 = 3,
+    BEZ_PEAK_TEX3D_F16 = 4,
+    BEZ_PEAK_STORE = 5,
+    BEZ_PEAK_COPY = 6
+} bez_peak_kind;
+bez_status bez_measure_peak(bez_ctx ctx, int kind, double* value, void* stream);
+
+/*
  * bez_probe_filter -- characterise the texture unit's linear-filter weights.
  *
  * Paper Sec. 2.3: the hardware converts texture coordinates to a fixed-point

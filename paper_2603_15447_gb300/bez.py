@@ -481,3 +481,20 @@ def bez_eval_batch(desc, dim, ctrl_pool, weight_pool, out_pool, *, stream=None, 
                             _ptr(weight_pool), _numel(weight_pool), _ptr(out_pool), _numel(out_pool),
                             _stream_handle(stream, dev)))
     return out_pool
+
+
+PEAK_KINDS = {"fma": 0, "tex2d_f32": 1, "tex2d_f16": 2, "tex3d_f32": 3, "tex3d_f16": 4, "store": 5, "copy": 6}
+
+
+def bez_measure_peak(kind, *, stream=None, ctx=None):
+    """Run one peak microbenchmark (see include/bez.h): FMA lane-ops/s,
+    texture fetches/s, or memory GB/s."""
+    L = lib()
+    if not getattr(L, "_peak_ready", False):
+        L.bez_measure_peak.argtypes = [_VP, _INT, ctypes.POINTER(ctypes.c_double), _VP]
+        L.bez_measure_peak.restype = ctypes.c_int
+        L._peak_ready = True
+    c = ctx or context()
+    v = ctypes.c_double()
+    _check(L.bez_measure_peak(c.handle, PEAK_KINDS[kind], ctypes.byref(v), _stream_handle(stream, c.device)))
+    return v.value

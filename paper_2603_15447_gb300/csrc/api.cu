@@ -696,6 +696,17 @@ bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights,
     return stg.finish(o->sync);
 }
 
+bez_status bez_measure_peak(bez_ctx c, int kind, double* value, void* stream)
+{
+    if (!c || !value) return fail(BEZ_ERR_INVALID_ARG, "null argument");
+    if (kind < BEZ_PEAK_FMA || kind > BEZ_PEAK_COPY) return fail(BEZ_ERR_INVALID_ARG, "unknown peak kind %d", kind);
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    *value = 0.0;
+    BEZ_CUDA(measure_peak(kind, c->sm_count, static_cast<cudaStream_t>(stream), value), "peak microbenchmark");
+    return BEZ_OK;
+}
+
 bez_status bez_probe_filter(bez_ctx c, const float* xyz, int64_t n, float* out, void* stream)
 {
     if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");

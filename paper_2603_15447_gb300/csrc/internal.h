@@ -167,6 +167,11 @@ struct BatchArgs {
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
                          const LaunchHooks& h, int* launches);
 
+// Peak microbenchmarks (peaks.cu): kind 0 FP32 FMA lane-ops/s, 1..4 texture
+// fetches/s (2D float4, 2D half4, 3D float4, 3D half4), 5 store GB/s,
+// 6 copy GB/s.
+cudaError_t measure_peak(int kind, int sm_count, cudaStream_t s, double* value);
+
 // Message returned by bez_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
