@@ -413,6 +413,7 @@ def run_batch(args):
     full.close()
     ev = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=False, use_graph=True, ctx=ctx)
     ms_ev, st_ev = timer.run(ev.launch, args.steps, args.warmup)
+    cfg_ev = ev.config()
     ev.close()
     bytes_step = n_pts * 12 + w["ctrl_pool"].nbytes + w["weight_pool"].nbytes
     return _hbm_line(f"batch: {len(desc)} mixed curves (50% Bezier deg 1-7, 25% cubic B-spline, 25% NURBS), "
@@ -421,7 +422,8 @@ def run_batch(args):
                      ms_ev / args.steps, "k_batch_eval (graph replay, spans extracted once)",
                      {"setup_each_launch_points_per_s": n_pts * args.steps / (ms_full * 1e-3),
                       "eval_only_points_per_s": n_pts * args.steps / (ms_ev * 1e-3),
-                      "gpu_launches": int(st_full["launches"]), "autotuned": cfg, "n_points": n_pts})
+                      "gpu_launches": int(st_full["launches"]), "autotuned": cfg, "autotuned_eval_only": cfg_ev,
+                      "n_points": n_pts})
 
 
 def run_tensor(args):

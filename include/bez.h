@@ -240,8 +240,10 @@ bez_status bez_eval_volume(bez_ctx ctx, const void* ctrl, int64_t n, int du, int
  *
  * bez_batch_create validates every descriptor on the host (offsets against
  * the pool lengths), builds the work-item table (curve, chunk of samples),
- * allocates the plan's device buffers (descriptors, items, the FP64-extracted
- * Bezier span pool of the splines), optionally autotunes chunk size,
+ * computes the FP64 knot-insertion operators of every distinct (n_ctrl,
+ * degree) of the splines, allocates the plan's device buffers (descriptors,
+ * items, operators, the span pool), optionally autotunes the span
+ * representation (Bezier points / power basis about 1/2), chunk size,
  * scheduler (static round-robin or atomic work queue) and block size by
  * timing candidates on the real batch (results cached in memory and, when
  * the environment variable BEZ_AUTOTUNE_CACHE names a file, in that JSON
@@ -267,9 +269,11 @@ typedef struct bez_batch_opts {
     int32_t autotune;          /* time candidate launch shapes at creation      */
     int32_t setup_each_launch; /* re-extract spline spans on every launch        */
     int32_t use_graph;         /* capture setup + evaluation in a CUDA graph     */
-    int32_t chunk;             /* samples per work item, 0 = default / tuned     */
+    int32_t chunk;             /* samples per work item (multiple of 256), 0 = default / tuned */
     int32_t schedule;          /* -1 default / tuned, 0 static, 1 atomic queue   */
-    int32_t threads;           /* threads per block, 0 = default / tuned         */
+    int32_t threads;           /* threads per block (128, 256), 0 = default / tuned */
+    int32_t repr;              /* -1 default / tuned, 0 Bezier points (de Casteljau),
+                                * 1 power basis about 1/2 (Horner)              */
 } bez_batch_opts;
 
 typedef struct bez_batch_s* bez_batch;
@@ -279,8 +283,8 @@ bez_status bez_batch_create(bez_ctx ctx, const bez_curve_desc* desc, int64_t n_c
                             float* out_pool, int64_t out_len, const bez_batch_opts* bopts, void* stream,
                             bez_batch* batch);
 bez_status bez_batch_launch(bez_batch batch, void* stream);
-/* chosen launch shape: chunk, schedule (0 static, 1 atomic), threads */
-bez_status bez_batch_config(bez_batch batch, int32_t* chunk, int32_t* schedule, int32_t* threads);
+/* chosen launch shape: chunk, schedule (0 static, 1 atomic), threads, span representation */
+bez_status bez_batch_config(bez_batch batch, int32_t* chunk, int32_t* schedule, int32_t* threads, int32_t* repr);
 bez_status bez_batch_destroy(bez_batch batch);
 bez_status bez_eval_batch(bez_ctx ctx, const bez_curve_desc* desc, int64_t n_curves, int dim, const float* ctrl_pool,
                           int64_t ctrl_len, const float* weight_pool, int64_t weight_len, float* out_pool,

@@ -402,7 +402,8 @@ DESC_DTYPE = np.dtype([("type", "<i4"), ("degree", "<i4"), ("n_ctrl", "<i4"), ("
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int32), ("setup_each_launch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("schedule", ctypes.c_int32), ("threads", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("schedule", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("repr", ctypes.c_int32)]
 
 
 def descriptors(type, degree, n_ctrl, n_samples, ctrl_off, weight_off, out_off):
@@ -419,8 +420,7 @@ def _batch_lib():
         L.bez_batch_create.argtypes = [_VP, _VP, _I64, _INT, _VP, _I64, _VP, _I64, _VP, _I64,
                                        ctypes.POINTER(BatchOpts), _VP, ctypes.POINTER(_VP)]
         L.bez_batch_launch.argtypes = [_VP, _VP]
-        L.bez_batch_config.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                       ctypes.POINTER(ctypes.c_int32)]
+        L.bez_batch_config.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 4
         L.bez_batch_destroy.argtypes = [_VP]
         L.bez_eval_batch.argtypes = [_VP, _VP, _I64, _INT, _VP, _I64, _VP, _I64, _VP, _I64, _VP]
         for n in ("bez_batch_create", "bez_batch_launch", "bez_batch_config", "bez_batch_destroy", "bez_eval_batch"):
@@ -437,13 +437,13 @@ class Batch:
     """A mixed-batch plan (bez_batch_create); ``launch()`` replays it."""
 
     def __init__(self, desc, dim, ctrl_pool, weight_pool, out_pool, *, autotune=False, setup_each_launch=True,
-                 use_graph=True, chunk=0, schedule=-1, threads=0, stream=None, ctx=None):
+                 use_graph=True, chunk=0, schedule=-1, threads=0, repr=-1, stream=None, ctx=None):
         L = _batch_lib()
         desc = np.ascontiguousarray(desc, dtype=DESC_DTYPE)
         self.dev = ctrl_pool.device.index
         self.ctx = ctx or context(self.dev)
         self._keep = (ctrl_pool, weight_pool, out_pool)
-        bo = BatchOpts(int(autotune), int(setup_each_launch), int(use_graph), chunk, schedule, threads)
+        bo = BatchOpts(int(autotune), int(setup_each_launch), int(use_graph), chunk, schedule, threads, repr)
         h = _VP()
         _check(L.bez_batch_create(self.ctx.handle, desc.ctypes.data, len(desc), dim, _ptr(ctrl_pool),
                                   _numel(ctrl_pool), _ptr(weight_pool), _numel(weight_pool), _ptr(out_pool),
@@ -455,9 +455,10 @@ class Batch:
         _check(_batch_lib().bez_batch_launch(self.handle, _stream_handle(stream, self.dev)))
 
     def config(self):
-        c, s, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _check(_batch_lib().bez_batch_config(self.handle, ctypes.byref(c), ctypes.byref(s), ctypes.byref(t)))
-        return {"chunk": c.value, "schedule": s.value, "threads": t.value}
+        c, s, t, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_batch_lib().bez_batch_config(self.handle, ctypes.byref(c), ctypes.byref(s), ctypes.byref(t),
+                                             ctypes.byref(r)))
+        return {"chunk": c.value, "schedule": s.value, "threads": t.value, "repr": r.value}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -9,9 +9,11 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "context.h"
+#include "spline.cuh"
 
 using namespace bez;
 
@@ -21,6 +23,7 @@ struct Shape {
     int chunk = 512;
     int schedule = 0;
     int threads = 256;
+    int repr = 1;  // 0 Bezier points + de Casteljau, 1 centred power basis + Horner
 };
 
 void no_count(void*) {}
@@ -61,7 +64,9 @@ void load_cache_file(const char* path)
         field("\"chunk\"", &sh.chunk);
         field("\"schedule\"", &sh.schedule);
         field("\"threads\"", &sh.threads);
-        if (sh.chunk > 0 && (sh.schedule == 0 || sh.schedule == 1) && (sh.threads == 128 || sh.threads == 256))
+        field("\"repr\"", &sh.repr);
+        if (sh.chunk > 0 && sh.chunk % 256 == 0 && (sh.schedule == 0 || sh.schedule == 1) &&
+            (sh.threads == 128 || sh.threads == 256) && (sh.repr == 0 || sh.repr == 1))
             g_tune_cache[key] = sh;
         pos = b1 + 1;
     }
@@ -75,8 +80,9 @@ void save_cache_file(const char* path)
     fprintf(f, "{\n");
     size_t i = 0;
     for (auto& kv : g_tune_cache) {
-        fprintf(f, "  \"%s\": {\"chunk\": %d, \"schedule\": %d, \"threads\": %d}%s\n", kv.first.c_str(),
-                kv.second.chunk, kv.second.schedule, kv.second.threads, ++i < g_tune_cache.size() ? "," : "");
+        fprintf(f, "  \"%s\": {\"chunk\": %d, \"schedule\": %d, \"threads\": %d, \"repr\": %d}%s\n",
+                kv.first.c_str(), kv.second.chunk, kv.second.schedule, kv.second.threads, kv.second.repr,
+                ++i < g_tune_cache.size() ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
@@ -93,7 +99,11 @@ struct bez_batch_s {
     std::vector<bez_curve_desc> hdesc;
     bez_curve_desc* d_desc = nullptr;
     int64_t* d_span_off = nullptr;
-    int64_t* d_spline_ids = nullptr;
+    double* d_ops = nullptr;
+    int64_t* d_span_ops = nullptr;
+    int64_t* d_op_off = nullptr;
+    int2* d_span_tab = nullptr;
+    bool spans_ready = false;
     int2* d_items = nullptr;
     size_t items_cap = 0;
     float* d_spans = nullptr;
@@ -110,11 +120,19 @@ namespace {
 
 bez_status build_items(bez_batch b, int chunk, cudaStream_t s)
 {
-    std::vector<int2> items;
+    // items grouped by class (one evaluator kernel per class)
+    std::vector<std::vector<int2>> per_class(kBatchClasses);
     for (size_t c = 0; c < b->hdesc.size(); ++c) {
         const int n = b->hdesc[c].n_samples;
-        for (int k = 0; (int64_t)k * chunk < n; ++k) items.push_back(make_int2((int)c, k));
+        auto& v = per_class[batch_item_class(b->hdesc[c], b->a.dim)];
+        for (int k = 0; (int64_t)k * chunk < n; ++k) v.push_back(make_int2((int)c, k));
     }
+    std::vector<int2> items;
+    for (int k = 0; k < kBatchClasses; ++k) {
+        b->a.class_start[k] = (int64_t)items.size();
+        items.insert(items.end(), per_class[k].begin(), per_class[k].end());
+    }
+    for (int k = kBatchClasses; k < 16; ++k) b->a.class_start[k] = (int64_t)items.size();
     if (items.size() > b->items_cap) {
         if (b->d_items) {
             cudaError_t e = cudaStreamSynchronize(s);  // the old table may still be read
@@ -138,19 +156,37 @@ bez_status build_items(bez_batch b, int chunk, cudaStream_t s)
     return BEZ_OK;
 }
 
+bez_status run_setup(bez_batch b, cudaStream_t s)
+{
+    const LaunchHooks h{no_count, no_event, no_event, nullptr, b->ctx->sm_count};
+    int k = 0;
+    // the setup kernel alone: an evaluator launch over zero items does no work
+    BatchArgs a = b->a;
+    a.n_items = 0;
+    for (int k = 0; k < 16; ++k) a.class_start[k] = 0;
+    cudaError_t e = launch_batch(a, b->shape.threads, b->ctx->sm_count, true, s, h, &k);
+    if (e != cudaSuccess) return cuda_fail(e, "batch setup");
+    b->spans_ready = true;
+    return BEZ_OK;
+}
+
 bez_status apply_shape(bez_batch b, const Shape& sh, cudaStream_t s)
 {
     if (b->a.chunk != sh.chunk || !b->a.items) {
         bez_status st = build_items(b, sh.chunk, s);
         if (st != BEZ_OK) return st;
     }
+    const bool repr_changed = b->a.repr != sh.repr;
     b->a.schedule = sh.schedule;
     b->a.grab = 4;
+    b->a.repr = sh.repr;
     b->shape = sh;
+    if (repr_changed || !b->spans_ready) return run_setup(b, s);
     return BEZ_OK;
 }
 
-// time the evaluator (no setup) for one shape: median of 3 after a warm-up
+// time one shape (setup included when it runs on every launch): median of 3
+// after a warm-up
 bez_status time_shape(bez_batch b, const Shape& sh, cudaStream_t s, float* ms_out)
 {
     bez_status st = apply_shape(b, sh, s);
@@ -161,10 +197,10 @@ bez_status time_shape(bez_batch b, const Shape& sh, cudaStream_t s, float* ms_ou
     cudaEventCreate(&e1);
     float t[3];
     int k = 0;
-    cudaError_t e = launch_batch(b->a, sh.threads, b->ctx->sm_count, false, s, h, &k);
+    cudaError_t e = launch_batch(b->a, sh.threads, b->ctx->sm_count, b->setup_each, s, h, &k);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
         cudaEventRecord(e0, s);
-        e = launch_batch(b->a, sh.threads, b->ctx->sm_count, false, s, h, &k);
+        e = launch_batch(b->a, sh.threads, b->ctx->sm_count, b->setup_each, s, h, &k);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&t[r], e0, e1);
@@ -188,10 +224,11 @@ bez_status autotune(bez_batch b, cudaStream_t s)
     }
     Shape best;
     float best_ms = 1e30f;
+    for (int repr : {1, 0})
     for (int chunk : {256, 512, 1024, 2048})
         for (int sched : {0, 1})
             for (int threads : {128, 256}) {
-                Shape sh{chunk, sched, threads};
+                Shape sh{chunk, sched, threads, repr};
                 float ms = 0.f;
                 bez_status st = time_shape(b, sh, s, &ms);
                 if (st != BEZ_OK) return st;
@@ -213,7 +250,10 @@ void free_batch(bez_batch b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     cudaFree(b->d_desc);
     cudaFree(b->d_span_off);
-    cudaFree(b->d_spline_ids);
+    cudaFree(b->d_ops);
+    cudaFree(b->d_span_ops);
+    cudaFree(b->d_op_off);
+    cudaFree(b->d_span_tab);
     cudaFree(b->d_items);
     cudaFree(b->d_spans);
     cudaFree(b->d_counter);
@@ -253,8 +293,11 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
         }
     }
     // validate every descriptor against the pools
-    std::vector<int64_t> span_off((size_t)n_curves, 0);
-    std::vector<int64_t> spline_ids;
+    std::vector<int64_t> span_off((size_t)n_curves, 0), op_off((size_t)n_curves, 0);
+    std::map<std::pair<int, int>, int64_t> op_index;   // (n_ctrl, degree) -> offset into span_ops
+    std::map<std::vector<long long>, int64_t> mat_index;  // distinct matrices -> offset into ops
+    std::vector<int64_t> span_ops;                       // per span: offset of its matrix in ops
+    std::vector<double> ops;
     int64_t spans = 0, total_samples = 0, n_type[3] = {0, 0, 0}, deg_sum = 0;
     for (int64_t i = 0; i < n_curves; ++i) {
         const bez_curve_desc& d = b->hdesc[(size_t)i];
@@ -275,11 +318,34 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
         n_type[d.type] += 1;
         deg_sum += d.degree;
         total_samples += d.n_samples;
+        const int comps = d.type == BEZ_CURVE_NURBS ? dim + 1 : dim;
+        const int n_spans = d.type == BEZ_CURVE_BEZIER ? 1 : d.n_ctrl - d.degree;
+        span_off[(size_t)i] = spans;
+        spans += (int64_t)n_spans * (d.degree + 1) * comps;
         if (d.type != BEZ_CURVE_BEZIER) {
-            const int comps = d.type == BEZ_CURVE_NURBS ? dim + 1 : dim;
-            span_off[(size_t)i] = spans;
-            spans += (int64_t)(d.n_ctrl - d.degree) * (d.degree + 1) * comps;
-            spline_ids.push_back(i);
+            // knot insertion once per distinct (n_ctrl, degree), in FP64
+            const auto key = std::make_pair(d.n_ctrl, d.degree);
+            auto it = op_index.find(key);
+            if (it == op_index.end()) {
+                // operators of every span, de-duplicated: on clamped uniform
+                // knots all interior spans of one degree share one matrix
+                const int p = d.degree, sq = (p + 1) * (p + 1);
+                const int64_t off = (int64_t)span_ops.size();
+                std::vector<double> M((size_t)sq);
+                for (int k = p; k < d.n_ctrl; ++k) {
+                    span_operator(nullptr, d.n_ctrl, p, k, M.data());
+                    std::vector<long long> mk(1, p);
+                    for (double v : M) mk.push_back(std::llround(v * 1099511627776.0));  // 2^40
+                    auto mt = mat_index.find(mk);
+                    if (mt == mat_index.end()) {
+                        mt = mat_index.emplace(mk, (int64_t)ops.size()).first;
+                        ops.insert(ops.end(), M.begin(), M.end());
+                    }
+                    span_ops.push_back(mt->second);
+                }
+                it = op_index.emplace(key, off).first;
+            }
+            op_off[(size_t)i] = it->second;
         }
     }
     // plan-owned device buffers
@@ -289,15 +355,31 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     };
     alloc((void**)&b->d_desc, (size_t)n_curves * sizeof(bez_curve_desc));
     alloc((void**)&b->d_span_off, (size_t)n_curves * sizeof(int64_t));
-    alloc((void**)&b->d_spline_ids, spline_ids.size() * sizeof(int64_t));
+    alloc((void**)&b->d_ops, ops.size() * sizeof(double));
+    alloc((void**)&b->d_span_ops, span_ops.size() * sizeof(int64_t));
+    alloc((void**)&b->d_op_off, (size_t)n_curves * sizeof(int64_t));
     alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
-    alloc(&b->d_counter, sizeof(unsigned long long));
+    alloc(&b->d_counter, kBatchClasses * sizeof(unsigned long long));
+    // (curve, span) of every span: one setup thread each
+    std::vector<int2> span_tab;
+    for (int64_t i = 0; i < n_curves; ++i) {
+        const bez_curve_desc& d = b->hdesc[(size_t)i];
+        const int n_spans = d.type == BEZ_CURVE_BEZIER ? 1 : d.n_ctrl - d.degree;
+        for (int s = 0; s < n_spans; ++s) span_tab.push_back(make_int2((int)i, s));
+    }
+    alloc((void**)&b->d_span_tab, span_tab.size() * sizeof(int2));
+    if (e == cudaSuccess && !span_tab.empty())
+        e = cudaMemcpy(b->d_span_tab, span_tab.data(), span_tab.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_curves > 0)
         e = cudaMemcpy(b->d_desc, b->hdesc.data(), (size_t)n_curves * sizeof(bez_curve_desc), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_curves > 0)
         e = cudaMemcpy(b->d_span_off, span_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !spline_ids.empty())
-        e = cudaMemcpy(b->d_spline_ids, spline_ids.data(), spline_ids.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ops.empty())
+        e = cudaMemcpy(b->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !span_ops.empty())
+        e = cudaMemcpy(b->d_span_ops, span_ops.data(), span_ops.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_curves > 0)
+        e = cudaMemcpy(b->d_op_off, op_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "batch buffers");
@@ -311,13 +393,18 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     a.out_pool = out_pool;
     a.span_pool = b->d_spans;
     a.span_off = b->d_span_off;
-    a.spline_ids = b->d_spline_ids;
-    a.n_splines = (int64_t)spline_ids.size();
+    a.op_pool = b->d_ops;
+    a.span_ops = b->d_span_ops;
+    a.op_off = b->d_op_off;
+    a.span_tab = b->d_span_tab;
+    a.n_span_tab = (int64_t)span_tab.size();
+    a.repr = -1;  // set by apply_shape, which then runs the setup
     a.counter = b->d_counter;
     b->setup_each = bo ? bo->setup_each_launch != 0 : true;
     b->use_graph = bo ? bo->use_graph != 0 : false;
     char key[160];
-    snprintf(key, sizeof(key), "batch-v1:n%d:dim%d:mix%lld/%lld/%lld:deg%d:s%d", log2_bucket((double)n_curves), dim,
+    snprintf(key, sizeof(key), "batch-v2:setup%d:n%d:dim%d:mix%lld/%lld/%lld:deg%d:s%d", b->setup_each ? 1 : 0,
+             log2_bucket((double)n_curves), dim,
              (long long)(n_curves ? 100 * n_type[0] / n_curves : 0), (long long)(n_curves ? 100 * n_type[1] / n_curves : 0),
              (long long)(n_curves ? 100 * n_type[2] / n_curves : 0), n_curves ? (int)std::lround((double)deg_sum / n_curves) : 0,
              log2_bucket(n_curves ? (double)total_samples / n_curves : 0.0));
@@ -327,21 +414,16 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     if (bo && bo->chunk > 0) sh.chunk = bo->chunk;
     if (bo && (bo->schedule == 0 || bo->schedule == 1)) sh.schedule = bo->schedule;
     if (bo && (bo->threads == 128 || bo->threads == 256)) sh.threads = bo->threads;
+    if (bo && (bo->repr == 0 || bo->repr == 1)) sh.repr = bo->repr;
+    if (bo && bo->chunk > 0 && bo->chunk % 256 != 0) {
+        free_batch(b);
+        return fail(BEZ_ERR_INVALID_ARG, "chunk must be a multiple of 256");
+    }
     if (bo && bo->threads != 0 && bo->threads != 128 && bo->threads != 256) {
         free_batch(b);
         return fail(BEZ_ERR_INVALID_ARG, "threads must be 128 or 256");
     }
     bez_status st = BEZ_OK;
-    // spans must exist before the evaluator runs (autotuning included)
-    if (a.n_splines > 0) {
-        const LaunchHooks h0{no_count, no_event, no_event, nullptr, c->sm_count};
-        int k = 0;
-        st = apply_shape(b, sh, s);
-        if (st == BEZ_OK) {
-            e = launch_batch(a, sh.threads, c->sm_count, true, s, h0, &k);
-            if (e != cudaSuccess) st = cuda_fail(e, "batch setup");
-        }
-    }
     if (st == BEZ_OK) st = (bo && bo->autotune) ? autotune(b, s) : apply_shape(b, sh, s);
     if (st == BEZ_OK && b->use_graph) {
         cudaStream_t cs = nullptr;
@@ -393,9 +475,10 @@ bez_status bez_batch_launch(bez_batch b, void* stream)
     return BEZ_OK;
 }
 
-bez_status bez_batch_config(bez_batch b, int32_t* chunk, int32_t* schedule, int32_t* threads)
+bez_status bez_batch_config(bez_batch b, int32_t* chunk, int32_t* schedule, int32_t* threads, int32_t* repr)
 {
     if (!b) return fail(BEZ_ERR_INVALID_ARG, "null batch");
+    if (repr) *repr = b->shape.repr;
     if (chunk) *chunk = b->shape.chunk;
     if (schedule) *schedule = b->shape.schedule;
     if (threads) *threads = b->shape.threads;
@@ -415,7 +498,7 @@ bez_status bez_eval_batch(bez_ctx c, const bez_curve_desc* desc, int64_t n_curve
                           int64_t ctrl_len, const float* weight_pool, int64_t weight_len, float* out_pool,
                           int64_t out_len, void* stream)
 {
-    bez_batch_opts bo{0, 1, 0, 0, -1, 0};
+    bez_batch_opts bo{0, 1, 0, 0, -1, 0, -1};
     bez_batch b = nullptr;
     bez_status st = bez_batch_create(c, desc, n_curves, dim, ctrl_pool, ctrl_len, weight_pool, weight_len, out_pool,
                                      out_len, &bo, stream, &b);

@@ -153,17 +153,24 @@ struct BatchArgs {
     const float* ctrl_pool;
     const float* weight_pool;
     float* out_pool;
-    float* span_pool;            // Bezier spans of the spline curves
+    float* span_pool;            // every curve's spans in the evaluation representation
     const int64_t* span_off;     // per curve, floats into span_pool
-    const int64_t* spline_ids;   // indices of the spline curves
-    int64_t n_splines;
-    const int2* items;           // (curve, chunk index)
+    const double* op_pool;       // FP64 span extraction operators of the splines
+    const int64_t* op_off;       // per curve, index of its first span in span_ops (splines only)
+    const int64_t* span_ops;     // per spline span: offset of its operator matrix in op_pool
+    const int2* span_tab;        // (curve, span) of every span: one setup thread each
+    int64_t n_span_tab;
+    int32_t repr;                // 0 Bezier points (de Casteljau), 1 power basis about 1/2 (Horner)
+    const int2* items;           // (curve, chunk index), sorted by item class
     int64_t n_items;
+    int64_t class_start[16];     // items of class k: [class_start[k], class_start[k+1])
     int32_t chunk;
     int32_t schedule;            // 0 static round-robin, 1 atomic queue
     int32_t grab;                // items taken per atomic
-    void* counter;               // 8-byte work counter (atomic schedule)
+    void* counter;               // one 8-byte work counter per class (atomic schedule)
 };
+constexpr int kBatchClasses = 15;  // 7 degrees x {integral, rational} for 3D curves + generic
+int batch_item_class(const bez_curve_desc& d, int dim);
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
                          const LaunchHooks& h, int* launches);
 

@@ -36,30 +36,14 @@ __host__ __device__ __forceinline__ double clamped_uniform_knot(int i, int n, in
     return (double)(i - p) / (double)(n - p);
 }
 
-// Bezier points of span k (p <= k < n) of one spline into q[(p+1)*comps]
-// (FP32).  ctrl [n][dim], w [n] or NULL, knots [n+p+1] or NULL.
-__device__ inline void extract_span(const float* ctrl, const float* w, const float* knots, int n, int p, int dim,
-                                    int k, float* q_out)
+// Knot-insertion passes on the p+1 de Boor points of one span, in place
+// (rows of Q, `comps` columns), given the span's local knots s[1..2p].
+// Returns false for an empty span (s_p == s_(p+1)), leaving Q untouched.
+template <int MAXC>
+__host__ __device__ inline bool boehm_span(double (&Q)[kMaxDegree + 1][MAXC], int comps, const double* s, int p)
 {
-    const int comps = w ? dim + 1 : dim;
-    double s[2 * kMaxDegree + 1];   // s[1..2p]
-    for (int j = 1; j <= 2 * p; ++j) {
-        const int i = k - p + j;
-        s[j] = knots ? (double)knots[i] : clamped_uniform_knot(i, n, p);
-    }
     const double a = s[p], b = s[p + 1];
-    double Q[kMaxDegree + 1][5];
-    for (int i = 0; i <= p; ++i) {
-        const int g = k - p + i;
-        const double wi = w ? (double)w[g] : 1.0;
-        for (int q = 0; q < dim; ++q) Q[i][q] = wi * (double)ctrl[g * dim + q];
-        if (w) Q[i][dim] = wi;
-    }
-    if (!(a < b)) {
-        for (int i = 0; i <= p; ++i)
-            for (int q = 0; q < comps; ++q) q_out[i * comps + q] = 0.f;
-        return;
-    }
+    if (!(a < b)) return false;
     for (int l = 1; l <= p - 1; ++l)
         for (int i = 0; i <= p - l; ++i) {
             const double lo = s[i + l], hi = s[p + i + 1];
@@ -74,8 +58,55 @@ __device__ inline void extract_span(const float* ctrl, const float* w, const flo
             const double al = (b - a) / (T - a);
             for (int q = 0; q < comps; ++q) Q[i][q] = Q[i - 1][q] + al * (Q[i][q] - Q[i - 1][q]);
         }
+    return true;
+}
+
+// local knots s[1..2p] = U_(k-p+1)..U_(k+p) of span k
+__host__ __device__ inline void span_knots(const float* knots, int n, int p, int k, double* s)
+{
+    for (int j = 1; j <= 2 * p; ++j) {
+        const int i = k - p + j;
+        s[j] = knots ? (double)knots[i] : clamped_uniform_knot(i, n, p);
+    }
+}
+
+// Bezier points of span k (p <= k < n) of one spline into q[(p+1)*comps]
+// (FP32).  ctrl [n][dim], w [n] or NULL, knots [n+p+1] or NULL.
+__device__ inline void extract_span(const float* ctrl, const float* w, const float* knots, int n, int p, int dim,
+                                    int k, float* q_out)
+{
+    const int comps = w ? dim + 1 : dim;
+    double s[2 * kMaxDegree + 1];   // s[1..2p]
+    span_knots(knots, n, p, k, s);
+    double Q[kMaxDegree + 1][5];
+    for (int i = 0; i <= p; ++i) {
+        const int g = k - p + i;
+        const double wi = w ? (double)w[g] : 1.0;
+        for (int q = 0; q < dim; ++q) Q[i][q] = wi * (double)ctrl[g * dim + q];
+        if (w) Q[i][dim] = wi;
+    }
+    if (!boehm_span<5>(Q, comps, s, p)) {
+        for (int i = 0; i <= p; ++i)
+            for (int q = 0; q < comps; ++q) q_out[i * comps + q] = 0.f;
+        return;
+    }
     for (int i = 0; i <= p; ++i)
         for (int q = 0; q < comps; ++q) q_out[i * comps + q] = (float)Q[i][q];
+}
+
+// Extraction operator of span k of a degree-p spline with n control points:
+// M[i][j] (row-major, (p+1)^2 doubles) maps the de Boor points
+// P_(k-p+j) to the span's Bezier point i.  Knot insertion on unit vectors.
+__host__ __device__ inline void span_operator(const float* knots, int n, int p, int k, double* M)
+{
+    double s[2 * kMaxDegree + 1];
+    span_knots(knots, n, p, k, s);
+    double Q[kMaxDegree + 1][kMaxDegree + 1];
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p; ++j) Q[i][j] = i == j ? 1.0 : 0.0;
+    const bool nonempty = boehm_span<kMaxDegree + 1>(Q, p + 1, s, p);
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p; ++j) M[i * (p + 1) + j] = nonempty ? Q[i][j] : 0.0;
 }
 
 // Span of t on the clamped uniform knots k / ns: the largest k with

@@ -72,13 +72,14 @@ def _desc(w):
                            w["out_off"])
 
 
-@pytest.mark.parametrize("schedule,chunk,threads", [(0, 256, 256), (1, 512, 128), (0, 2048, 128)])
-def test_batch_plan_graph_replay(workload, schedule, chunk, threads):
+@pytest.mark.parametrize("schedule,chunk,threads,repr", [(0, 256, 256, 1), (1, 512, 128, 0), (0, 2048, 128, 1),
+                                                          (1, 1024, 256, 1), (0, 512, 256, 0)])
+def test_batch_plan_graph_replay(workload, schedule, chunk, threads, repr):
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
     w, ref = workload
     ctrl, wts, out = _pools(torch, w)
-    b = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, chunk=chunk, schedule=schedule, threads=threads)
+    b = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, chunk=chunk, schedule=schedule, threads=threads, repr=repr)
     for _ in range(2):
         out.fill_(float("nan"))
         b.launch()
@@ -86,8 +87,32 @@ def test_batch_plan_graph_replay(workload, schedule, chunk, threads):
         got = out.cpu().numpy()
         assert np.isfinite(got).all()
         assert _check_all(got, ref, w) <= FP32_BAR
-    assert b.config() == {"chunk": chunk, "schedule": schedule, "threads": threads}
+    assert b.config() == {"chunk": chunk, "schedule": schedule, "threads": threads, "repr": repr}
     b.close()
+
+
+@pytest.mark.parametrize("dim", [1, 2, 4])
+def test_batch_other_dims(dim):
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez, synth
+    w = synth.batch(n_curves=400, max_samples=300, dim=dim)
+    ref = _reference(w)
+    ctrl, wts, out = _pools(torch, w)
+    for repr in (0, 1):
+        out.fill_(float("nan"))
+        bez.Batch(_desc(w), dim, ctrl, wts, out, repr=repr).launch()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+        # scalar and 2D curves: normalise by the control polygon (secondary normaliser)
+        for c in range(len(w["type"])):
+            ns = int(w["n_samples"][c])
+            if ns == 0:
+                continue
+            g = got[w["out_off"][c]: w["out_off"][c] + ns * dim].reshape(ns, dim)
+            r = ref[w["out_off"][c]: w["out_off"][c] + ns * dim].reshape(ns, dim)
+            cp = w["ctrl_pool"][w["ctrl_off"][c]: w["ctrl_off"][c] + int(w["n_ctrl"][c]) * dim].reshape(-1, dim)
+            scale = max(np.linalg.norm(cp.max(axis=0) - cp.min(axis=0)), 2.0 ** -4)
+            assert np.linalg.norm(g - r, axis=-1).max() / scale <= FP32_BAR
 
 
 def test_batch_autotune_and_static_spans(workload, tmp_path, monkeypatch):
@@ -105,9 +130,9 @@ def test_batch_autotune_and_static_spans(workload, tmp_path, monkeypatch):
     assert _check_all(out.cpu().numpy(), ref, w) <= FP32_BAR
     b.close()
     text = (tmp_path / "tune.json").read_text()
-    assert '"chunk"' in text and "batch-v1" in text
-    # a second plan of the same shape takes the cached choice
-    b2 = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, autotune=True)
+    assert '"chunk"' in text and "batch-v2:setup0" in text
+    # a second plan of the same shape and setup mode takes the cached choice
+    b2 = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, autotune=True, setup_each_launch=False)
     assert b2.config() == cfg
     b2.close()
 
