@@ -400,7 +400,7 @@ def run_batch(args):
 
     from paper_2603_15447_gb300 import bez, synth
     ctx = bez.context(0)
-    w = synth.batch()
+    w = synth.batch(n_curves=args.batch_curves)
     ctrl, wts = torch.from_numpy(w["ctrl_pool"]).cuda(), torch.from_numpy(w["weight_pool"]).cuda()
     out = torch.empty(w["out_len"], device="cuda")
     desc = bez.descriptors(w["type"], w["degree"], w["n_ctrl"], w["n_samples"], w["ctrl_off"], w["weight_off"],
@@ -538,6 +538,7 @@ def main():
     ap.add_argument("--n-chains", type=int, default=16384)
     ap.add_argument("--chain-t", type=int, default=65536)
     ap.add_argument("--skip-chains", action="store_true")
+    ap.add_argument("--batch-curves", type=int, default=262144)
     ap.add_argument("--accuracy-curves", type=int, default=4096)
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -73,10 +73,15 @@ __global__ void __launch_bounds__(kTensorThreads) k_surface_bicubic3(const Tenso
     const int quads_per_row = nv / 4;
     const int n_quads = nu * quads_per_row;
     const int64_t pts = (int64_t)nu * nv;
+    // the next patch's control points are loaded while the current one is
+    // evaluated and stored
+    float nxt = (tid < 48 && (int64_t)blockIdx.x < a.n) ? load_elem(a.ctrl, a.dtype, (int64_t)blockIdx.x * 48 + tid) : 0.f;
     for (int64_t p = blockIdx.x; p < a.n; p += gridDim.x) {
         __syncthreads();  // tables ready / previous patch done with s_c, s_x
-        if (tid < 48) s_c[tid] = load_elem(a.ctrl, a.dtype, p * 48 + tid);
+        if (tid < 48) s_c[tid] = nxt;
         __syncthreads();
+        const int64_t pn = p + gridDim.x;
+        if (tid < 48 && pn < a.n) nxt = load_elem(a.ctrl, a.dtype, pn * 48 + tid);
         for (int e = tid; e < nu * 12; e += kTensorThreads) {
             const int row = e / 12, jk = e - row * 12;
             const float* bu = s_bu + row * 4;
@@ -204,13 +209,31 @@ __global__ void __launch_bounds__(kTensorThreads) k_volume(const TensorArgs a)
         __syncthreads();
         float* out = a.out + p * pts * dim;
         const int line = nw * dim;
-        for (int e = tid; e < nu * nv * line; e += kTensorThreads) {
-            // consecutive threads write consecutive floats of the volume
-            const int ab = e / line, ck = e - ab * line;
-            const int c = ck / dim, k = ck - c * dim;
-            float v = 0.f;
-            for (int l = 0; l <= dw; ++l) v = fmaf(s_bw[c * (dw + 1) + l], s_z[ab * lk + l * dim + k], v);
-            out[e] = v;
+        if (line % 4 == 0 && (((uintptr_t)out) & 15) == 0) {
+            // one thread per (a, b) line: its nw * dim values as float4 stores
+            for (int ab = tid; ab < nu * nv; ab += kTensorThreads) {
+                float4* o = reinterpret_cast<float4*>(out + (int64_t)ab * line);
+                const float* z = s_z + ab * lk;
+                for (int f4 = 0; f4 < line / 4; ++f4) {
+                    float r[4];
+                    for (int m = 0; m < 4; ++m) {
+                        const int ck = f4 * 4 + m, c = ck / dim, k = ck - c * dim;
+                        float v = 0.f;
+                        for (int l = 0; l <= dw; ++l) v = fmaf(s_bw[c * (dw + 1) + l], z[l * dim + k], v);
+                        r[m] = v;
+                    }
+                    o[f4] = make_float4(r[0], r[1], r[2], r[3]);
+                }
+            }
+        } else {
+            for (int e = tid; e < nu * nv * line; e += kTensorThreads) {
+                // consecutive threads write consecutive floats of the volume
+                const int ab = e / line, ck = e - ab * line;
+                const int c = ck / dim, k = ck - c * dim;
+                float v = 0.f;
+                for (int l = 0; l <= dw; ++l) v = fmaf(s_bw[c * (dw + 1) + l], s_z[ab * lk + l * dim + k], v);
+                out[e] = v;
+            }
         }
     }
 }
