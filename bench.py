@@ -39,14 +39,20 @@ sys.path.insert(0, ROOT)
 METRIC = "curve points evaluated/sec vs FP32 Horner on same GB300, at max err vs FP64 oracle"
 N_CURVES = 1 << 20
 N_T = 1024
-WORKLOAD = ("precision/texture: 1,048,576 cubic 3D Bezier curves (U[-1,1]^3 FP32), 1024 parameters per curve "
+
+
+def workload_name(n_curves=N_CURVES, n_t=N_T):
+    return (f"precision/texture: {n_curves:,} cubic 3D Bezier curves (U[-1,1]^3 FP32), {n_t} parameters per curve "
             "drawn U[0,1) in-kernel, fused per-curve polyline length (no point stores)")
 
 # Algorithmic lane operations per point (cubic, 3D):
-# parameter draw 12 (xor, lowbias32 = 3 shift + 3 xor + 2 mul, funnel shift,
-# subtract) + evaluation + polyline step 8 (3 sub, mul + 2 fma, sqrt, add).
-T_OPS, LEN_OPS = 12, 8
-EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 10, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
+# parameter draw 9 (xor of the sample index into the curve key, whose first
+# lowbias32 shift-xor is applied once per curve since the index is < 2^16;
+# 2 mul + 2 shift + 2 xor; funnel shift; subtract) + evaluation + polyline
+# step 8 (3 sub, mul + 2 fma, sqrt, add).  The centred form folds its shift by
+# 1/2 into the draw's subtraction, so it evaluates in 9 fma like Horner.
+T_OPS, LEN_OPS = 9, 8
+EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
             "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
 # filtered fetches per point and the peak they are held to
 TEX_FETCHES = {"TEX_DECASTELJAU": (1, "tex3d_f32"), "TEX_SEILER": (1, "tex2d_f32"), "TEX_HYBRID": (2, "tex2d_f32")}
@@ -314,7 +320,7 @@ def run_precision(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": args.variant, "n_curves": args.n_curves, "n_t": args.n_t,
+        "config": {"workload": workload_name(args.n_curves, args.n_t), "variant": args.variant, "n_curves": args.n_curves, "n_t": args.n_t,
                    "degree": 3, "dim": 3, "l2": "flushed between timed steps (256 MiB device write)",
                    "speedup_vs_horner": head["speedup_vs_horner"],
                    "max_norm_err": head.get("max_norm_err")},
@@ -516,7 +522,7 @@ def run_reference(args, rank):
     return {"metric": METRIC, "value": v, "unit": "points/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample_curves_per_step": args.ref_curves, "n_t": args.n_t},
+            "config": {"workload": workload_name(args.n_curves, args.n_t), "sample_curves_per_step": args.ref_curves, "n_t": args.n_t},
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": threads, "kind": "oracle",
                              "sample": f"{args.ref_curves} curves x {args.n_t} parameters per step"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -13,7 +13,9 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // parameter-stream kinds as seen by kernels (the C enum's SHARED / PER_CURVE
 // both become TM_ARRAY with a per-curve stride of 0 or n_t)
-enum { TM_ARRAY = 0, TM_UNIFORM = 1, TM_HASH = 2 };
+// TM_HASH16: the same draw as TM_HASH when every sample index is < 2^16, with
+// the per-curve key pre-mixed (lowbias32_premixed).
+enum { TM_ARRAY = 0, TM_UNIFORM = 1, TM_HASH = 2, TM_HASH16 = 3 };
 enum { OM_POINTS = 0, OM_LENGTH = 1 };
 enum { VAR_HORNER = 1, VAR_HORNER_CENTRED = 2, VAR_BERNSTEIN = 3, VAR_DECASTELJAU = 4, VAR_SEILER = 5 };
 
@@ -33,11 +35,30 @@ __host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x)
     return x;
 }
 
+// lowbias32(k ^ j) for j < 2^16, given km = k ^ (k >> 16): the first
+// xorshift distributes over the xor and j >> 16 == 0, so
+// (k ^ j) ^ ((k ^ j) >> 16) == km ^ j.  Same value, two instructions fewer.
+__device__ __forceinline__ uint32_t lowbias32_premixed(uint32_t km, uint32_t j)
+{
+    uint32_t x = km ^ j;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// 1 + (23 high bits of h) 2^-23, in [1,2): (0x7f : h) >> 9 == 0x3f800000 | (h >> 9),
+// so one funnel shift builds the float 1.m
+__device__ __forceinline__ float hash_one_plus(uint32_t h)
+{
+    return __uint_as_float(__funnelshift_r(h, 0x7fu, 9));
+}
+
 // 23 high bits of h as a uniform in [0,1): 1.m - 1 is exact in FP32.
 __device__ __forceinline__ float hash_unit(uint32_t h)
 {
-    // (0x7f : h) >> 9 == 0x3f800000 | (h >> 9): one funnel shift builds 1.m
-    return __uint_as_float(__funnelshift_r(h, 0x7fu, 9)) - 1.0f;
+    return hash_one_plus(h) - 1.0f;
 }
 
 // a + t (b - a) written as (a - t a) + t b: exact at t = 0 and t = 1, and

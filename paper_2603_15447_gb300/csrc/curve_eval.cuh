@@ -143,9 +143,10 @@ struct Eval<VAR_HORNER_CENTRED, D, DIM> {
         if (d >= kFp64SetupCentred) setup_t<double>(b);
         else setup_t<float>(b);
     }
-    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const
+    __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const { eval_u(t - 0.5f, P); }
+    // evaluate at u = t - 1/2
+    __device__ __forceinline__ void eval_u(float u, float (&P)[DIM]) const
     {
-        const float u = t - 0.5f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             float acc = a[N - 1][k];
@@ -448,13 +449,24 @@ struct Pick<VAR, 0, DIM> {
 // ---------------------------------------------------------------- kernel
 
 constexpr int kWarps = 8;  // warps per block; one curve per warp per iteration
+constexpr int kCurvesPerWarp = 8;  // curves per warp when the grid is not persistent
 
 template <int TM>
 __device__ __forceinline__ float param(const CurveArgs& a, int64_t c, int j, uint32_t kc)
 {
     if (TM == TM_ARRAY) return clamp01(__ldg(a.t + c * a.t_stride + j));
     if (TM == TM_UNIFORM) return a.n_t > 1 ? __fdiv_rn((float)j, (float)(a.n_t - 1)) : 0.f;
+    if (TM == TM_HASH16) return hash_unit(lowbias32_premixed(kc, (uint32_t)j));
     return hash_unit(lowbias32(kc ^ (uint32_t)j));
+}
+
+// per-curve key of the in-kernel draw (pre-mixed for TM_HASH16)
+template <int TM>
+__device__ __forceinline__ uint32_t curve_key(const CurveArgs& a, int64_t c)
+{
+    if (TM != TM_HASH && TM != TM_HASH16) return 0u;
+    const uint32_t kc = lowbias32(a.key ^ (uint32_t)c);
+    return TM == TM_HASH16 ? kc ^ (kc >> 16) : kc;
 }
 
 template <int DIM>
@@ -467,6 +479,79 @@ __device__ __forceinline__ float seg_len(const float (&p)[DIM], const float (&q)
         s = fmaf(e, e, s);
     }
     return sqrt_approx(s);
+}
+
+// Evaluate at the pre-mixed draw of sample index x = kg ^ i (TM_HASH16).  The
+// centred form takes u = 1.m - 3/2 in one subtraction: 1.m - 1 and then - 1/2
+// are both exact, so the value is the same as eval(t).
+template <class E>
+struct DrawEval {
+    template <int DIM>
+    __device__ __forceinline__ static void at(const E& e, uint32_t x, float (&P)[DIM])
+    {
+        e.eval(hash_one_plus(lowbias32_premixed(x, 0u)) - 1.0f, P);
+    }
+};
+template <int D, int DIM0>
+struct DrawEval<Eval<VAR_HORNER_CENTRED, D, DIM0>> {
+    template <int DIM>
+    __device__ __forceinline__ static void at(const Eval<VAR_HORNER_CENTRED, D, DIM0>& e, uint32_t x,
+                                              float (&P)[DIM])
+    {
+        e.eval_u(hash_one_plus(lowbias32_premixed(x, 0u)) - 1.5f, P);
+    }
+};
+
+// Polyline length over the samples [jb, je) of one lane with the pre-mixed
+// draw.  jb is a multiple of 4, so sample jb + i (i < 4) has index
+// (jb + i) == (g ^ i) for its group start g and km ^ (g ^ i) == (km ^ g) ^ i:
+// one xor per sample gives the draw's input.  `first` and `last` return the
+// run's end points for the join with the neighbouring lanes.
+template <class E, int DIM>
+__device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb, int je, float (&first)[DIM],
+                                                float (&last)[DIM])
+{
+    float acc = 0.f;
+    const uint32_t k0 = km ^ (uint32_t)jb;
+    DrawEval<E>::at(e, k0, first);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) last[k] = first[k];
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+        if (jb + i < je) {
+            float P[DIM];
+            DrawEval<E>::at(e, k0 ^ (uint32_t)i, P);
+            acc += seg_len<DIM>(P, last);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) last[k] = P[k];
+        }
+    }
+    int g = jb + 4;
+    for (; g + 4 <= je; g += 4) {
+        const uint32_t kg = km ^ (uint32_t)g;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float P[DIM];
+            DrawEval<E>::at(e, kg ^ (uint32_t)i, P);
+            acc += seg_len<DIM>(P, last);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) last[k] = P[k];
+        }
+    }
+    if (g < je) {
+        const uint32_t kg = km ^ (uint32_t)g;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (g + i < je) {
+                float P[DIM];
+                DrawEval<E>::at(e, kg ^ (uint32_t)i, P);
+                acc += seg_len<DIM>(P, last);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) last[k] = P[k];
+            }
+        }
+    }
+    return acc;
 }
 
 // Warp-per-curve kernel.  Warps are independent (no block barrier): each
@@ -522,7 +607,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_curve(const CurveArgs a)
         cur.load(a, c + n_warps, per, lane);   // prefetch the next curve of this warp
         E e;
         e.setup(b, deg);
-        const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
+        const uint32_t kc = curve_key<TM>(a, c);
         const int n_t = a.n_t;
 
         if (OM == OM_POINTS) {
@@ -548,14 +633,17 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_curve(const CurveArgs a)
         } else {
             // each lane walks a contiguous run of samples; the segment
             // joining two runs is closed with one shuffle
-            const int chunk = (n_t + 31) / 32;
+            // (runs of a multiple of 4 samples under the pre-mixed draw)
+            const int chunk = TM == TM_HASH16 ? (((n_t + 31) / 32 + 3) & ~3) : (n_t + 31) / 32;
             const int jb = lane * chunk;
             const int je = min(jb + chunk, n_t);
             float acc = 0.f;
             float first[DIM], prev[DIM];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) first[k] = prev[k] = 0.f;
-            if (jb < je) {
+            if (TM == TM_HASH16) {
+                if (jb < je) acc = run_length_h16<E, DIM>(e, kc, jb, je, first, prev);
+            } else if (jb < je) {
                 e.eval(param<TM>(a, c, jb, kc), first);
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) prev[k] = first[k];
@@ -585,7 +673,16 @@ LaunchResult launch_one(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h
 {
     auto kern = k_curve<VAR, D, DIM, TM, OM>;
     const int64_t work = (a.n_curves + kWarps - 1) / kWarps;
-    const int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    if (work > grid) {
+        // More curves than resident warps: launch blocks of kCurvesPerWarp
+        // curves per warp instead of a persistent grid.  The block scheduler
+        // then refills SMs whose warps finish first.  With a persistent grid
+        // every warp has a fixed share, warps progress unevenly, and 131,072
+        // cubics averaged 32 of the 48 resident warps per SM.
+        const int64_t g = (a.n_curves + (int64_t)kWarps * kCurvesPerWarp - 1) / ((int64_t)kWarps * kCurvesPerWarp);
+        if (g > grid) grid = (int)(g < 2147483647 ? g : 2147483647);
+    }
     h.count(h.self);
     h.begin(h.self, s);
     kern<<<grid, kWarps * 32, 0, s>>>(a);
@@ -604,6 +701,9 @@ LaunchResult launch_modes(const CurveArgs& a, int tm, int om, cudaStream_t s, co
     }
     if (tm == TM_ARRAY) return launch_one<VAR, D, DIM, TM_ARRAY, OM_LENGTH>(a, s, h);
     if (tm == TM_UNIFORM) return launch_one<VAR, D, DIM, TM_UNIFORM, OM_LENGTH>(a, s, h);
+    // the fused evaluate-and-measure form of 3D curves of fixed degree gets the
+    // pre-mixed draw when every sample index fits 16 bits
+    if (D > 0 && DIM == 3 && a.n_t <= 65536) return launch_one<VAR, D, DIM, (D > 0 && DIM == 3 ? TM_HASH16 : TM_HASH), OM_LENGTH>(a, s, h);
     return launch_one<VAR, D, DIM, TM_HASH, OM_LENGTH>(a, s, h);
 }
 

@@ -118,6 +118,94 @@ __global__ void __launch_bounds__(kTensorThreads) k_surface_bicubic3(const Tenso
     }
 }
 
+// Fast path for small grids (nu <= 64, nv a multiple of 4): one warp per
+// patch, no block barrier after the tables.  Lane l builds the isoline
+// control points X[a] of rows a = l, l + 32 (12 floats each), then the warp
+// sweeps the grid one row of up to 32 points at a time: lane l evaluates
+// point (a, b0 + l) with Bv[b0 + l] held in registers, stages its 3 floats in
+// a warp-private buffer and 24 lanes write the 384-byte row segment as float4.
+constexpr int kSurfWarps = 8;
+constexpr int kSurfMaxRows = 64;
+
+__global__ void __launch_bounds__(kSurfWarps * 32, 5) k_surface_bicubic3_warp(const TensorArgs a)
+{
+    __shared__ float4 s_bv[kTensorMaxGrid];                   // Bv[b][0..3]
+    __shared__ float4 s_bu[kSurfMaxRows];                     // Bu[a][0..3]
+    __shared__ float4 s_x[kSurfWarps][kSurfMaxRows * 3];      // X[a][j][k], 12 floats per row
+    __shared__ float4 s_st[kSurfWarps][2][24];                // 32 points x 3 floats, two buffers
+    __shared__ float4 s_c4[kSurfWarps][12];                   // C[i][j][k]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    bernstein_table(reinterpret_cast<float*>(s_bu), a.nu, 3, tid, kSurfWarps * 32);
+    bernstein_table(reinterpret_cast<float*>(s_bv), a.nv, 3, tid, kSurfWarps * 32);
+    __syncthreads();
+
+    const int nu = a.nu, nv = a.nv;
+    const int64_t pts = (int64_t)nu * nv;
+    const int64_t stride = (int64_t)gridDim.x * kSurfWarps;
+    int64_t p = (int64_t)blockIdx.x * kSurfWarps + w;
+    float c0 = 0.f, c1 = 0.f;   // this lane's control-point elements, l and 32 + l
+    if (p < a.n) {
+        c0 = load_elem(a.ctrl, a.dtype, p * 48 + lane);
+        if (lane < 16) c1 = load_elem(a.ctrl, a.dtype, p * 48 + 32 + lane);
+    }
+    float* cw = reinterpret_cast<float*>(s_c4[w]);
+    int buf = 0;
+    for (; p < a.n; p += stride) {
+        __syncwarp();  // the previous patch is done with s_c and s_x
+        cw[lane] = c0;
+        if (lane < 16) cw[32 + lane] = c1;
+        __syncwarp();
+        const int64_t pn = p + stride;  // the next patch of this warp, loaded while this one runs
+        if (pn < a.n) {
+            c0 = load_elem(a.ctrl, a.dtype, pn * 48 + lane);
+            if (lane < 16) c1 = load_elem(a.ctrl, a.dtype, pn * 48 + 32 + lane);
+        }
+        const float4* cw4 = reinterpret_cast<const float4*>(cw);   // C[i][4q..4q+3] = cw4[3 i + q]
+#pragma unroll 1
+        for (int q = 0; q < 3; ++q) {   // columns 4q..4q+3 of the 12 per row
+            const float4 k0 = cw4[q], k1 = cw4[3 + q], k2 = cw4[6 + q], k3 = cw4[9 + q];
+            for (int row = lane; row < nu; row += 32) {
+                const float4 bu = s_bu[row];
+                float4 x;
+                x.x = fmaf(bu.w, k3.x, fmaf(bu.z, k2.x, fmaf(bu.y, k1.x, bu.x * k0.x)));
+                x.y = fmaf(bu.w, k3.y, fmaf(bu.z, k2.y, fmaf(bu.y, k1.y, bu.x * k0.y)));
+                x.z = fmaf(bu.w, k3.z, fmaf(bu.z, k2.z, fmaf(bu.y, k1.z, bu.x * k0.z)));
+                x.w = fmaf(bu.w, k3.w, fmaf(bu.z, k2.w, fmaf(bu.y, k1.w, bu.x * k0.w)));
+                s_x[w][row * 3 + q] = x;
+            }
+        }
+        __syncwarp();
+        float4* out = reinterpret_cast<float4*>(a.out + p * pts * 3);
+        for (int b0 = 0; b0 < nv; b0 += 32) {
+            const int b = b0 + lane;
+            const float4 bv = b < nv ? s_bv[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int nvec = min(32, nv - b0) * 3 / 4;   // float4 per row segment
+#pragma unroll 2
+            for (int row = 0; row < nu; ++row) {
+                const float4 x0 = s_x[w][row * 3], x1 = s_x[w][row * 3 + 1], x2 = s_x[w][row * 3 + 2];
+                // X[row][j][k] sits at float 3 j + k of the row
+                float P0 = bv.x * x0.x, P1 = bv.x * x0.y, P2 = bv.x * x0.z;
+                P0 = fmaf(bv.y, x0.w, P0);
+                P1 = fmaf(bv.y, x1.x, P1);
+                P2 = fmaf(bv.y, x1.y, P2);
+                P0 = fmaf(bv.z, x1.z, P0);
+                P1 = fmaf(bv.z, x1.w, P1);
+                P2 = fmaf(bv.z, x2.x, P2);
+                P0 = fmaf(bv.w, x2.y, P0);
+                P1 = fmaf(bv.w, x2.z, P1);
+                P2 = fmaf(bv.w, x2.w, P2);
+                float* st = reinterpret_cast<float*>(s_st[w][buf]);
+                st[lane * 3 + 0] = P0;
+                st[lane * 3 + 1] = P1;
+                st[lane * 3 + 2] = P2;
+                __syncwarp();
+                if (lane < nvec) out[((int64_t)row * nv + b0) * 3 / 4 + lane] = s_st[w][buf][lane];
+                buf ^= 1;   // the next row stages in the other buffer, so no second barrier
+            }
+        }
+    }
+}
+
 // General surfaces: any degrees <= 7, dim 1..4, grid <= 256 per axis.  One
 // thread per output point (strided), outputs staged in shared memory and
 // written as consecutive floats.
@@ -275,7 +363,15 @@ LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const 
     const TensorArgs a = to_args(t);
     const void* kern;
     size_t smem = 0;
-    if (a.dw < 0 && a.du == 3 && a.dv == 3 && a.dim == 3 && a.nv % 4 == 0 && ((uintptr_t)a.out & 15) == 0) {
+    int threads = kTensorThreads;
+    int64_t work = a.n;
+    const bool bicubic3 = a.dw < 0 && a.du == 3 && a.dv == 3 && a.dim == 3 && a.nv % 4 == 0 &&
+                          ((uintptr_t)a.out & 15) == 0;
+    if (bicubic3 && a.nu <= kSurfMaxRows) {
+        kern = (const void*)k_surface_bicubic3_warp;
+        threads = kSurfWarps * 32;
+        work = (a.n + kSurfWarps - 1) / kSurfWarps;
+    } else if (bicubic3) {
         kern = (const void*)k_surface_bicubic3;
     } else {
         kern = a.dw < 0 ? (const void*)k_surface_generic : (const void*)k_volume;
@@ -285,11 +381,11 @@ LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const 
             if (e != cudaSuccess) return {0, e};
         }
     }
-    const int grid = persistent_grid(kern, kTensorThreads, smem, h.sm_count, a.n);
+    const int grid = persistent_grid(kern, threads, smem, h.sm_count, work);
     void* args[] = {(void*)&a};
     h.count(h.self);
     h.begin(h.self, s);
-    cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(kTensorThreads), args, smem, s);
+    cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, smem, s);
     h.end(h.self, s);
     return {1, e};
 }

@@ -171,6 +171,23 @@ def test_polyline_length_hash(variant):
     assert np.all(np.abs(got - L) <= tol)
 
 
+@pytest.mark.parametrize("n_t", [3, 5, 127, 65536, 65537])
+def test_polyline_length_hash_index_width(n_t):
+    # up to 2^16 samples the draw uses the pre-mixed curve key and runs of a
+    # multiple of 4 samples per lane; above that the plain key; both give the
+    # oracle's draw
+    torch = need_gpu()
+    rng = np.random.default_rng(4000 + n_t)
+    n = 5
+    ctrl = _ctrl(rng, n, 3, 3)
+    got = _run(torch, ctrl, n_t=n_t, variant="HORNER_CENTRED", out_mode="POLYLINE_LENGTH", t_mode="HASH",
+               seed=99, stream_id=7)
+    th = oracle.hash_t(99, 7, 0, n, n_t)
+    pts = oracle.bezier(ctrl, th)
+    L = oracle.polyline_length(pts)
+    assert np.all(np.abs(got - L) <= _length_tol(pts, L, n_t))
+
+
 @pytest.mark.parametrize("n_t", [0, 1, 2, 31, 33, 100])
 def test_polyline_length_edge_sizes(n_t):
     torch = need_gpu()

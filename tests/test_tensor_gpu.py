@@ -41,6 +41,21 @@ def test_bicubic_fast_path():
     np.testing.assert_array_equal(got[:, -1, -1], ctrl[:, -1, -1])
 
 
+@pytest.mark.parametrize("nu,nv", [(1, 4), (5, 20), (33, 36), (64, 256), (65, 8), (200, 40)])
+def test_bicubic_grid_shapes(nu, nv):
+    # nu <= 64 takes the warp-per-patch kernel (ragged 32-point row segments
+    # when nv is not a multiple of 32), larger nu the block-per-patch kernel
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(nu * 1000 + nv)
+    ctrl = rng.uniform(-1, 1, (37, 4, 4, 3)).astype(np.float32)
+    got = bez.bez_eval_surface(torch.from_numpy(ctrl).cuda(), nu, nv).cpu().numpy()
+    ref = oracle.surface(ctrl, nu, nv)
+    assert got.shape == ref.shape
+    assert _err_ctrl(got, ref, ctrl).max() <= FP32_BAR
+    np.testing.assert_array_equal(got[:, 0, 0], ctrl[:, 0, 0])
+
+
 @pytest.mark.parametrize("du,dv,dim,nu,nv", [(3, 3, 3, 17, 9), (1, 2, 3, 5, 7), (4, 2, 2, 33, 12), (7, 5, 4, 8, 8),
                                              (3, 3, 1, 32, 32), (2, 6, 3, 1, 1)])
 def test_generic_surfaces(du, dv, dim, nu, nv):
