@@ -52,6 +52,14 @@ def workload_name(n_curves=N_CURVES, n_t=N_T):
 # step 8 (3 sub, mul + 2 fma, sqrt, add).  The centred form folds its shift by
 # 1/2 into the draw's subtraction, so it evaluates in 9 fma like Horner.
 T_OPS, LEN_OPS = 9, 8
+
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels, per unit of work; null in the JSON line for other kernels.  The
+# curve kernel was captured on 131,072 curves (6,305,280 B: the control
+# points; the 4 B lengths stay in L2) and scales with the curve count; the
+# surface kernel on the full 65,536-patch tensor workload.
+TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6305280 / 131072}
+TRAFFIC_SURFACE_65536 = 12626688 + 743121664
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
             "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
 # filtered fetches per point and the peak they are held to
@@ -209,9 +217,9 @@ def run_precision(args, rank, world, local_rank):
     timer = Timer(torch, ctx, dev, world)
     ts = synth.PRECISION_T_STREAM
 
-    def step_for(v):
+    def step_for(v, c=ctrl):
         def step():
-            bez.bez_eval(ctrl, None, n_t=args.n_t, variant=bez.Variant[v], out_mode=bez.OutMode.POLYLINE_LENGTH,
+            bez.bez_eval(c, None, n_t=args.n_t, variant=bez.Variant[v], out_mode=bez.OutMode.POLYLINE_LENGTH,
                          t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, out=out, ctx=ctx)
         return step
 
@@ -220,10 +228,17 @@ def run_precision(args, rank, world, local_rank):
         if must not in run_variants:
             run_variants.append(must)
     results = {}
+    results16 = {}
+    ctrl16 = None if args.skip_f16 else ctrl.half()
     with ClockSampler(local_rank) as clocks:
         for v in run_variants:
             ms, st = timer.run(step_for(v), args.steps, args.warmup)
             results[v] = {"ms": ms, "stats": st}
+        if ctrl16 is not None:
+            # half storage (half4 texture atlases), FP32 arithmetic
+            for v in run_variants:
+                ms, st = timer.run(step_for(v, ctrl16), args.steps, args.warmup)
+                results16[v] = {"ms": ms, "stats": st}
     clock_summary = clocks.summary()
 
     # chain part of the workload: register de Casteljau vs zig-zag texture
@@ -286,6 +301,19 @@ def run_precision(args, rank, world, local_rank):
     horner = variants["HORNER"]["points_per_s"]
     for v in run_variants:
         variants[v]["speedup_vs_horner"] = variants[v]["points_per_s"] / horner
+    variants16 = {}
+    for v, r in results16.items():
+        st = r["stats"]
+        kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
+        row = {"points_per_s": pts_step * args.steps / (r["ms"] * 1e-3), "kernel_ms": kern_ms}
+        row["speedup_vs_horner"] = row["points_per_s"] / horner
+        if v in TEX_FETCHES:
+            nf, kind = TEX_FETCHES[v]
+            kind = kind.replace("f32", "f16")
+            row["fetches_per_s"] = nf * pts_step / (kern_ms * 1e-3)
+            row["tex_frac"] = row["fetches_per_s"] / peaks[kind]
+            row["tex_peak"] = kind
+        variants16[v] = row
 
     if not args.skip_accuracy:
         import oracle
@@ -302,8 +330,17 @@ def run_precision(args, rank, world, local_rank):
             variants[v]["max_norm_err"] = float(err.max())
             variants[v]["bar"] = bar
             variants[v]["meets_bar"] = bool(err.max() <= bar)
+            if v in variants16:
+                # against the oracle of the FP32 control points: includes the 2^-11 storage rounding
+                pts = bez.bez_eval(sample.half(), None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
+                                   seed=seed, stream_id=ts, ctx=ctx)
+                err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
+                variants16[v]["max_norm_err"] = float(err.max())
 
     head = variants[args.variant]
+    traffic = args.traffic
+    if traffic is None and args.variant in TRAFFIC_PER_CURVE:
+        traffic = TRAFFIC_PER_CURVE[args.variant] * args.n_curves
     kern_ms = head["kernel_ms"]
     ops_launch = head["ops_per_point"] * pts_step
     achieved = ops_launch / (kern_ms * 1e-3)
@@ -325,7 +362,7 @@ def run_precision(args, rank, world, local_rank):
                    "speedup_vs_horner": head["speedup_vs_horner"],
                    "max_norm_err": head.get("max_norm_err")},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_alu / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_alu, "traffic": args.traffic, "peak_source": peak_note,
+                     "frac": achieved / peak_alu, "traffic": traffic, "peak_source": peak_note,
                      "ops_per_launch": ops_launch, "kernel": "k_curve (fused draw + eval + polyline length)",
                      "measured_fma_peak_tops": peaks["fma"] / 1e12},
         "e2e": {"value": pts_step / e2e_s, "unit": "points/s",
@@ -333,6 +370,7 @@ def run_precision(args, rank, world, local_rank):
         "gpu_launches": int(results[args.variant]["stats"]["launches"]),
         "clocks": clock_summary,
         "variants": variants,
+        "variants_f16_storage": variants16 or None,
         "peaks_measured": {"fma_tops": peaks["fma"] / 1e12,
                            **{k + "_gfetch_s": peaks[k] / 1e9 for k in peaks if k.startswith("tex")}},
     }
@@ -367,14 +405,14 @@ def cpu_baseline(ctrl_np, seed, n_t, seconds):
 
 # ------------------------------------------------------------------ other workloads
 
-def _hbm_line(name, value, unit, steps, warmup, ms, bytes_step, kern_ms, kernel, extra):
+def _hbm_line(name, value, unit, steps, warmup, ms, bytes_step, kern_ms, kernel, extra, traffic=None):
     peak, note = hbm_peak(load_peaks())
     achieved = bytes_step / (kern_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic", "config": {"workload": name},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": note, "bytes_per_launch": bytes_step, "kernel": kernel}}
+                         "traffic": traffic, "peak_source": note, "bytes_per_launch": bytes_step, "kernel": kernel}}
     line.update(extra)
     return line
 
@@ -449,10 +487,11 @@ def run_tensor(args):
     kv = st_v["timed_ms"] / st_v["timed_launches"]
     return _hbm_line("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
                      (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
-                     ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3",
+                     ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3_warp",
                      {"surface_points_per_s": n_s * args.steps / (ms_s * 1e-3),
                       "volume_values_per_s": n_v * args.steps / (ms_v * 1e-3), "volume_kernel_ms": kv,
-                      "volume_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9})
+                      "volume_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9},
+                     traffic=TRAFFIC_SURFACE_65536)
 
 
 def run_fit(args):
@@ -547,6 +586,7 @@ def main():
     ap.add_argument("--batch-curves", type=int, default=262144)
     ap.add_argument("--accuracy-curves", type=int, default=4096)
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-f16", action="store_true", help="skip the half-storage variant table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-curves", type=int, default=16384)
