@@ -239,6 +239,22 @@ def run_precision(args, rank, world, local_rank):
             for v in run_variants:
                 ms, st = timer.run(step_for(v, ctrl16), args.steps, args.warmup)
                 results16[v] = {"ms": ms, "stats": st}
+        # co-issue: `share` of every 8 samples through the texture unit, the
+        # rest on the FP32 pipes, in one kernel
+        coissue = {}
+        if not args.skip_coissue:
+            for label, c in (("f32", ctrl), ("f16", ctrl16)):
+                if c is None:
+                    continue
+                for share in range(1, 8):
+                    def cstep(c=c, share=share):
+                        bez.bez_eval(c, None, n_t=args.n_t, variant=bez.Variant.COISSUE,
+                                     out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed,
+                                     stream_id=ts, out=out, ctx=ctx, tex_share=share)
+                    ms, st = timer.run(cstep, args.steps, args.warmup)
+                    coissue[f"{label}_share{share}of8"] = {
+                        "points_per_s": args.n_curves * args.n_t * args.steps / (ms * 1e-3),
+                        "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
     clock_summary = clocks.summary()
 
     # chain part of the workload: register de Casteljau vs zig-zag texture
@@ -337,6 +353,18 @@ def run_precision(args, rank, world, local_rank):
                 err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
                 variants16[v]["max_norm_err"] = float(err.max())
 
+    if not args.skip_accuracy and coissue:
+        # lengths of the accuracy sample against the oracle's FP64 lengths
+        import oracle
+        ns = args.accuracy_curves
+        L = oracle.hashed_bezier_polyline_length(ctrl_np[:ns], args.n_t, seed, ts)
+        for key in coissue:
+            c = (ctrl if key.startswith("f32") else ctrl16)[:ns].contiguous()
+            share = int(key.split("share")[1][0])
+            got = bez.bez_eval(c, None, n_t=args.n_t, variant=bez.Variant.COISSUE, out_mode=bez.OutMode.POLYLINE_LENGTH,
+                               t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, ctx=ctx, tex_share=share)
+            coissue[key]["max_rel_length_err"] = float(np.max(np.abs(got.cpu().numpy() - L) / L))
+
     head = variants[args.variant]
     traffic = args.traffic
     if traffic is None and args.variant in TRAFFIC_PER_CURVE:
@@ -371,6 +399,7 @@ def run_precision(args, rank, world, local_rank):
         "clocks": clock_summary,
         "variants": variants,
         "variants_f16_storage": variants16 or None,
+        "coissue": coissue or None,
         "peaks_measured": {"fma_tops": peaks["fma"] / 1e12,
                            **{k + "_gfetch_s": peaks[k] / 1e9 for k in peaks if k.startswith("tex")}},
     }
@@ -482,15 +511,33 @@ def run_tensor(args):
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
     ms_s, st_s = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, out=so, ctx=ctx), args.steps, args.warmup)
     ms_v, st_v = timer.run(lambda: bez.bez_eval_volume(v, 16, 16, 16, out=vo, ctx=ctx), args.steps, args.warmup)
+    tex = bez.Variant.TEX_DECASTELJAU
+    ms_t, st_t = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=tex, out=so, ctx=ctx), args.steps,
+                           args.warmup)
     n_s, n_v = 65536 * 1024, 4096 * 4096
     ks = st_s["timed_ms"] / st_s["timed_launches"]
     kv = st_v["timed_ms"] / st_v["timed_launches"]
+    kt = st_t["timed_ms"] / st_t["timed_launches"]
+    # accuracy on the first 1024 patches: max point error over the AABB
+    # diagonal of the patch's FP64 grid points
+    import oracle
+    sub = s[:1024].contiguous()
+    ref = oracle.surface(sub.cpu().numpy(), 32, 32).reshape(1024, -1, 3)
+    diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
+
+    def surf_err(var):
+        got = bez.bez_eval_surface(sub, 32, 32, variant=var, ctx=ctx).cpu().numpy().reshape(1024, -1, 3)
+        return float((np.linalg.norm(got.astype(np.float64) - ref, axis=-1).max(axis=1) / diag).max())
     return _hbm_line("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
                      (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
                      ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3_warp",
                      {"surface_points_per_s": n_s * args.steps / (ms_s * 1e-3),
                       "volume_values_per_s": n_v * args.steps / (ms_v * 1e-3), "volume_kernel_ms": kv,
-                      "volume_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9},
+                      "volume_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9,
+                      "surface_max_norm_err": surf_err(bez.Variant.AUTO),
+                      "surface_tex": {"points_per_s": n_s * args.steps / (ms_t * 1e-3), "kernel_ms": kt,
+                                      "gbs": n_s * 12 / (kt * 1e-3) / 1e9, "max_norm_err": surf_err(tex),
+                                      "kernel": "k_surface_tex<3> (one trilinear read per row and coordinate)"}},
                      traffic=TRAFFIC_SURFACE_65536)
 
 
@@ -587,6 +634,7 @@ def main():
     ap.add_argument("--accuracy-curves", type=int, default=4096)
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-f16", action="store_true", help="skip the half-storage variant table")
+    ap.add_argument("--skip-coissue", action="store_true", help="skip the texture + FP32 co-issue sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-curves", type=int, default=16384)

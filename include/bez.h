@@ -62,7 +62,10 @@ typedef enum bez_variant {
     BEZ_VAR_TEX_DECASTELJAU = 6, /* tex3D 2x2x2 de Casteljau tile (+ register levels)    */
     BEZ_VAR_TEX_SEILER = 7,      /* tex2D (d=2,3) / tex3D (d=4,5) Seiler tile            */
     BEZ_VAR_TEX_HYBRID = 8,      /* two bilinear reads + FP32 lerp (cubic)               */
-    BEZ_VAR_TENSOR = 9           /* surfaces / volumes: tensor-core contraction          */
+    BEZ_VAR_TENSOR = 9,          /* reserved (tensor-core grid contraction, not built:   *
+                                  * the grid kernels are bound by their stores)          */
+    BEZ_VAR_COISSUE = 10         /* tex2D Seiler for opts->tex_share of every 8 samples, *
+                                  * centred Horner for the rest, in one kernel           */
 } bez_variant;
 
 typedef enum bez_dtype { BEZ_F32 = 0, BEZ_F16 = 1, BEZ_BF16 = 2 } bez_dtype;
@@ -90,6 +93,8 @@ typedef struct bez_opts {
     int32_t sync;      /* nonzero: synchronise `stream` before returning                 */
     int32_t* err_word; /* device int32 or NULL: incremented for data faults (NURBS zero  *
                         * denominators)                                                 */
+    int32_t tex_share; /* BEZ_VAR_COISSUE only: samples out of every 8 read through the  *
+                        * texture unit, 1..7; 0 = library default (2)                    */
 } bez_opts;
 
 /* Opaque context: owns staging buffers, texture atlases, timing events. */
@@ -140,6 +145,15 @@ bez_status bez_reset_stats(bez_ctx ctx);
  *   h = H(H(key ^ c) ^ j),  key = H(lo(seed) ^ H(hi(seed) ^ H(stream_id))),
  *   H = lowbias32 (Wellons 2018: x^=x>>16; x*=0x7feb352d; x^=x>>15;
  *   x*=0x846ca68b; x^=x>>16), c < 2^32, j < 2^32.
+ *
+ * BEZ_VAR_COISSUE (Sec. 5: a texture read pays off when it overlaps
+ * arithmetic): cubic 3D curves, POLYLINE_LENGTH, BEZ_T_HASH with
+ * n_t <= 65536, dtype F32 or F16.  In every group of 8 consecutive samples
+ * of a lane's run, the first opts->tex_share samples are read from the
+ * curve's tex2D Seiler tile and the rest are evaluated by centred Horner in
+ * registers, so the texture unit and the FP32 pipes work side by side.
+ * Accuracy is that of the texture reads.  Other combinations return
+ * BEZ_ERR_UNSUPPORTED.
  */
 bez_status bez_eval(bez_ctx ctx, const void* ctrl, int64_t n_curves, int degree, int dim,
                     const float* t, int64_t n_t, float* out, const bez_opts* opts, void* stream);
@@ -208,14 +222,24 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
  * patch evaluates its four column curves at u, giving the control points of
  * the isoline cubic in v); a volume splits it between u, v and w.  The
  * kernels contract separably (columns at u, then v, then w) with Bernstein
- * tables of the grid values fl32(a)/fl32(n-1), one block per patch, and
- * write the output with coalesced (float4 where aligned) stores.
+ * tables of the grid values fl32(a)/fl32(n-1) (one warp per patch for
+ * bicubic 3D patches with nu <= 64, else one block per patch), and write
+ * the output with coalesced (float4 where aligned) stores.
  *
  *   surface ctrl [n][du+1][dv+1][dim]        -> out [n][nu][nv][dim]
  *   volume  ctrl [n][du+1][dv+1][dw+1][dim]  -> out [n][nu][nv][nw][dim]
  *   degrees 1..7, grid sizes 1..256 per axis, dim 1..4; ctrl element type
- *   opts->dtype (FP32, FP16 or BF16 storage, FP32 math); variant AUTO or
- *   BERNSTEIN; out_mode POINTS; t_mode and t are not used.
+ *   opts->dtype (FP32, FP16 or BF16 storage, FP32 math); out_mode POINTS;
+ *   t_mode and t are not used.
+ *   variant AUTO or BERNSTEIN: FP32 contraction on CUDA cores.
+ *   variant TEX_DECASTELJAU (bicubic surfaces, nu <= 64, FP32 or FP16
+ *   storage): per patch and coordinate a 2x2x2 RGBA texture tile holds the
+ *   four column cubics (Sec. 2.2); one trilinear read at (u,u,u) per grid
+ *   row gives the isoline control points, the cubic in v runs in FP32.
+ *   Accuracy is that of 8-bit filter weights (about 3 x 2^-8 of the column
+ *   range); the tiles live in a context-owned atlas, so texture calls of one
+ *   context are ordered on the device.  Other combinations return
+ *   BEZ_ERR_UNSUPPORTED.
  */
 bez_status bez_eval_surface(bez_ctx ctx, const void* ctrl, int64_t n, int du, int dv, int dim, int nu, int nv,
                             float* out, const bez_opts* opts, void* stream);

@@ -186,7 +186,7 @@ bez_status check_common(bez_ctx c, const bez_opts* o)
     if (o->out_mode < BEZ_OUT_POINTS || o->out_mode > BEZ_OUT_POLYLINE_LENGTH)
         return fail(BEZ_ERR_INVALID_ARG, "bad out_mode %d", o->out_mode);
     if (o->t_mode < BEZ_T_SHARED || o->t_mode > BEZ_T_HASH) return fail(BEZ_ERR_INVALID_ARG, "bad t_mode %d", o->t_mode);
-    if (o->variant < BEZ_VAR_AUTO || o->variant > BEZ_VAR_TENSOR)
+    if (o->variant < BEZ_VAR_AUTO || o->variant > BEZ_VAR_COISSUE)
         return fail(BEZ_ERR_INVALID_ARG, "bad variant %d", o->variant);
     return BEZ_OK;
 }
@@ -270,6 +270,7 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.seil3);
     atlas_free(c->tex.chain);
     atlas_free(c->tex.probe);
+    atlas_free(c->tex.surf3);
     if (c->tex_done) cudaEventDestroy(c->tex_done);
     delete c;
     return BEZ_OK;
@@ -324,8 +325,19 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
     if (degree < 1) return fail(BEZ_ERR_INVALID_ARG, "degree %d < 1", degree);
     int var = o->variant == BEZ_VAR_AUTO ? BEZ_VAR_SEILER : o->variant;
-    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER || var == BEZ_VAR_TEX_HYBRID;
-    if (var > BEZ_VAR_TEX_HYBRID) return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for bez_eval", var);
+    const bool coissue = var == BEZ_VAR_COISSUE;
+    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER || var == BEZ_VAR_TEX_HYBRID ||
+                     coissue;
+    if (var > BEZ_VAR_TEX_HYBRID && !coissue)
+        return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for bez_eval", var);
+    if (coissue) {
+        if (degree != 3 || dim != 3 || o->out_mode != BEZ_OUT_POLYLINE_LENGTH || o->t_mode != BEZ_T_HASH ||
+            n_t > 65536)
+            return fail(BEZ_ERR_UNSUPPORTED,
+                        "co-issue evaluates cubic 3D curves to polyline lengths at <= 65536 hashed parameters");
+        if (o->tex_share < 0 || o->tex_share > 7)
+            return fail(BEZ_ERR_INVALID_ARG, "tex_share %d not in 0..7", o->tex_share);
+    }
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
     if (var == BEZ_VAR_TEX_SEILER && (degree < 2 || degree > 5))
         return fail(BEZ_ERR_UNSUPPORTED, "Seiler textures are defined for degrees 2..5 (got %d)", degree);
@@ -372,7 +384,8 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     if (tex) {
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        r = launch_tex_curve(a, var, tm, om, c->tex, s, h);
+        r = coissue ? launch_tex_coissue(a, o->tex_share ? o->tex_share : kDefaultTexShare, c->tex, s, h)
+                    : launch_tex_curve(a, var, tm, om, c->tex, s, h);
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "batch of %lld curves does not fit one texture atlas",
                         (long long)n_curves);
@@ -584,9 +597,16 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     if (nu > 256 || nv > 256 || nw > 256) return fail(BEZ_ERR_UNSUPPORTED, "grids above 256 per axis");
     if (o->out_mode != BEZ_OUT_POINTS) return fail(BEZ_ERR_UNSUPPORTED, "surfaces and volumes output points");
     const int var = o->variant;
-    if (var != BEZ_VAR_AUTO && var != BEZ_VAR_BERNSTEIN)
+    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU;
+    if (var != BEZ_VAR_AUTO && var != BEZ_VAR_BERNSTEIN && !tex)
         return fail(BEZ_ERR_UNSUPPORTED,
-                    "variant %d: the store-bound grid contraction runs on CUDA cores (AUTO / BERNSTEIN)", var);
+                    "variant %d: grids run on CUDA cores (AUTO / BERNSTEIN) or, for bicubic surfaces, through "
+                    "texture tiles (TEX_DECASTELJAU)", var);
+    if (tex && (vol || du != 3 || dv != 3))
+        return fail(BEZ_ERR_UNSUPPORTED, "texture tiles hold bicubic surfaces only");
+    if (tex && nu > kSurfTexMaxRows)
+        return fail(BEZ_ERR_UNSUPPORTED, "texture surfaces take at most %d rows in u", kSurfTexMaxRows);
+    if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     TensorLaunch t{};
     t.dtype = o->dtype;
     t.n = n;
@@ -611,6 +631,17 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     st = stg.out(out, (size_t)n * nu * nv * (vol ? nw : 1) * dim * sizeof(float), 2, &od);
     if (st != BEZ_OK) return st;
     t.out = static_cast<float*>(od);
+    if (tex) {
+        // the atlases are shared by all calls of this context: order their use
+        if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
+        LaunchResult r = launch_tex_surface(t, c->tex, s, hooks_of(c));
+        if (r.err == cudaErrorInvalidValue && r.launches == 0)
+            return fail(BEZ_ERR_UNSUPPORTED, "%lld patches do not fit one texture atlas", (long long)n);
+        if (r.err != cudaSuccess) return cuda_fail(r.err, "texture surface launch");
+        BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
+        c->tex_used = true;
+        return stg.finish(o->sync);
+    }
     LaunchResult r = launch_tensor_product(t, s, hooks_of(c));
     if (r.err != cudaSuccess) return cuda_fail(r.err, "tensor-product launch");
     return stg.finish(o->sync);

@@ -69,6 +69,7 @@ struct TexState {
     Atlas seil3;  // 3D 2x2x2 Seiler tiles (degree 4, 5)
     Atlas chain;  // zig-zag C0 chain textures
     Atlas probe;  // 2x2x2 weight probe
+    Atlas surf3;  // bicubic surface tiles: four column cubics per 2x2x2 RGBA tile
     int max3d = 16384, max2d_w = 131072, max2d_h = 65536;
 };
 
@@ -76,6 +77,10 @@ struct TexState {
 // then evaluate.  `variant` is a bez_variant texture value.
 LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, TexState& ts, cudaStream_t s,
                               const LaunchHooks& h);
+// Co-issue: `share` of every 8 samples through the tex2D Seiler tile, the
+// rest by centred Horner (cubic, dim 3, hashed t with n_t <= 65536, length).
+constexpr int kDefaultTexShare = 2;
+LaunchResult launch_tex_coissue(const CurveArgs& a, int share, TexState& ts, cudaStream_t s, const LaunchHooks& h);
 // Filter-weight probe: out[i] = filtered (x, y, z) texel index at coords xyz[i].
 LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState& ts, cudaStream_t s,
                               const LaunchHooks& h);
@@ -124,6 +129,9 @@ struct TensorLaunch {
     float* out;
 };
 LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const LaunchHooks& h);
+// Bicubic surfaces through 2x2x2 RGBA texture tiles (nu <= kSurfTexMaxRows).
+constexpr int kSurfTexMaxRows = 64;
+LaunchResult launch_tex_surface(const TensorLaunch& t, TexState& ts, cudaStream_t s, const LaunchHooks& h);
 size_t tensor_product_smem(const TensorLaunch& t);
 
 // ---------------------------------------------------------------- adjoint

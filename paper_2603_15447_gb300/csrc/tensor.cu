@@ -3,7 +3,8 @@
 // between u, v and w; the bicubic case evaluates the four column curves at u
 // and then the isoline cubic in v).
 //
-// Separable contraction, one block per patch (grid-stride):
+// Separable contraction, one block per patch (grid-stride; bicubic 3D
+// patches on grids of up to 64 rows take one warp per patch):
 //   surface  X[a][j] = sum_i Bu[a][i] C[i][j]          (isoline control points)
 //            P[a][b] = sum_j X[a][j] Bv[b][j]
 //   volume   Y[a][j][l] = sum_i Bu[a][i] C[i][j][l]
@@ -15,45 +16,9 @@
 // coalesced.  The contraction has a reduction depth of 4 for bicubic
 // patches, far too small to keep tensor cores busy on a store-bound kernel,
 // so it runs on the FP32 pipes.
-#include "curve_eval.cuh"
+#include "tensor_common.cuh"
 
 namespace bez {
-
-constexpr int kTensorThreads = 256;
-constexpr int kTensorMaxDeg = 7;
-constexpr int kTensorMaxGrid = 256;
-
-struct TensorArgs {  // kernel-side copy of TensorLaunch
-    const void* ctrl;
-    int32_t dtype;
-    int64_t n;
-    int32_t du, dv, dw;  // dw < 0: surface
-    int32_t dim;
-    int32_t nu, nv, nw;
-    float* out;
-};
-
-// Bernstein table B[a][i] for n grid values and degree d, via de Casteljau
-// on unit vectors (each entry is a product of lerp weights, exact at ends).
-__device__ void bernstein_table(float* B, int n, int d, int tid, int nthreads)
-{
-    for (int a = tid; a < n; a += nthreads) {
-        const float t = n > 1 ? __fdiv_rn((float)a, (float)(n - 1)) : 0.f;
-        const float s = 1.0f - t;
-        // B_i^d(t) = C(d,i) s^(d-i) t^i, built from powers
-        float tp[kTensorMaxDeg + 1], sp[kTensorMaxDeg + 1];
-        tp[0] = sp[0] = 1.f;
-        for (int i = 1; i <= d; ++i) {
-            tp[i] = tp[i - 1] * t;
-            sp[i] = sp[i - 1] * s;
-        }
-        float bin = 1.f;
-        for (int i = 0; i <= d; ++i) {
-            B[a * (d + 1) + i] = bin * sp[d - i] * tp[i];
-            bin = bin * (float)(d - i) / (float)(i + 1);
-        }
-    }
-}
 
 // Fast path: bicubic 3D patches, nv a multiple of 4.  Each thread owns four
 // consecutive points of one grid row and writes them as three float4.
@@ -124,9 +89,6 @@ __global__ void __launch_bounds__(kTensorThreads) k_surface_bicubic3(const Tenso
 // sweeps the grid one row of up to 32 points at a time: lane l evaluates
 // point (a, b0 + l) with Bv[b0 + l] held in registers, stages its 3 floats in
 // a warp-private buffer and 24 lanes write the 384-byte row segment as float4.
-constexpr int kSurfWarps = 8;
-constexpr int kSurfMaxRows = 64;
-
 __global__ void __launch_bounds__(kSurfWarps * 32, 5) k_surface_bicubic3_warp(const TensorArgs a)
 {
     __shared__ float4 s_bv[kTensorMaxGrid];                   // Bv[b][0..3]

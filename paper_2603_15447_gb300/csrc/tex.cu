@@ -365,6 +365,131 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, T
     }
 }
 
+// ---------------------------------------------------------------- co-issue
+
+// Sec. 5: a texture evaluator only helps when its reads overlap arithmetic
+// that the FP32 pipes would do anyway.  k_coissue evaluates cubic 3D curves
+// to polyline lengths with both units in one instruction stream: in every
+// group of 8 samples of a lane's run the first S come from the curve's tex2D
+// Seiler tile (one bilinear read each, issued first), the other 8 - S from
+// centred Horner in registers while those reads are in flight.  Draws are
+// those of bez_eval's hash (pre-mixed key, sample indices < 2^16).
+template <int S, bool FIRST, bool FULL>
+__device__ __forceinline__ void coissue_group(const Eval<VAR_HORNER_CENTRED, 3, 3>& e, const TexArgs& ta, float xb,
+                                              float yb, uint32_t kg, int n, float (&first)[3], float (&last)[3],
+                                              float& acc)
+{
+    float4 T[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        if (FULL || i < n) {
+            const float t = hash_one_plus(lowbias32_premixed(kg ^ (uint32_t)i, 0u)) - 1.0f;
+            T[i] = tex2D<float4>(ta.tex, xb + t, yb + fmaf(-t, t, t));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (FULL || i < n) {
+            float P[3];
+            if (i < S) {
+                P[0] = T[i < S ? i : 0].x;
+                P[1] = T[i < S ? i : 0].y;
+                P[2] = T[i < S ? i : 0].z;
+            } else {
+                DrawEval<Eval<VAR_HORNER_CENTRED, 3, 3>>::at(e, kg ^ (uint32_t)i, P);
+            }
+            if (FIRST && i == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) first[k] = last[k] = P[k];
+            } else {
+                acc += seg_len<3>(P, last);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) last[k] = P[k];
+            }
+        }
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kWarps * 32, S <= 1 ? 5 : 4) k_coissue(const CurveArgs a, const TexArgs ta)
+{
+    using E = Eval<VAR_HORNER_CENTRED, 3, 3>;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    int64_t c = (int64_t)blockIdx.x * kWarps + wib;
+    CtrlRegs<4, 3> cur;
+    cur.load(a, c, 12, lane);
+    for (; c < a.n_curves; c += n_warps) {
+        float b[4][3];
+        cur.unpack(b, 3);
+        cur.load(a, c + n_warps, 12, lane);
+        E e;
+        e.setup(b, 3);
+        const uint32_t km = curve_key<TM_HASH16>(a, c);
+        const float xb = (float)((int)(c % ta.tw) * ta.wt) + 0.5f;
+        const float yb = (float)((int)(c / ta.tw) * 2) + 0.5f;
+        const int n_t = a.n_t;
+        // 8-aligned runs: sample g + i of a group starting at g has index g ^ i
+        const int chunk = ((n_t + 31) / 32 + 7) & ~7;
+        const int jb = lane * chunk;
+        const int je = min(jb + chunk, n_t);
+        float acc = 0.f;
+        float first[3] = {0.f, 0.f, 0.f}, last[3] = {0.f, 0.f, 0.f};
+        if (jb < je) {
+            coissue_group<S, true, false>(e, ta, xb, yb, km ^ (uint32_t)jb, je - jb, first, last, acc);
+            int g = jb + 8;
+            for (; g + 8 <= je; g += 8) coissue_group<S, false, true>(e, ta, xb, yb, km ^ (uint32_t)g, 8, first, last, acc);
+            if (g < je) coissue_group<S, false, false>(e, ta, xb, yb, km ^ (uint32_t)g, je - g, first, last, acc);
+        }
+        float pl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pl[k] = __shfl_up_sync(kFull, last[k], 1);
+        if (lane > 0 && jb < je) acc += seg_len<3>(first, pl);
+        acc = warp_sum(acc);
+        if (lane == 0) a.out[c] = acc;
+    }
+}
+
+LaunchResult launch_tex_coissue(const CurveArgs& a, int share, TexState& ts, cudaStream_t s, const LaunchHooks& h)
+{
+    const int wt = 2;
+    const int tw = tiles_per_row(a.n_curves, wt, ts.max2d_w);
+    const int64_t rows = (a.n_curves + tw - 1) / tw;
+    if (rows * 2 > ts.max2d_h) return {0, cudaErrorInvalidValue};
+    const int fmt = a.dtype == 1 ? 1 : 0;
+    cudaError_t e = atlas_ensure(ts.seil2, tw * wt, (int)(rows * 2), 0, fmt);
+    if (e != cudaSuccess) return {0, e};
+    TexArgs ta{ts.seil2.tex, tw, wt, 3};
+    h.count(h.self);
+    k_pack<TK_SEIL2><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, ts.seil2.surf, fmt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return {1, e};
+    const void* kern;
+    switch (share) {
+    case 1: kern = (const void*)k_coissue<1>; break;
+    case 2: kern = (const void*)k_coissue<2>; break;
+    case 3: kern = (const void*)k_coissue<3>; break;
+    case 4: kern = (const void*)k_coissue<4>; break;
+    case 5: kern = (const void*)k_coissue<5>; break;
+    case 6: kern = (const void*)k_coissue<6>; break;
+    default: kern = (const void*)k_coissue<7>; break;
+    }
+    const int64_t work = (a.n_curves + kWarps - 1) / kWarps;
+    int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, work);
+    if (work > grid) {
+        // as for k_curve: blocks of kCurvesPerWarp curves per warp
+        const int64_t g = (a.n_curves + (int64_t)kWarps * kCurvesPerWarp - 1) / ((int64_t)kWarps * kCurvesPerWarp);
+        if (g > grid) grid = (int)(g < 2147483647 ? g : 2147483647);
+    }
+    void* args[] = {(void*)&a, (void*)&ta};
+    h.count(h.self);
+    h.begin(h.self, s);
+    e = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);
+    h.end(h.self, s);
+    return {2, e};
+}
+
 // ---------------------------------------------------------------- zig-zag C0 chains
 
 // Sec. 2.1 (Eq. 1-2, Fig. 2): N quadratic segments with shared end points in

@@ -29,14 +29,15 @@ WERR = 2.0 ** -8 + 2.0 ** -11
 
 
 def _run(torch, ctrl, t=None, n_t=None, variant="TEX_DECASTELJAU", out_mode="POINTS", t_mode=None, seed=0,
-         stream_id=0, half=False):
+         stream_id=0, half=False, tex_share=0):
     from paper_2603_15447_gb300 import bez
     c = torch.from_numpy(ctrl).cuda()
     if half:
         c = c.half()
     tt = None if t is None else torch.from_numpy(np.ascontiguousarray(t, np.float32)).cuda()
     out = bez.bez_eval(c, tt, n_t=n_t, variant=bez.Variant[variant], out_mode=bez.OutMode[out_mode],
-                       t_mode=None if t_mode is None else bez.TMode[t_mode], seed=seed, stream_id=stream_id)
+                       t_mode=None if t_mode is None else bez.TMode[t_mode], seed=seed, stream_id=stream_id,
+                       tex_share=tex_share)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -203,3 +204,96 @@ def test_texture_unsupported_combinations():
         bez.bez_eval(torch.zeros((4, 4, 3), device="cuda", dtype=torch.bfloat16), torch.zeros(3, device="cuda"),
                      variant=bez.Variant.TEX_DECASTELJAU)
     assert e.value.status == bez.Status.UNSUPPORTED
+
+
+@pytest.mark.parametrize("dim,nu,nv,half", [(3, 32, 32, False), (1, 5, 20, False), (2, 64, 256, False),
+                                            (4, 17, 9, False), (3, 1, 1, False), (3, 32, 32, True)])
+def test_texture_bicubic_surface(dim, nu, nv, half):
+    # Sec. 2.2: a 2x2x2 RGBA tile per coordinate holds the four column cubics
+    # C[.][j][k]; one trilinear read at (u,u,u) gives the isoline control
+    # points of row u and the cubic in v runs in FP32.  The v stage is a convex
+    # combination, so the error is that of one 3-axis filtered read of the
+    # column tile: 3 x WERR x the largest column range of the coordinate.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(7000 + 100 * dim + nu + nv)
+    ctrl = rng.uniform(-1, 1, (301, 4, 4, dim)).astype(np.float32)
+    c = torch.from_numpy(ctrl).cuda()
+    if half:
+        c = c.half()
+    got = bez.bez_eval_surface(c, nu, nv, variant=bez.Variant.TEX_DECASTELJAU).cpu().numpy().astype(np.float64)
+    src = c.float().cpu().numpy()
+    ref = oracle.surface(src, nu, nv)
+    col_range = (src.max(axis=1) - src.min(axis=1)).max(axis=1)            # [n][dim]: max over columns j
+    tol = 3 * WERR * col_range + 8 * U * np.abs(src).max(axis=(1, 2))      # [n][dim]
+    if half:
+        ref_true = oracle.surface(ctrl, nu, nv)
+        err_true = np.abs(got - ref_true).max()
+        assert err_true <= (3 * WERR * 2 + 2.0 ** -10)                  # storage rounding on top, |C| <= 1
+    err = np.abs(got - ref)                                                # [n][nu][nv][dim]
+    assert np.all(err <= tol[:, None, None, :])
+    if not half:
+        np.testing.assert_array_equal(got[:, 0, 0], ctrl[:, 0, 0])         # texel centres: exact corners
+        if nu > 1 and nv > 1:
+            np.testing.assert_array_equal(got[:, -1, -1], ctrl[:, -1, -1])
+
+
+def test_texture_surface_unsupported():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    tex = bez.Variant.TEX_DECASTELJAU
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_surface(torch.zeros((2, 3, 4, 3), device="cuda"), 8, 8, variant=tex)   # not bicubic
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_surface(torch.zeros((2, 4, 4, 3), device="cuda"), 65, 8, variant=tex)  # rows > 64
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_surface(torch.zeros((2, 4, 4, 3), device="cuda", dtype=torch.bfloat16), 8, 8, variant=tex)
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_volume(torch.zeros((2, 4, 4, 4, 1), device="cuda"), 4, 4, 4, variant=tex)
+    assert e.value.status == bez.Status.UNSUPPORTED
+
+
+@pytest.mark.parametrize("share", [1, 2, 3, 5, 7])
+@pytest.mark.parametrize("n_t", [1024, 77])
+def test_coissue_length_mixes_texture_and_register_points(share, n_t):
+    # In every 8 consecutive samples the first `share` come from the tex2D
+    # Seiler tile and the rest from centred Horner; both use the bez_eval
+    # draw and the same tile as TEX_SEILER, so the kernel's length must be
+    # the polyline through TEX_SEILER points at j mod 8 < share and
+    # HORNER_CENTRED points elsewhere, up to FP32 accumulation.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(90 + share)
+    n = 333
+    ctrl = rng.uniform(-1, 1, size=(n, 4, 3)).astype(np.float32)
+    kw = dict(n_t=n_t, t_mode="HASH", seed=5, stream_id=3)
+    got = _run(torch, ctrl, variant="COISSUE", out_mode="POLYLINE_LENGTH", **kw, tex_share=share)
+    p_tex = _run(torch, ctrl, variant="TEX_SEILER", **kw)[..., :3].astype(np.float64)
+    p_reg = _run(torch, ctrl, variant="HORNER_CENTRED", **kw).astype(np.float64)
+    use_tex = (np.arange(n_t) % 8) < share
+    mixed = np.where(use_tex[None, :, None], p_tex, p_reg)
+    L = oracle.polyline_length(mixed)
+    assert np.all(np.abs(got - L) <= (n_t / 32 + 12) * U * L + 1e-7)
+
+
+def test_coissue_default_share_and_unsupported():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(91)
+    ctrl = rng.uniform(-1, 1, size=(40, 4, 3)).astype(np.float32)
+    kw = dict(n_t=256, variant="COISSUE", out_mode="POLYLINE_LENGTH", t_mode="HASH", seed=1)
+    np.testing.assert_array_equal(_run(torch, ctrl, **kw), _run(torch, ctrl, **kw, tex_share=2))
+    c = torch.from_numpy(ctrl).cuda()
+    co = dict(variant=bez.Variant.COISSUE, t_mode=bez.TMode.HASH)
+    for args, status in [
+        (dict(ctrl=c, n_t=64, out_mode=bez.OutMode.POINTS), bez.Status.UNSUPPORTED),
+        (dict(ctrl=c[:, :3].contiguous(), n_t=64, out_mode=bez.OutMode.POLYLINE_LENGTH), bez.Status.UNSUPPORTED),
+        (dict(ctrl=c, n_t=65537, out_mode=bez.OutMode.POLYLINE_LENGTH), bez.Status.UNSUPPORTED),
+        (dict(ctrl=c, n_t=64, out_mode=bez.OutMode.POLYLINE_LENGTH, tex_share=8), bez.Status.INVALID_ARG),
+    ]:
+        with pytest.raises(bez.BezError) as e:
+            bez.bez_eval(args.pop("ctrl"), None, **co, **args)
+        assert e.value.status == status
