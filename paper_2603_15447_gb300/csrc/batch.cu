@@ -2,16 +2,20 @@
 // one persistent kernel (setup + evaluation captured in one CUDA graph).
 //
 // Every curve is a list of spans (a Bezier curve is one span).  The setup
-// kernel (FP64, one warp per curve, lanes over spans) forms each span of a
-// spline by applying its extraction operator -- knot insertion done once per
-// distinct (n_ctrl, degree) on the host (spline.cuh span_operator) -- to the
-// de Boor points, in homogeneous form for NURBS, and stores the span either
-// as Bezier points (de Casteljau evaluation) or as power coefficients about
-// tau = 1/2 (Horner evaluation), rounded once to FP32.
+// kernel (one thread per span component) forms each span of a spline by
+// applying its extraction operator -- knot insertion done once per distinct
+// (n_ctrl, degree) on the host in FP64 (spline.cuh span_operator) -- to the
+// de Boor points, in homogeneous form for NURBS, in compensated FP32, and
+// stores the span either as Bezier points (de Casteljau evaluation) or as
+// power coefficients about tau = 1/2 (Horner evaluation), rounded once to
+// FP32.
 //
-// Work is cut into items (curve, chunk of samples).  Warps take items
-// round-robin (static) or `grab` at a time from an atomic counter.  Within an
-// item, each lane evaluates runs of 8 consecutive samples
+// Work is cut into items (a chunk of one curve's samples), each a 48-byte
+// record holding everything its evaluation needs, sorted by class (degree,
+// integral / rational).  The class evaluators run side by side on forked
+// streams.  Warps take items round-robin, reading the next record while they
+// evaluate the current item (static), or `grab` at a time from an atomic
+// counter.  Within an item, each lane evaluates runs of 8 consecutive samples
 // t_j = fl32(j) / fl32(n_samples - 1), keeping the coefficients of its
 // current span in registers and reloading them only when the span changes;
 // results go through a padded per-warp shared-memory tile and out with
@@ -25,65 +29,146 @@ namespace bez {
 constexpr int kRun = 8;              // consecutive samples per lane
 constexpr int kTile = 32 * kRun;     // samples per warp sub-tile
 constexpr int kBatchMaxComps = 5;
+constexpr int kItemsPerWarp = 4;  // static schedule: items per warp of a block
 
 // ---------------------------------------------------------------- setup
 
-// Bezier points b[0..p] (FP64) -> power coefficients about 1/2, in place:
-// c_m = binom(p,m) * (Bernstein value at 1/2 of the m-th forward differences)
-__device__ inline void bezier_to_centred(double* b, int p)
+// Bezier points b[0..P] (FP64, registers) -> power coefficients about 1/2,
+// in place: c_m = binom(P,m) * (Bernstein value at 1/2 of the m-th forward
+// differences)
+template <int P>
+__device__ __forceinline__ void bezier_to_centred_fixed(double (&b)[P + 1])
 {
-    double w[kMaxDegree + 1], c[kMaxDegree + 1];
-    for (int i = 0; i <= p; ++i) w[i] = b[i];
+    double w[P + 1], c[P + 1];
+#pragma unroll
+    for (int i = 0; i <= P; ++i) w[i] = b[i];
     double bin = 1.0;
-    for (int m = 0; m <= p; ++m) {
-        double h[kMaxDegree + 1];
-        for (int i = 0; i <= p - m; ++i) h[i] = w[i];
-        for (int r = 1; r <= p - m; ++r)
-            for (int i = 0; i <= p - m - r; ++i) h[i] = 0.5 * (h[i] + h[i + 1]);
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        double h[P + 1];
+#pragma unroll
+        for (int i = 0; i <= P; ++i) h[i] = w[i];
+#pragma unroll
+        for (int r = 1; r <= P; ++r)
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (r <= P - m && i <= P - m - r) h[i] = 0.5 * (h[i] + h[i + 1]);
         c[m] = bin * h[0];
-        bin = bin * (double)(p - m) / (double)(m + 1);
-        for (int i = 0; i < p - m; ++i) w[i] = w[i + 1] - w[i];
+        bin = bin * (double)(P - m) / (double)(m + 1);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if (i < P - m) w[i] = w[i + 1] - w[i];
     }
-    for (int i = 0; i <= p; ++i) b[i] = c[i];
+#pragma unroll
+    for (int i = 0; i <= P; ++i) b[i] = c[i];
 }
 
+// Component q of one span of degree P.  The span's Bezier points are its
+// extraction operator (splines; NURBS in homogeneous form) applied to the de
+// Boor points in compensated FP32: each operator entry is an unevaluated sum
+// hi + lo of two floats (48 significant bits), each homogeneous point w P an
+// exact sum (the product's error by one fma), and every row is a Dot2-style
+// compensated dot product (Ogita, Rump & Oishi 2005): products split exactly
+// by fma, partial sums by Knuth's TwoSum, the lower-order terms collected in
+// a correction that is added once at the end.  The result is as accurate as
+// a dot product in twice the working precision, then rounded: the FP64
+// operator's result to within a few units of 2^-48, at FP32 instruction rates
+// (GB300 runs FP64 at a small fraction of FP32).  The power basis about 1/2
+// is then formed in FP64 from the compensated sums.  Results are rounded once
+// to FP32.
+template <int P>
+__device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s, int q, int comps,
+                                           const bez_curve_desc& dsc)
+{
+    const bool spline = dsc.type != BEZ_CURVE_BEZIER;
+    const bool rat = dsc.type == BEZ_CURVE_NURBS;
+    const int dim = a.dim;
+    const float* ctrl = a.ctrl_pool + dsc.ctrl_off;
+    const float* wts = rat ? a.weight_pool + dsc.weight_off : nullptr;
+    float xh[P + 1], xl[P + 1];  // X_j = xh_j + xl_j exactly
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+        const int g = s + i;
+        if (rat) {
+            const float w = __ldg(wts + g);
+            if (q < dim) {
+                const float v = __ldg(ctrl + (int64_t)g * dim + q);
+                xh[i] = __fmul_rn(w, v);
+                xl[i] = fmaf(w, v, -xh[i]);
+            } else {
+                xh[i] = w;
+                xl[i] = 0.f;
+            }
+        } else {
+            xh[i] = __ldg(ctrl + (int64_t)g * dim + q);
+            xl[i] = 0.f;
+        }
+    }
+    float yh[P + 1], yl[P + 1];  // Y_i ~ yh_i + yl_i
+    if (spline) {
+        const float2* M = a.op_pool + a.span_ops[a.op_off[c] + s];
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+            float sh = 0.f, corr = 0.f;
+#pragma unroll
+            for (int j = 0; j <= P; ++j) {
+                const float2 m = __ldg(M + i * (P + 1) + j);
+                const float pr = __fmul_rn(m.x, xh[j]);
+                float e = fmaf(m.x, xh[j], -pr);       // exact: m.x xh_j = pr + e
+                e = fmaf(m.x, xl[j], e);               // lower-order terms
+                e = fmaf(m.y, xh[j], e);
+                const float t = __fadd_rn(sh, pr);     // TwoSum: sh + pr = t + err exactly
+                const float bv = __fsub_rn(t, sh);
+                const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(pr, bv));
+                sh = t;
+                corr = __fadd_rn(corr, __fadd_rn(err, e));
+            }
+            yh[i] = sh;
+            yl[i] = corr;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+            yh[i] = xh[i];
+            yl[i] = xl[i];
+        }
+    }
+    float* dst = a.span_pool + a.span_off[c] + (int64_t)s * (P + 1) * comps;
+    if (a.repr == 1) {
+        double Y[P + 1];
+#pragma unroll
+        for (int i = 0; i <= P; ++i) Y[i] = (double)yh[i] + (double)yl[i];
+        bezier_to_centred_fixed<P>(Y);
+#pragma unroll
+        for (int i = 0; i <= P; ++i) dst[i * comps + q] = (float)Y[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i <= P; ++i) dst[i * comps + q] = __fadd_rn(yh[i], yl[i]);
+    }
+}
+
+// Span extraction, one thread per (curve, span, component).
 __global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a)
 {
+    const int per = a.dim + 1;  // component slots per span (dim + 1 for homogeneous NURBS)
+    const int64_t total = a.n_span_tab * per;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n_span_tab; idx += stride) {
-        const int2 cs = a.span_tab[idx];
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const int64_t sp = idx / per;
+        const int q = (int)(idx - sp * per);
+        const int2 cs = a.span_tab[sp];
         const int64_t c = cs.x;
-        const int s = cs.y;
         const bez_curve_desc dsc = a.desc[c];
-        const int p = dsc.degree;
-        const bool spline = dsc.type != BEZ_CURVE_BEZIER;
-        const bool rat = dsc.type == BEZ_CURVE_NURBS;
-        const int dim = a.dim;
-        const int comps = rat ? dim + 1 : dim;
-        const float* ctrl = a.ctrl_pool + dsc.ctrl_off;
-        const float* wts = rat ? a.weight_pool + dsc.weight_off : nullptr;
-        {
-            const double* M = spline ? a.op_pool + a.span_ops[a.op_off[c] + s] : nullptr;
-            float* dst = a.span_pool + a.span_off[c] + (int64_t)s * (p + 1) * comps;
-            for (int q = 0; q < comps; ++q) {
-                double P[kMaxDegree + 1], Q[kMaxDegree + 1];
-                for (int i = 0; i <= p; ++i) {
-                    const int g = s + i;
-                    const double wi = rat ? (double)__ldg(wts + g) : 1.0;
-                    P[i] = q < dim ? wi * (double)__ldg(ctrl + (int64_t)g * dim + q) : wi;
-                }
-                for (int i = 0; i <= p; ++i) {
-                    if (!spline) {
-                        Q[i] = P[i];
-                        continue;
-                    }
-                    double acc = 0.0;
-                    for (int j = 0; j <= p; ++j) acc = fma(M[i * (p + 1) + j], P[j], acc);
-                    Q[i] = acc;
-                }
-                if (a.repr == 1) bezier_to_centred(Q, p);
-                for (int i = 0; i <= p; ++i) dst[i * comps + q] = (float)Q[i];
-            }
+        const int comps = dsc.type == BEZ_CURVE_NURBS ? a.dim + 1 : a.dim;
+        if (q >= comps) continue;
+        switch (dsc.degree) {
+        case 1: setup_comp<1>(a, c, cs.y, q, comps, dsc); break;
+        case 2: setup_comp<2>(a, c, cs.y, q, comps, dsc); break;
+        case 3: setup_comp<3>(a, c, cs.y, q, comps, dsc); break;
+        case 4: setup_comp<4>(a, c, cs.y, q, comps, dsc); break;
+        case 5: setup_comp<5>(a, c, cs.y, q, comps, dsc); break;
+        case 6: setup_comp<6>(a, c, cs.y, q, comps, dsc); break;
+        default: setup_comp<7>(a, c, cs.y, q, comps, dsc); break;
         }
     }
 }
@@ -120,18 +205,20 @@ __device__ __forceinline__ void span_eval(const float (&k)[P + 1][C], float tau,
 // one item of a 3D curve with compile-time degree P; C = 3 (integral) or 4
 // (rational, homogeneous)
 template <int P, int C, int REPR>
-__device__ void item_fixed(const BatchArgs& a, const bez_curve_desc& dsc, const float* base, int n_spans, int j0,
-                           int j1, float* stage, int lane)
+__device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage, int lane)
 {
     constexpr bool RAT = C == 4;
     constexpr int DIM = 3;
     constexpr int LS = kRun * DIM + 1;  // padded per-lane stride of the tile
-    const int n = dsc.n_samples;
-    const bool spline = dsc.type != BEZ_CURVE_BEZIER;
+    const int n = it.n_samples;
+    const bool spline = it.n_spans > 0;
+    const int n_spans = it.n_spans;
+    const int j0 = it.j0, j1 = it.j1;
+    const float* base = a.span_pool + it.span_base;
     const float den = (float)(n - 1);
     float coef[P + 1][C];
     int cached = -1;
-    float* out = a.out_pool + dsc.out_off;
+    float* out = a.out_pool + it.out_off;
     for (int tb = j0; tb < j1; tb += kTile) {
         const int my0 = tb + lane * kRun;
 #pragma unroll 2
@@ -161,11 +248,20 @@ __device__ void item_fixed(const BatchArgs& a, const bez_curve_desc& dsc, const 
             }
         }
         __syncwarp();
+        // Coalesced write-out: float f = 32 m + lane of the tile is element
+        // f mod 24 of lane run f div 24 (a run is kRun * DIM = 24 floats).
+        // With lane = 24 r0 + o0 and a = o0 div 8, run = r0 + m + w and
+        // offset = o0 + 8 m - 24 w where w = (a + m) div 3, so its staged
+        // position is base + m (LS + 8) + w (LS - 24).
+        static_assert(kRun * DIM == 24 && LS == 25, "write-out index formula");
         const int valid = min(kTile, j1 - tb) * DIM;
-        float* o = out + (int64_t)tb * DIM;
-        for (int idx = lane; idx < valid; idx += 32) {
-            const int smp = idx / DIM, q = idx - smp * DIM;
-            o[idx] = stage[(smp / kRun) * LS + (smp % kRun) * DIM + q];
+        float* o = out + (int64_t)tb * DIM + lane;
+        const int a3 = (lane % 24) / 8;
+        const int base = (lane / 24) * LS + lane % 24;
+#pragma unroll
+        for (int m = 0; m < kRun * DIM; ++m) {
+            const int w = m / 3 + ((m % 3) != 0 && a3 >= 3 - (m % 3) ? 1 : 0);
+            if (32 * m + lane < valid) o[32 * m] = stage[base + m * (LS + 8) + w * (LS - 24)];
         }
         __syncwarp();
     }
@@ -173,16 +269,18 @@ __device__ void item_fixed(const BatchArgs& a, const bez_curve_desc& dsc, const 
 
 // any dimension / degree (runtime loops)
 template <int REPR>
-__device__ void item_generic(const BatchArgs& a, const bez_curve_desc& dsc, const float* base, int n_spans, int j0,
-                             int j1, float* stage, int lane)
+__device__ void item_generic(const BatchArgs& a, const BatchItem& it, float* stage, int lane)
 {
-    const int dim = a.dim, p = dsc.degree;
-    const bool spline = dsc.type != BEZ_CURVE_BEZIER, rat = dsc.type == BEZ_CURVE_NURBS;
+    const int dim = a.dim, p = it.degree;
+    const bool spline = it.n_spans > 0, rat = it.rational != 0;
+    const int n_spans = it.n_spans;
+    const int j0 = it.j0, j1 = it.j1;
+    const float* base = a.span_pool + it.span_base;
     const int comps = rat ? dim + 1 : dim;
-    const int n = dsc.n_samples;
+    const int n = it.n_samples;
     const int LS = kRun * dim + 1;
     const float den = (float)(n - 1);
-    float* out = a.out_pool + dsc.out_off;
+    float* out = a.out_pool + it.out_off;
     for (int tb = j0; tb < j1; tb += kTile) {
         const int my0 = tb + lane * kRun;
         for (int r = 0; r < kRun; ++r) {
@@ -232,21 +330,28 @@ int batch_item_class(const bez_curve_desc& d, int dim)
     return (d.type == BEZ_CURVE_NURBS ? 7 : 0) + (d.degree - 1);
 }
 
-__device__ __forceinline__ void item_range(const BatchArgs& a, int64_t item, const bez_curve_desc*& dsc_out,
-                                           bez_curve_desc& dsc, int& j0, int& j1, int& n_spans, const float*& base)
+__device__ __forceinline__ BatchItem load_item(const BatchArgs& a, int64_t i)
 {
-    const int2 it = a.items[item];
-    const int64_t c = it.x;
-    dsc = a.desc[c];
-    j0 = it.y * a.chunk;
-    j1 = min(j0 + a.chunk, dsc.n_samples);
-    n_spans = dsc.type != BEZ_CURVE_BEZIER ? dsc.n_ctrl - dsc.degree : 1;
-    base = a.span_pool + a.span_off[c];
-    dsc_out = &dsc;
+    // every lane reads the same 48 bytes: three broadcast 16-byte loads
+    const int4* src = reinterpret_cast<const int4*>(a.items + i);
+    const int4 x = __ldg(src), y = __ldg(src + 1), z = __ldg(src + 2);
+    BatchItem it;
+    it.j0 = x.x;
+    it.j1 = x.y;
+    it.n_samples = x.z;
+    it.n_spans = x.w;
+    it.degree = y.x;
+    it.rational = y.y;
+    it.out_off = (int64_t)(((uint64_t)(uint32_t)y.w << 32) | (uint32_t)y.z);
+    it.span_base = (int64_t)(((uint64_t)(uint32_t)z.y << 32) | (uint32_t)z.x);
+    it.reserved = 0;
+    return it;
 }
 
-// Persistent evaluator of one item class: items [first, first + count) of the
-// sorted table, taken round-robin or from this class's atomic counter.
+// Evaluator of one item class: items [first, first + count) of the sorted
+// table.  Static schedule: warp w takes items w, w + n_warps, ... and reads
+// the record of its next item while it evaluates the current one; atomic
+// schedule: `grab` items at a time from this class's counter.
 template <int P, int C, int REPR>
 __global__ void __launch_bounds__(256) k_batch_class(const BatchArgs a, int64_t first, int64_t count,
                                                      unsigned long long* counter)
@@ -256,17 +361,19 @@ __global__ void __launch_bounds__(256) k_batch_class(const BatchArgs a, int64_t 
     const int wib = threadIdx.x >> 5;
     float* stage = s_stage + wib * (32 * (kRun * a.dim + 1));
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    auto run = [&](int64_t item) {
-        bez_curve_desc dsc;
-        const bez_curve_desc* dp;
-        int j0, j1, n_spans;
-        const float* base;
-        item_range(a, first + item, dp, dsc, j0, j1, n_spans, base);
-        if (P == 0) item_generic<REPR>(a, dsc, base, n_spans, j0, j1, stage, lane);
-        else item_fixed<(P > 0 ? P : 1), (C > 0 ? C : 3), REPR>(a, dsc, base, n_spans, j0, j1, stage, lane);
+    auto run = [&](const BatchItem& it) {
+        if (P == 0) item_generic<REPR>(a, it, stage, lane);
+        else item_fixed<(P > 0 ? P : 1), (C > 0 ? C : 3), REPR>(a, it, stage, lane);
     };
     if (a.schedule == 0) {
-        for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; item < count; item += n_warps) run(item);
+        int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+        if (item >= count) return;
+        BatchItem nxt = load_item(a, first + item);
+        for (; item < count; item += n_warps) {
+            const BatchItem cur = nxt;
+            if (item + n_warps < count) nxt = load_item(a, first + item + n_warps);
+            run(cur);
+        }
     } else {
         for (;;) {
             int64_t f = 0;
@@ -274,7 +381,7 @@ __global__ void __launch_bounds__(256) k_batch_class(const BatchArgs a, int64_t 
             f = __shfl_sync(kFull, f, 0);
             if (f >= count) break;
             const int64_t last = min(f + a.grab, count);
-            for (int64_t item = f; item < last; ++item) run(item);
+            for (int64_t item = f; item < last; ++item) run(load_item(a, first + item));
         }
     }
 }
@@ -302,12 +409,12 @@ static const void* class_kernel(int cls)
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
-                         const LaunchHooks& h, int* launches)
+                         const BatchStreams* bs, const LaunchHooks& h, int* launches)
 {
     *launches = 0;
     cudaError_t e;
     if (with_setup && a.n_curves > 0) {
-        const int grid = (int)std::min<int64_t>((a.n_span_tab + 255) / 256, (int64_t)sm_count * 16);
+        const int grid = (int)std::min<int64_t>((a.n_span_tab * (a.dim + 1) + 255) / 256, (int64_t)sm_count * 16);
         h.count(h.self);
         k_batch_setup<<<grid > 0 ? grid : 1, 256, 0, s>>>(a);
         ++*launches;
@@ -318,23 +425,48 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
         if (e != cudaSuccess) return e;
     }
     const size_t smem = (size_t)(threads / 32) * 32 * (kRun * a.dim + 1) * sizeof(float);
-    bool first_kernel = true;
+    int active = 0;
+    for (int cls = 0; cls < kBatchClasses; ++cls) active += a.class_start[cls + 1] > a.class_start[cls];
+    if (active == 0) return cudaSuccess;
+    // class evaluators run side by side: fork the side streams off `s`
+    const bool fork = bs && active > 1;
+    h.begin(h.self, s);
+    if (fork) {
+        if ((e = cudaEventRecord(bs->fork, s)) != cudaSuccess) return e;
+        for (int i = 0; i < kBatchSideStreams; ++i)
+            if ((e = cudaStreamWaitEvent(bs->side[i], bs->fork, 0)) != cudaSuccess) return e;
+    }
     e = cudaSuccess;
-    for (int cls = 0; cls < kBatchClasses; ++cls) {
+    int m = 0;
+    for (int cls = 0; cls < kBatchClasses && e == cudaSuccess; ++cls) {
         const int64_t first = a.class_start[cls], count = a.class_start[cls + 1] - first;
         if (count <= 0) continue;
+        const int lane_of = fork ? m % (kBatchSideStreams + 1) : 0;
+        ++m;
+        cudaStream_t cs = lane_of == 0 ? s : bs->side[lane_of - 1];
         const void* kern = a.repr == 1 ? class_kernel<1>(cls) : class_kernel<0>(cls);
-        const int grid = persistent_grid(kern, threads, smem, sm_count, (count + threads / 32 - 1) / (threads / 32));
+        const int wpb = threads / 32;
+        int grid = persistent_grid(kern, threads, smem, sm_count, (count + wpb - 1) / wpb);
+        if (a.schedule == 0) {
+            // blocks of kItemsPerWarp items per warp, scheduled by the hardware
+            const int64_t g = (count + (int64_t)wpb * kItemsPerWarp - 1) / ((int64_t)wpb * kItemsPerWarp);
+            if (g > grid) grid = (int)std::min<int64_t>(g, 2147483647);
+        }
         unsigned long long* counter = static_cast<unsigned long long*>(a.counter) + cls;
         void* args[] = {(void*)&a, (void*)&first, (void*)&count, (void*)&counter};
         h.count(h.self);
-        if (first_kernel) h.begin(h.self, s);
-        first_kernel = false;
-        e = cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, smem, s);
+        e = cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, smem, cs);
         ++*launches;
-        if (e != cudaSuccess) break;
     }
-    if (!first_kernel) h.end(h.self, s);
+    if (fork) {
+        // every side stream waited on the fork (and so joined a capture): join all of them back
+        for (int i = 0; i < kBatchSideStreams; ++i) {
+            cudaError_t e2 = cudaEventRecord(bs->join[i], bs->side[i]);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, bs->join[i], 0);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    h.end(h.self, s);
     return e;
 }
 

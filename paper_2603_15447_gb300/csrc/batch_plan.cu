@@ -99,13 +99,16 @@ struct bez_batch_s {
     std::vector<bez_curve_desc> hdesc;
     bez_curve_desc* d_desc = nullptr;
     int64_t* d_span_off = nullptr;
-    double* d_ops = nullptr;
+    float2* d_ops = nullptr;
     int64_t* d_span_ops = nullptr;
     int64_t* d_op_off = nullptr;
     int2* d_span_tab = nullptr;
     bool spans_ready = false;
-    int2* d_items = nullptr;
+    BatchItem* d_items = nullptr;
     size_t items_cap = 0;
+    std::vector<int64_t> hspan_off;   // per curve, floats into the span pool
+    BatchStreams streams{};
+    bool have_streams = false;
     float* d_spans = nullptr;
     void* d_counter = nullptr;
     Shape shape;
@@ -118,16 +121,30 @@ struct bez_batch_s {
 
 namespace {
 
+const BatchStreams* streams_of(bez_batch b) { return b->have_streams ? &b->streams : nullptr; }
+
 bez_status build_items(bez_batch b, int chunk, cudaStream_t s)
 {
     // items grouped by class (one evaluator kernel per class)
-    std::vector<std::vector<int2>> per_class(kBatchClasses);
+    std::vector<std::vector<BatchItem>> per_class(kBatchClasses);
     for (size_t c = 0; c < b->hdesc.size(); ++c) {
-        const int n = b->hdesc[c].n_samples;
-        auto& v = per_class[batch_item_class(b->hdesc[c], b->a.dim)];
-        for (int k = 0; (int64_t)k * chunk < n; ++k) v.push_back(make_int2((int)c, k));
+        const bez_curve_desc& d = b->hdesc[c];
+        const int n = d.n_samples;
+        auto& v = per_class[batch_item_class(d, b->a.dim)];
+        for (int k = 0; (int64_t)k * chunk < n; ++k) {
+            BatchItem it{};
+            it.j0 = k * chunk;
+            it.j1 = (int)std::min<int64_t>((int64_t)(k + 1) * chunk, n);
+            it.n_samples = n;
+            it.n_spans = d.type == BEZ_CURVE_BEZIER ? 0 : d.n_ctrl - d.degree;
+            it.degree = d.degree;
+            it.rational = d.type == BEZ_CURVE_NURBS;
+            it.out_off = d.out_off;
+            it.span_base = b->hspan_off[c];
+            v.push_back(it);
+        }
     }
-    std::vector<int2> items;
+    std::vector<BatchItem> items;
     for (int k = 0; k < kBatchClasses; ++k) {
         b->a.class_start[k] = (int64_t)items.size();
         items.insert(items.end(), per_class[k].begin(), per_class[k].end());
@@ -140,12 +157,13 @@ bez_status build_items(bez_batch b, int chunk, cudaStream_t s)
             cudaFree(b->d_items);
             b->d_items = nullptr;
         }
-        cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(int2));
+        cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(BatchItem));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc batch items");
         b->items_cap = items.size();
     }
     if (!items.empty()) {
-        cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+        cudaError_t e =
+            cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "copy batch items");
         e = cudaStreamSynchronize(s);  // `items` is a host temporary
         if (e != cudaSuccess) return cuda_fail(e, "copy batch items");
@@ -164,7 +182,7 @@ bez_status run_setup(bez_batch b, cudaStream_t s)
     BatchArgs a = b->a;
     a.n_items = 0;
     for (int k = 0; k < 16; ++k) a.class_start[k] = 0;
-    cudaError_t e = launch_batch(a, b->shape.threads, b->ctx->sm_count, true, s, h, &k);
+    cudaError_t e = launch_batch(a, b->shape.threads, b->ctx->sm_count, true, s, nullptr, h, &k);
     if (e != cudaSuccess) return cuda_fail(e, "batch setup");
     b->spans_ready = true;
     return BEZ_OK;
@@ -197,10 +215,10 @@ bez_status time_shape(bez_batch b, const Shape& sh, cudaStream_t s, float* ms_ou
     cudaEventCreate(&e1);
     float t[3];
     int k = 0;
-    cudaError_t e = launch_batch(b->a, sh.threads, b->ctx->sm_count, b->setup_each, s, h, &k);
+    cudaError_t e = launch_batch(b->a, sh.threads, b->ctx->sm_count, b->setup_each, s, streams_of(b), h, &k);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
         cudaEventRecord(e0, s);
-        e = launch_batch(b->a, sh.threads, b->ctx->sm_count, b->setup_each, s, h, &k);
+        e = launch_batch(b->a, sh.threads, b->ctx->sm_count, b->setup_each, s, streams_of(b), h, &k);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&t[r], e0, e1);
@@ -248,6 +266,13 @@ bez_status autotune(bez_batch b, cudaStream_t s)
 void free_batch(bez_batch b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->have_streams) {
+        for (int i = 0; i < kBatchSideStreams; ++i) {
+            cudaStreamDestroy(b->streams.side[i]);
+            cudaEventDestroy(b->streams.join[i]);
+        }
+        cudaEventDestroy(b->streams.fork);
+    }
     cudaFree(b->d_desc);
     cudaFree(b->d_span_off);
     cudaFree(b->d_ops);
@@ -355,7 +380,13 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     };
     alloc((void**)&b->d_desc, (size_t)n_curves * sizeof(bez_curve_desc));
     alloc((void**)&b->d_span_off, (size_t)n_curves * sizeof(int64_t));
-    alloc((void**)&b->d_ops, ops.size() * sizeof(double));
+    // operators as unevaluated float pairs hi + lo: hi = fl32(M), lo = fl32(M - hi)
+    std::vector<float2> ops2(ops.size());
+    for (size_t k = 0; k < ops.size(); ++k) {
+        const float hi = (float)ops[k];
+        ops2[k] = make_float2(hi, (float)(ops[k] - (double)hi));
+    }
+    alloc((void**)&b->d_ops, ops2.size() * sizeof(float2));
     alloc((void**)&b->d_span_ops, span_ops.size() * sizeof(int64_t));
     alloc((void**)&b->d_op_off, (size_t)n_curves * sizeof(int64_t));
     alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
@@ -375,7 +406,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     if (e == cudaSuccess && n_curves > 0)
         e = cudaMemcpy(b->d_span_off, span_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ops.empty())
-        e = cudaMemcpy(b->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_ops, ops2.data(), ops2.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !span_ops.empty())
         e = cudaMemcpy(b->d_span_ops, span_ops.data(), span_ops.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_curves > 0)
@@ -383,6 +414,29 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "batch buffers");
+    }
+    b->hspan_off = std::move(span_off);
+    // side streams for the class evaluators (joined back on every launch)
+    {
+        BatchStreams& st = b->streams;
+        const bool have_fork = cudaEventCreateWithFlags(&st.fork, cudaEventDisableTiming) == cudaSuccess;
+        bool ok = have_fork;
+        int ns = 0, ne = 0;
+        for (int i = 0; ok && i < kBatchSideStreams; ++i) {
+            ok = cudaStreamCreateWithFlags(&st.side[i], cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) ++ns;
+            if (ok) ok = cudaEventCreateWithFlags(&st.join[i], cudaEventDisableTiming) == cudaSuccess;
+            if (ok) ++ne;
+        }
+        if (!ok) {
+            for (int i = 0; i < ns; ++i) cudaStreamDestroy(st.side[i]);
+            for (int i = 0; i < ne; ++i) cudaEventDestroy(st.join[i]);
+            if (have_fork) cudaEventDestroy(st.fork);
+            cudaGetLastError();
+            free_batch(b);
+            return fail(BEZ_ERR_CUDA, "batch side streams");
+        }
+        b->have_streams = true;
     }
     BatchArgs& a = b->a;
     a.desc = b->d_desc;
@@ -434,7 +488,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
         if (e == cudaSuccess) {
             const LaunchHooks h0{no_count, no_event, no_event, nullptr, c->sm_count};
             int k = 0;
-            cudaError_t le = launch_batch(a, b->shape.threads, c->sm_count, b->setup_each, cs, h0, &k);
+            cudaError_t le = launch_batch(a, b->shape.threads, c->sm_count, b->setup_each, cs, streams_of(b), h0, &k);
             e = cudaStreamEndCapture(cs, &graph);
             if (le != cudaSuccess) e = le;
             b->kernels_per_launch = k;
@@ -470,7 +524,7 @@ bez_status bez_batch_launch(bez_batch b, void* stream)
         return BEZ_OK;
     }
     int k = 0;
-    cudaError_t e = launch_batch(b->a, b->shape.threads, c->sm_count, b->setup_each, s, h, &k);
+    cudaError_t e = launch_batch(b->a, b->shape.threads, c->sm_count, b->setup_each, s, streams_of(b), h, &k);
     if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     return BEZ_OK;
 }

@@ -527,6 +527,7 @@ __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb,
         }
     }
     int g = jb + 4;
+#pragma unroll 2
     for (; g + 4 <= je; g += 4) {
         const uint32_t kg = km ^ (uint32_t)g;
 #pragma unroll

@@ -154,6 +154,29 @@ LaunchResult launch_grad(const GradArgs& a, cudaStream_t s, const LaunchHooks& h
 
 // ---------------------------------------------------------------- mixed batches
 
+// One work item of a batch: a chunk of one curve's samples with everything
+// the evaluator needs, so a warp reads one record (prefetched) per item.
+struct alignas(16) BatchItem {
+    int32_t j0, j1;     // samples [j0, j1) of the curve
+    int32_t n_samples;  // the curve's sample count
+    int32_t n_spans;    // spline spans; 0 for a Bezier curve (no span selection)
+    int32_t degree;
+    int32_t rational;
+    int64_t out_off;    // floats into out_pool: the curve's first point
+    int64_t span_base;  // floats into span_pool: the curve's first span
+    int64_t reserved;
+};
+static_assert(sizeof(BatchItem) == 48, "BatchItem is read as three 16-byte loads");
+
+// Side streams of a batch: class evaluators run concurrently between a fork
+// and a join on the launching stream (also inside graph capture).
+constexpr int kBatchSideStreams = 3;
+struct BatchStreams {
+    cudaStream_t side[kBatchSideStreams];
+    cudaEvent_t fork;
+    cudaEvent_t join[kBatchSideStreams];
+};
+
 struct BatchArgs {
     const bez_curve_desc* desc;  // device copy
     int64_t n_curves;
@@ -163,13 +186,13 @@ struct BatchArgs {
     float* out_pool;
     float* span_pool;            // every curve's spans in the evaluation representation
     const int64_t* span_off;     // per curve, floats into span_pool
-    const double* op_pool;       // FP64 span extraction operators of the splines
+    const float2* op_pool;       // span extraction operators of the splines, each entry hi + lo (FP64 -> 2 x FP32)
     const int64_t* op_off;       // per curve, index of its first span in span_ops (splines only)
     const int64_t* span_ops;     // per spline span: offset of its operator matrix in op_pool
     const int2* span_tab;        // (curve, span) of every span: one setup thread each
     int64_t n_span_tab;
     int32_t repr;                // 0 Bezier points (de Casteljau), 1 power basis about 1/2 (Horner)
-    const int2* items;           // (curve, chunk index), sorted by item class
+    const BatchItem* items;      // work items, sorted by item class
     int64_t n_items;
     int64_t class_start[16];     // items of class k: [class_start[k], class_start[k+1])
     int32_t chunk;
@@ -180,7 +203,7 @@ struct BatchArgs {
 constexpr int kBatchClasses = 15;  // 7 degrees x {integral, rational} for 3D curves + generic
 int batch_item_class(const bez_curve_desc& d, int dim);
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
-                         const LaunchHooks& h, int* launches);
+                         const BatchStreams* bs, const LaunchHooks& h, int* launches);
 
 // Peak microbenchmarks (peaks.cu): kind 0 FP32 FMA lane-ops/s, 1..4 texture
 // fetches/s (2D float4, 2D half4, 3D float4, 3D half4), 5 store GB/s,
