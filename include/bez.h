@@ -60,7 +60,7 @@ typedef enum bez_variant {
     BEZ_VAR_DECASTELJAU = 4,     /* de Casteljau, d(d+1)/2 lerps                          */
     BEZ_VAR_SEILER = 5,          /* Seiler interpolation, d lerps                         */
     BEZ_VAR_TEX_DECASTELJAU = 6, /* tex3D 2x2x2 de Casteljau tile (+ register levels)    */
-    BEZ_VAR_TEX_SEILER = 7,      /* tex2D (d=2,3) / tex3D (d=4,5) Seiler tile            */
+    BEZ_VAR_TEX_SEILER = 7,      /* tex2D (d=2,3) / tex3D (d=4..7) Seiler tile           */
     BEZ_VAR_TEX_HYBRID = 8,      /* two bilinear reads + FP32 lerp (cubic)               */
     BEZ_VAR_TENSOR = 9,          /* reserved (tensor-core grid contraction, not built:   *
                                   * the grid kernels are bound by their stores)          */
@@ -133,11 +133,13 @@ bez_status bez_reset_stats(bez_ctx ctx);
  *   ctrl  [n_curves][degree+1][dim], element type opts->dtype
  *   t     per opts->t_mode (NULL for UNIFORM / HASH)
  *   out   POINTS: [n_curves][n_t][dim] FP32;  POLYLINE_LENGTH: [n_curves] FP32
- *   degree 1..15 (texture Seiler: 2..5); dim 1..4.
+ *   degree 1..15 (texture Seiler: 2..7); dim 1..4.
  *
  * Texture variants pack the control points into a cudaArray atlas owned by
  * the context (one surface-write kernel), then evaluate with hardware linear
- * filtering (one kernel).  dtype F32 gives float4 texels, F16 half4 texels;
+ * filtering (one kernel).  Seiler tiles: the paper's layouts for degrees 2..5
+ * (read at (t, st) and (t, st, st)); for degrees 6, 7 a 2x2x2 tile holding
+ * L(d_k, d_(d-k), t) / 4^k in its corners, read at (t, 4 st, 16 st^2).  dtype F32 gives float4 texels, F16 half4 texels;
  * BF16 has no texture format (BEZ_ERR_UNSUPPORTED).  Calls of one context
  * that use the atlases are ordered across streams by the library.
  *

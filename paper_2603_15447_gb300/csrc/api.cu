@@ -339,8 +339,8 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
             return fail(BEZ_ERR_INVALID_ARG, "tex_share %d not in 0..7", o->tex_share);
     }
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
-    if (var == BEZ_VAR_TEX_SEILER && (degree < 2 || degree > 5))
-        return fail(BEZ_ERR_UNSUPPORTED, "Seiler textures are defined for degrees 2..5 (got %d)", degree);
+    if (var == BEZ_VAR_TEX_SEILER && (degree < 2 || degree > 7))
+        return fail(BEZ_ERR_UNSUPPORTED, "Seiler textures are defined for degrees 2..7 (got %d)", degree);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     if (n_curves == 0 || (n_t == 0 && o->out_mode == BEZ_OUT_POINTS)) return BEZ_OK;
     if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");

@@ -391,13 +391,17 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     alloc((void**)&b->d_op_off, (size_t)n_curves * sizeof(int64_t));
     alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
     alloc(&b->d_counter, kBatchClasses * sizeof(unsigned long long));
-    // (curve, span) of every span: one setup thread each
+    // (curve, span) of every span, grouped by (degree, type) so that the
+    // warps of the setup kernel run one degree's code at a time
     std::vector<int2> span_tab;
-    for (int64_t i = 0; i < n_curves; ++i) {
-        const bez_curve_desc& d = b->hdesc[(size_t)i];
-        const int n_spans = d.type == BEZ_CURVE_BEZIER ? 1 : d.n_ctrl - d.degree;
-        for (int s = 0; s < n_spans; ++s) span_tab.push_back(make_int2((int)i, s));
-    }
+    for (int deg = 1; deg <= 7; ++deg)
+        for (int ty = BEZ_CURVE_BEZIER; ty <= BEZ_CURVE_NURBS; ++ty)
+            for (int64_t i = 0; i < n_curves; ++i) {
+                const bez_curve_desc& d = b->hdesc[(size_t)i];
+                if (d.degree != deg || d.type != ty) continue;
+                const int n_spans = d.type == BEZ_CURVE_BEZIER ? 1 : d.n_ctrl - d.degree;
+                for (int s = 0; s < n_spans; ++s) span_tab.push_back(make_int2((int)i, s));
+            }
     alloc((void**)&b->d_span_tab, span_tab.size() * sizeof(int2));
     if (e == cudaSuccess && !span_tab.empty())
         e = cudaMemcpy(b->d_span_tab, span_tab.data(), span_tab.size() * sizeof(int2), cudaMemcpyHostToDevice);

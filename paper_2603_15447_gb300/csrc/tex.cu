@@ -19,6 +19,14 @@
 //   SEIL3 degrees 4, 5: 2x2x2 tile, z=0 [[b0,bd],[b0,bd]],
 //         z=1 [[b0+d1, bd+d_(d-1)], [b0+d1+d2, bd+d_(d-1)+d_(d-2)]] read at
 //         (t, st, st) (Sec. 4, Eq. 7 and the layout table).
+//   SEIL3Q degrees 6, 7 (beyond the layout table; Sec. 6 leaves them open):
+//         trilinear filtering of a 2x2x2 tile at (x, y, z) is
+//         L0(x) + y L1(x) + z L2(x) + yz L3(x) with L_k linear in x, so reading
+//         at (t, 4 st, 16 st^2) a tile holding L0 = L(d0, dd), L1/4, L2/16 and
+//         L3/64 in its corners gives the Seiler form L0 + st L1 + st^2 L2 +
+//         st^3 L3 of any degree <= 7 (L_k = L(d_k, d_(d-k), t)).  The 4 and 16
+//         use the whole weight range of the y and z axes; d_k come from the
+//         exact peeling of the s-power form in FP64.
 //
 // Coordinates are unnormalised with texel centres at i + 0.5, so the paper's
 // [0.25, 0.75] remap of a 2-texel axis becomes x = x0 + 0.5 + t; for the st
@@ -27,7 +35,7 @@
 
 namespace bez {
 
-enum { TK_DC3 = 0, TK_DCN = 1, TK_HYB3 = 2, TK_HYBN = 3, TK_SEIL2 = 4, TK_SEIL3 = 5 };
+enum { TK_DC3 = 0, TK_DCN = 1, TK_HYB3 = 2, TK_HYBN = 3, TK_SEIL2 = 4, TK_SEIL3 = 5, TK_SEIL3Q = 6 };
 
 struct TexArgs {
     cudaTextureObject_t tex;
@@ -127,6 +135,40 @@ __device__ void seiler_terms(const float4* b, int d, float4& d1, float4& dl, flo
     }
 }
 
+// Seiler terms of degree 6 or 7 by peeling P = L(P(0), P(1), t) + t(1-t) Q
+// in the Bernstein basis (FP64): lo[k] = d_k, hi[k] = d_(d-k), k = 0..3
+// (d_0 = b_0, d_d = b_d; for d = 6, lo[3] = hi[3] = d_3).
+__device__ void seiler_terms_peeled(const float4* b, int d, float4 (&lo)[4], float4 (&hi)[4])
+{
+    for (int k = 0; k < 4; ++k) {
+        double c[8];
+        for (int i = 0; i <= d; ++i) c[i] = k == 0 ? b[i].x : k == 1 ? b[i].y : k == 2 ? b[i].z : b[i].w;
+        int m = d;
+        for (int lvl = 0; lvl < 4; ++lvl) {
+            const double c0 = c[0], cm = c[m < 0 ? 0 : m];
+            float* L = k == 0 ? &lo[lvl].x : k == 1 ? &lo[lvl].y : k == 2 ? &lo[lvl].z : &lo[lvl].w;
+            float* R = k == 0 ? &hi[lvl].x : k == 1 ? &hi[lvl].y : k == 2 ? &hi[lvl].z : &hi[lvl].w;
+            if (m < 0) {
+                *L = *R = 0.f;
+                continue;
+            }
+            *L = (float)c0;
+            *R = (float)cm;
+            if (m < 2) {
+                m = -1;
+                continue;
+            }
+            const double mm = (double)m;
+            for (int j = 0; j <= m - 2; ++j) {
+                const double i1 = (double)(j + 1);
+                const double q = (c[j + 1] - c0) - (i1 / mm) * (cm - c0);
+                c[j] = q * (mm * (mm - 1.0)) / (i1 * (mm - 1.0 - (double)j));
+            }
+            m -= 2;
+        }
+    }
+}
+
 template <int KIND>
 __global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, int fmt)
 {
@@ -147,6 +189,21 @@ __global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, 
     } else if (KIND == TK_HYB3 || KIND == TK_HYBN) {
         for (int y = 0; y < 2; ++y)
             for (int x = 0; x < ta.wt; ++x) put(surf, fmt, x0 + x, y0 + y, 0, false, b[min(x + y, d)]);
+    } else if (KIND == TK_SEIL3Q) {
+        float4 lo[4], hi[4];
+        seiler_terms_peeled(b, d, lo, hi);
+        const float4 z0y1l = add4(lo[0], scale4(0.25f, lo[1])), z0y1h = add4(hi[0], scale4(0.25f, hi[1]));
+        const float4 z1y0l = add4(lo[0], scale4(0.0625f, lo[2])), z1y0h = add4(hi[0], scale4(0.0625f, hi[2]));
+        const float4 z1y1l = add4(z0y1l, add4(scale4(0.0625f, lo[2]), scale4(0.015625f, lo[3])));
+        const float4 z1y1h = add4(z0y1h, add4(scale4(0.0625f, hi[2]), scale4(0.015625f, hi[3])));
+        put(surf, fmt, x0, y0, 0, true, lo[0]);
+        put(surf, fmt, x0 + 1, y0, 0, true, hi[0]);
+        put(surf, fmt, x0, y0 + 1, 0, true, z0y1l);
+        put(surf, fmt, x0 + 1, y0 + 1, 0, true, z0y1h);
+        put(surf, fmt, x0, y0, 1, true, z1y0l);
+        put(surf, fmt, x0 + 1, y0, 1, true, z1y0h);
+        put(surf, fmt, x0, y0 + 1, 1, true, z1y1l);
+        put(surf, fmt, x0 + 1, y0 + 1, 1, true, z1y1h);
     } else {
         float4 d1, dl, d2, dl2;
         seiler_terms(b, d, d1, dl, d2, dl2);
@@ -193,6 +250,10 @@ __device__ __forceinline__ float4 tex_point(const TexArgs& ta, float xb, float y
     if (KIND == TK_SEIL3) {
         const float st = fmaf(-t, t, t);
         return tex3D<float4>(ta.tex, xb + t, yb + st, 0.5f + st);
+    }
+    if (KIND == TK_SEIL3Q) {
+        const float st = fmaf(-t, t, t);
+        return tex3D<float4>(ta.tex, xb + t, yb + 4.f * st, 0.5f + 16.f * (st * st));
     }
     const int d = ta.deg;
     if (KIND == TK_DCN) {
@@ -341,7 +402,7 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, T
         wt = d >= 2 ? d : 2;
         is3d = false;
     } else {  // BEZ_VAR_TEX_SEILER
-        kind = d <= 3 ? TK_SEIL2 : TK_SEIL3;
+        kind = d <= 3 ? TK_SEIL2 : d <= 5 ? TK_SEIL3 : TK_SEIL3Q;
         wt = 2;
         is3d = d > 3;
     }
@@ -352,7 +413,7 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, T
     if (h_needed > (is3d ? ts.max3d : ts.max2d_h)) return {0, cudaErrorInvalidValue};
     Atlas& at = kind == TK_DC3 || kind == TK_DCN ? ts.dc3
                 : kind == TK_HYB3 || kind == TK_HYBN ? ts.strip2
-                : kind == TK_SEIL2 ? ts.seil2 : ts.seil3;
+                : kind == TK_SEIL2 ? ts.seil2 : ts.seil3;   // SEIL3 and SEIL3Q share the 2x2x2 atlas
     cudaError_t e = atlas_ensure(at, tw * wt, (int)h_needed, is3d ? 2 : 0, fmt);
     if (e != cudaSuccess) return {0, e};
     switch (kind) {
@@ -361,7 +422,8 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, T
     case TK_HYB3: return launch_kind<TK_HYB3>(a, tm, om, at, tw, wt, s, h);
     case TK_HYBN: return launch_kind<TK_HYBN>(a, tm, om, at, tw, wt, s, h);
     case TK_SEIL2: return launch_kind<TK_SEIL2>(a, tm, om, at, tw, wt, s, h);
-    default: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, s, h);
+    case TK_SEIL3: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, s, h);
+    default: return launch_kind<TK_SEIL3Q>(a, tm, om, at, tw, wt, s, h);
     }
 }
 

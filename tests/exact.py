@@ -92,6 +92,56 @@ def seiler_eval(b, t, terms=None):
     return lerp(b[0], b[d], t) + st * D(1)
 
 
+def seiler_terms_peel(b):
+    """Difference terms {k: d_k} of the Seiler form for any degree, by exact
+    polynomial division (sympy): P_0 = C; d_k = P_k(0), d_(d-k) = P_k(1) and
+    P_(k+1) = (P_k - L(P_k(0), P_k(1), t)) / (t (1 - t)), which is exact since
+    the numerator vanishes at t = 0 and t = 1.  For degrees <= 5 the result
+    equals the paper's closed forms (pinned by a test)."""
+    import sympy
+    t = sympy.symbols("t")
+    d = len(b) - 1
+    P = sum(sympy.Rational(comb(d, i)) * (1 - t) ** (d - i) * t ** i * sympy.Rational(b[i].numerator, b[i].denominator)
+            for i in range(d + 1))
+    P = sympy.expand(P)
+    terms = {}
+    k = 0
+    m = d
+    while m >= 0:
+        lo, hi = P.subs(t, 0), P.subs(t, 1)
+        terms[k] = F(int(lo.p), int(lo.q))
+        terms[d - k] = F(int(hi.p), int(hi.q))
+        if m < 2:
+            break
+        q, r = sympy.div(sympy.expand(P - (lo + (hi - lo) * t)), sympy.expand(t * (1 - t)), t)
+        assert r == 0
+        P = sympy.expand(q)
+        k += 1
+        m -= 2
+    return terms
+
+
+def seiler_texture_quadratic_z(b):
+    """2x2x2 tile for degrees 6, 7 read at (t, 4 st, 16 st^2) (a derivation
+    beyond the paper's layout table): trilinear filtering of tile[z][y][x] at
+    (x, y, z) is L0(x) + y (L1 - L0) + z (L2 - L0) + yz (...), so with
+    L_k(t) = L(d_k, d_(d-k), t) and texels
+      z=0: [[d0, dd], [d0 + d1/4, dd + d_(d-1)/4]]
+      z=1: [[d0 + d2/16, dd + d_(d-2)/16],
+            [d0 + d1/4 + d2/16 + d3/64, dd + d_(d-1)/4 + d_(d-2)/16 + d_(d-3)/64]]
+    the read gives L0 + st L1 + st^2 L2 + st^3 L3, the Seiler form of degree
+    <= 7 (d_0 = b_0, d_d = b_d)."""
+    d = len(b) - 1
+    assert d in (6, 7)
+    dd = seiler_terms_peel(b)
+    lo = [dd[k] for k in range(4)]
+    hi = [dd[d - k] for k in range(4)]
+    z0 = [[lo[0], hi[0]], [lo[0] + lo[1] / 4, hi[0] + hi[1] / 4]]
+    z1 = [[lo[0] + lo[2] / 16, hi[0] + hi[2] / 16],
+          [lo[0] + lo[1] / 4 + lo[2] / 16 + lo[3] / 64, hi[0] + hi[1] / 4 + hi[2] / 16 + hi[3] / 64]]
+    return [z0, z1]
+
+
 def bilinear(tile, x, y):
     """tile[y][x] (2x2), fractional weights x, y in [0,1]."""
     return lerp(lerp(tile[0][0], tile[0][1], x), lerp(tile[1][0], tile[1][1], x), y)

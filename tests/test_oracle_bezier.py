@@ -70,6 +70,44 @@ def test_oracle_equals_paper_seiler_forms(d):
                 assert float(exact_value) == got[c, j, a]
 
 
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_peeled_seiler_terms_equal_paper_closed_forms(d):
+    # The peeling reading used from degree 6 on reproduces the paper's closed
+    # forms (Sec. 3.1) where those exist.
+    from exact import seiler_terms_peel
+    rng = random.Random(20 + d)
+    for _ in range(5):
+        b = [F(rng.randint(-8, 8)) for _ in range(d + 1)]
+        paper = seiler_terms(b)
+        peel = seiler_terms_peel(b)
+        for k, v in paper.items():
+            assert peel[k] == v, (d, k)
+
+
+@pytest.mark.parametrize("d", [6, 7])
+def test_degree_6_7_seiler_texture_equals_oracle(d):
+    # 2x2x2 Seiler tile for degrees 6, 7 read at (t, 4 st, 16 st^2): exact
+    # trilinear filtering reaches the Bernstein value (and the FP64 oracle),
+    # and so does the Seiler recursion with the peeled terms.
+    from exact import seiler_terms_peel, seiler_texture_quadratic_z
+    rng = random.Random(30 + d)
+    ctrl = _rand_int_ctrl(rng, 3, d, 2)
+    ks = list(range(0, 65, 7)) + [64]
+    got = oracle.bezier(ctrl, np.array([k / 64 for k in ks]))
+    for c in range(ctrl.shape[0]):
+        for a in range(2):
+            b = [F(int(v)) for v in ctrl[c, :, a]]
+            tile = seiler_texture_quadratic_z(b)
+            terms = seiler_terms_peel(b)
+            for j, k in enumerate(ks):
+                tf = F(k, 64)
+                st = (1 - tf) * tf
+                exact_value = bernstein_exact(b, tf)
+                assert seiler_eval(b, tf, terms) == exact_value
+                assert trilinear(tile, tf, 4 * st, 16 * st * st) == exact_value
+                assert float(exact_value) == got[c, j, a]
+
+
 def test_paper_d2_formula_degenerates_at_cubic():
     # For d = 3 the Sec. 3.1 d_2 expression collapses to 0 for any control
     # points, so it must not be used there (the cubic uses d_{d-1} instead).

@@ -62,6 +62,37 @@ def _seiler_terms(b):
     return d1, dl, d2, dl2
 
 
+def _seiler_terms_peeled(b):
+    """lo[k] = d_k, hi[k] = d_(d-k), k = 0..3, by FP64 polynomial division:
+    P_0 = C, P_(k+1) = (P_k - L(P_k(0), P_k(1), t)) / (t (1 - t)) (power basis,
+    numpy); b [B][d+1][dim]."""
+    from math import comb
+    B, d1_, dim = b.shape
+    d = d1_ - 1
+    lo = np.zeros((4, B, dim))
+    hi = np.zeros((4, B, dim))
+    for c in range(B):
+        for a in range(dim):
+            # power-basis coefficients, highest degree first
+            P = np.zeros(d + 1)
+            for i in range(d + 1):
+                term = np.poly1d([1.0])
+                term = term * comb(d, i) * np.poly1d([-1.0, 1.0]) ** (d - i) * np.poly1d([1.0, 0.0]) ** i
+                P = np.polyadd(P, term.coeffs * b[c, i, a])
+            P = np.poly1d(P)
+            for k in range(4):
+                l0, h0 = P(0.0), P(1.0)
+                lo[k, c, a], hi[k, c, a] = l0, h0
+                if P.order < 2:
+                    if k < 3:
+                        lo[k + 1:, c, a] = 0.0
+                        hi[k + 1:, c, a] = 0.0
+                    break
+                num = P - np.poly1d([h0 - l0, l0])
+                P, _ = np.polydiv(num, np.poly1d([-1.0, 1.0, 0.0]))
+    return lo, hi
+
+
 def texture_bound(variant, ctrl, texel_eps=U):
     """Per-curve bound on |P_tex - C| (see module doc).  texel_eps: relative
     rounding of a stored texel (2^-24 float, 2^-11 half)."""
@@ -77,6 +108,16 @@ def texture_bound(variant, ctrl, texel_eps=U):
         w = min(d, 2)
         bound = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0) * w * WERR
         tex_mag = np.abs(b).max(axis=(1, 2))
+    elif d >= 6:
+        # degree 6, 7 tile: corners L0, L0 + L1/4, L0 + L2/16, L0 + L1/4 + L2/16 + L3/64
+        lo, hi = _seiler_terms_peeled(b)
+        c0 = lo[0], hi[0]
+        c1 = lo[0] + lo[1] / 4, hi[0] + hi[1] / 4
+        c2 = lo[0] + lo[2] / 16, hi[0] + hi[2] / 16
+        c3 = c1[0] + lo[2] / 16 + lo[3] / 64, c1[1] + hi[2] / 16 + hi[3] / 64
+        tiles = np.stack([*c0, *c1, *c2, *c3], 1)
+        bound = 3 * WERR * _range(tiles)
+        tex_mag = np.abs(tiles).max(axis=(1, 2))
     else:
         d1, dl, d2, dl2 = _seiler_terms(b)
         b0, bd = b[:, 0], b[:, d]
@@ -126,7 +167,7 @@ def test_filter_weight_probe_single_axis():
 
 @pytest.mark.parametrize("variant,d", [("TEX_DECASTELJAU", d) for d in (1, 2, 3, 4, 5, 7)]
                          + [("TEX_HYBRID", d) for d in (1, 2, 3, 4, 6)]
-                         + [("TEX_SEILER", d) for d in (2, 3, 4, 5)])
+                         + [("TEX_SEILER", d) for d in (2, 3, 4, 5, 6, 7)])
 def test_texture_points_within_weight_bound(variant, d):
     torch = need_gpu()
     rng = np.random.default_rng(40 + d)
@@ -197,7 +238,7 @@ def test_texture_unsupported_combinations():
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
     with pytest.raises(bez.BezError) as e:
-        bez.bez_eval(torch.zeros((4, 7, 3), device="cuda"), torch.zeros(3, device="cuda"),
+        bez.bez_eval(torch.zeros((4, 9, 3), device="cuda"), torch.zeros(3, device="cuda"),
                      variant=bez.Variant.TEX_SEILER)
     assert e.value.status == bez.Status.UNSUPPORTED
     with pytest.raises(bez.BezError) as e:
