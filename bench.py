@@ -217,10 +217,10 @@ def run_precision(args, rank, world, local_rank):
     timer = Timer(torch, ctx, dev, world)
     ts = synth.PRECISION_T_STREAM
 
-    def step_for(v, c=ctrl):
+    def step_for(v, c=ctrl, fmt=bez.TexFormat.AUTO):
         def step():
             bez.bez_eval(c, None, n_t=args.n_t, variant=bez.Variant[v], out_mode=bez.OutMode.POLYLINE_LENGTH,
-                         t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, out=out, ctx=ctx)
+                         t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, out=out, ctx=ctx, tex_format=fmt)
         return step
 
     run_variants = [v for v in VARIANTS if v in args.variants.split(",")] if args.variants else list(VARIANTS)
@@ -239,6 +239,14 @@ def run_precision(args, rank, world, local_rank):
             for v in run_variants:
                 ms, st = timer.run(step_for(v, ctrl16), args.steps, args.warmup)
                 results16[v] = {"ms": ms, "stats": st}
+        # unorm texels with per-curve rescale (texture variants only)
+        results_unorm = {}
+        if not args.skip_f16:
+            for fmt in (bez.TexFormat.UNORM16, bez.TexFormat.UNORM8):
+                for v in run_variants:
+                    if v in TEX_FETCHES:
+                        ms, st = timer.run(step_for(v, ctrl, fmt), args.steps, args.warmup)
+                        results_unorm[(fmt.name, v)] = {"ms": ms, "stats": st}
         # co-issue: `share` of every 8 samples through the texture unit, the
         # rest on the FP32 pipes, in one kernel
         coissue = {}
@@ -317,6 +325,12 @@ def run_precision(args, rank, world, local_rank):
     horner = variants["HORNER"]["points_per_s"]
     for v in run_variants:
         variants[v]["speedup_vs_horner"] = variants[v]["points_per_s"] / horner
+    variants_unorm = {}
+    for (fname, v), r in results_unorm.items():
+        st = r["stats"]
+        kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
+        variants_unorm.setdefault(fname, {})[v] = {"points_per_s": pts_step * args.steps / (r["ms"] * 1e-3),
+                                                   "kernel_ms": kern_ms}
     variants16 = {}
     for v, r in results16.items():
         st = r["stats"]
@@ -346,6 +360,12 @@ def run_precision(args, rank, world, local_rank):
             variants[v]["max_norm_err"] = float(err.max())
             variants[v]["bar"] = bar
             variants[v]["meets_bar"] = bool(err.max() <= bar)
+            for fname, tab in variants_unorm.items():
+                if v in tab:
+                    pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
+                                       seed=seed, stream_id=ts, ctx=ctx, tex_format=bez.TexFormat[fname])
+                    err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
+                    tab[v]["max_norm_err"] = float(err.max())
             if v in variants16:
                 # against the oracle of the FP32 control points: includes the 2^-11 storage rounding
                 pts = bez.bez_eval(sample.half(), None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
@@ -399,6 +419,7 @@ def run_precision(args, rank, world, local_rank):
         "clocks": clock_summary,
         "variants": variants,
         "variants_f16_storage": variants16 or None,
+        "variants_unorm_texels": variants_unorm or None,
         "coissue": coissue or None,
         "peaks_measured": {"fma_tops": peaks["fma"] / 1e12,
                            **{k + "_gfetch_s": peaks[k] / 1e9 for k in peaks if k.startswith("tex")}},

@@ -83,6 +83,18 @@ typedef enum bez_t_mode {
                           * curve, j); t unused.  See bez_eval.                         */
 } bez_t_mode;
 
+/* Texel format of texture tiles.  AUTO: float4 for FP32 control points,
+ * half4 for FP16.  UNORM16 / UNORM8 (Sec. 2.3: low-bit-depth texels hold
+ * [0, 1]): each curve's tile is stored as (texel - lo) / scale per component,
+ * lo and scale its tile's minimum and range, and the filtered value is mapped
+ * back by lo + scale * f; texel rounding adds 2^-17 (16-bit) or 2^-9 (8-bit)
+ * of the tile's range to the 8-bit filter-weight error. */
+typedef enum bez_tex_format {
+    BEZ_TEX_AUTO = 0,
+    BEZ_TEX_UNORM16 = 1,
+    BEZ_TEX_UNORM8 = 2
+} bez_tex_format;
+
 typedef struct bez_opts {
     int32_t variant;   /* bez_variant                                                   */
     int32_t dtype;     /* bez_dtype of the control points                               */
@@ -95,6 +107,9 @@ typedef struct bez_opts {
                         * denominators)                                                 */
     int32_t tex_share; /* BEZ_VAR_COISSUE only: samples out of every 8 read through the  *
                         * texture unit, 1..7; 0 = library default (2)                    */
+    int32_t tex_format;/* bez_tex_format of texture tiles of bez_eval (texture variants   *
+                        * and BEZ_VAR_COISSUE); texture chains and surfaces take          *
+                        * BEZ_TEX_AUTO only; entry points without textures ignore it      */
 } bez_opts;
 
 /* Opaque context: owns staging buffers, texture atlases, timing events. */

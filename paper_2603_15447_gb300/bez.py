@@ -60,10 +60,17 @@ class TMode(enum.IntEnum):
     HASH = 3
 
 
+class TexFormat(enum.IntEnum):
+    AUTO = 0
+    UNORM16 = 1
+    UNORM8 = 2
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("dtype", ctypes.c_int32), ("out_mode", ctypes.c_int32),
                 ("t_mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
-                ("sync", ctypes.c_int32), ("err_word", ctypes.c_void_p), ("tex_share", ctypes.c_int32)]
+                ("sync", ctypes.c_int32), ("err_word", ctypes.c_void_p), ("tex_share", ctypes.c_int32),
+                ("tex_format", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -219,22 +226,25 @@ def context(device: int | None = None) -> Context:
     return _contexts[device]
 
 
-def _opts(variant, dtype, out_mode, t_mode, seed, stream_id, sync, tex_share=0):
+def _opts(variant, dtype, out_mode, t_mode, seed, stream_id, sync, tex_share=0, tex_format=TexFormat.AUTO):
     return Opts(int(variant), int(dtype), int(out_mode), int(t_mode), int(seed) & (2 ** 64 - 1),
-                int(stream_id) & 0xFFFFFFFF, int(sync), None, int(tex_share))
+                int(stream_id) & 0xFFFFFFFF, int(sync), None, int(tex_share), int(tex_format))
 
 
 # ---------------------------------------------------------------- entry points
 
 def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.POINTS, t_mode=None,
-             seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None, tex_share=0):
+             seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None, tex_share=0,
+             tex_format=TexFormat.AUTO):
     """Evaluate Bezier curves ``ctrl`` [n_curves][degree+1][dim].
 
     ``t``: [n_t] (shared) or [n_curves][n_t] (per curve), or None with
     ``t_mode`` UNIFORM / HASH and ``n_t`` given.  Returns points
     [n_curves][n_t][dim] or polyline lengths [n_curves] (FP32), on the same
     device as ``ctrl``.  ``tex_share``: COISSUE only, samples of every 8
-    read through the texture unit (1..7, 0 = library default)."""
+    read through the texture unit (1..7, 0 = library default).
+    ``tex_format``: texel format of the texture variants (AUTO, UNORM16,
+    UNORM8)."""
     n_curves, d1, dim = ctrl.shape
     if t_mode is None:
         t_mode = TMode.SHARED if (t is not None and t.ndim == 1) else TMode.PER_CURVE
@@ -246,7 +256,7 @@ def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.P
         out = _empty_like_location(ctrl, shape)
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, tex_share)
+    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, tex_share, tex_format)
     _check(lib().bez_eval(c.handle, _ptr(ctrl), n_curves, d1 - 1, dim, _ptr(t), n_t, _ptr(out), ctypes.byref(o),
                           _stream_handle(stream, dev)))
     return out
@@ -266,7 +276,8 @@ def bez_probe_filter(xyz, *, out=None, stream=None, ctx=None):
 
 
 def bez_eval_piecewise(ctrl, n_seg, degree, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.POINTS,
-                       t_mode=None, seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None):
+                       t_mode=None, seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None,
+                       tex_format=TexFormat.AUTO):
     """Evaluate C0 chains ``ctrl`` [n_chains][n_seg*degree+1][dim] at global
     parameters in [0, n_seg]."""
     n_chains, n_pts, dim = ctrl.shape
@@ -281,7 +292,7 @@ def bez_eval_piecewise(ctrl, n_seg, degree, t=None, *, n_t=None, variant=Variant
         out = _empty_like_location(ctrl, shape)
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
+    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, 0, tex_format)
     _check(lib().bez_eval_piecewise(c.handle, _ptr(ctrl), n_chains, n_seg, degree, dim, _ptr(t), n_t, _ptr(out),
                                     ctypes.byref(o), _stream_handle(stream, dev)))
     return out

@@ -188,6 +188,8 @@ bez_status check_common(bez_ctx c, const bez_opts* o)
     if (o->t_mode < BEZ_T_SHARED || o->t_mode > BEZ_T_HASH) return fail(BEZ_ERR_INVALID_ARG, "bad t_mode %d", o->t_mode);
     if (o->variant < BEZ_VAR_AUTO || o->variant > BEZ_VAR_COISSUE)
         return fail(BEZ_ERR_INVALID_ARG, "bad variant %d", o->variant);
+    if (o->tex_format < BEZ_TEX_AUTO || o->tex_format > BEZ_TEX_UNORM8)
+        return fail(BEZ_ERR_INVALID_ARG, "bad tex_format %d", o->tex_format);
     return BEZ_OK;
 }
 
@@ -271,6 +273,7 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.chain);
     atlas_free(c->tex.probe);
     atlas_free(c->tex.surf3);
+    cudaFree(c->tex.rescale);
     if (c->tex_done) cudaEventDestroy(c->tex_done);
     delete c;
     return BEZ_OK;
@@ -384,8 +387,8 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     if (tex) {
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        r = coissue ? launch_tex_coissue(a, o->tex_share ? o->tex_share : kDefaultTexShare, c->tex, s, h)
-                    : launch_tex_curve(a, var, tm, om, c->tex, s, h);
+        r = coissue ? launch_tex_coissue(a, o->tex_share ? o->tex_share : kDefaultTexShare, o->tex_format, c->tex, s, h)
+                    : launch_tex_curve(a, var, tm, om, o->tex_format, c->tex, s, h);
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "batch of %lld curves does not fit one texture atlas",
                         (long long)n_curves);
@@ -423,6 +426,8 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     if (tex && degree != 2)
         return fail(BEZ_ERR_UNSUPPORTED, "zig-zag chain textures hold quadratic segments (degree %d)", degree);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
+    if (tex && o->tex_format != BEZ_TEX_AUTO)
+        return fail(BEZ_ERR_UNSUPPORTED, "chain textures use float4 / half4 texels (tex_format AUTO)");
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
     const int64_t per = ((int64_t)n_seg * degree + 1) * dim;
     if (!tex && per > kChainMaxFloats)
@@ -604,6 +609,8 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
                     "texture tiles (TEX_DECASTELJAU)", var);
     if (tex && (vol || du != 3 || dv != 3))
         return fail(BEZ_ERR_UNSUPPORTED, "texture tiles hold bicubic surfaces only");
+    if (tex && o->tex_format != BEZ_TEX_AUTO)
+        return fail(BEZ_ERR_UNSUPPORTED, "texture surfaces use float4 / half4 tiles (tex_format AUTO)");
     if (tex && nu > kSurfTexMaxRows)
         return fail(BEZ_ERR_UNSUPPORTED, "texture surfaces take at most %d rows in u", kSurfTexMaxRows);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");

@@ -70,17 +70,20 @@ struct TexState {
     Atlas chain;  // zig-zag C0 chain textures
     Atlas probe;  // 2x2x2 weight probe
     Atlas surf3;  // bicubic surface tiles: four column cubics per 2x2x2 RGBA tile
+    float4* rescale = nullptr;  // unorm tiles: per curve (offset, scale)
+    int64_t rescale_cap = 0;    // curves the rescale buffer holds
     int max3d = 16384, max2d_w = 131072, max2d_h = 65536;
 };
 
 // Texture evaluators: pack the control points into the atlas of `variant`,
 // then evaluate.  `variant` is a bez_variant texture value.
-LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, TexState& ts, cudaStream_t s,
-                              const LaunchHooks& h);
+LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, int tex_format, TexState& ts,
+                              cudaStream_t s, const LaunchHooks& h);
 // Co-issue: `share` of every 8 samples through the tex2D Seiler tile, the
 // rest by centred Horner (cubic, dim 3, hashed t with n_t <= 65536, length).
 constexpr int kDefaultTexShare = 2;
-LaunchResult launch_tex_coissue(const CurveArgs& a, int share, TexState& ts, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, TexState& ts, cudaStream_t s,
+                                const LaunchHooks& h);
 // Filter-weight probe: out[i] = filtered (x, y, z) texel index at coords xyz[i].
 LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState& ts, cudaStream_t s,
                               const LaunchHooks& h);

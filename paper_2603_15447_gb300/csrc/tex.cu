@@ -42,6 +42,7 @@ struct TexArgs {
     int tw;   // tiles per atlas row
     int wt;   // tile width in texels
     int deg;
+    float4* rescale;  // unorm formats: per curve (offset, scale) of its tile; nullptr for float / half texels
 };
 
 // ---------------------------------------------------------------- atlases (host)
@@ -66,7 +67,11 @@ cudaError_t atlas_ensure(Atlas& at, int w, int h, int depth, int fmt)
         if (e != cudaSuccess) return e;
         atlas_free(at);
     }
-    cudaChannelFormatDesc cd = fmt == 0 ? cudaCreateChannelDesc<float4>() : cudaCreateChannelDescHalf4();
+    // fmt 0 float4, 1 half4, 2 unorm16 x 4, 3 unorm8 x 4 (read as normalised floats)
+    cudaChannelFormatDesc cd = fmt == 0   ? cudaCreateChannelDesc<float4>()
+                               : fmt == 1 ? cudaCreateChannelDescHalf4()
+                               : fmt == 2 ? cudaCreateChannelDesc<ushort4>()
+                                          : cudaCreateChannelDesc<uchar4>();
     cudaError_t e;
     if (depth > 0) e = cudaMalloc3DArray(&at.arr, &cd, make_cudaExtent(w, h, depth), cudaArraySurfaceLoadStore);
     else e = cudaMallocArray(&at.arr, &cd, w, h, cudaArraySurfaceLoadStore);
@@ -80,7 +85,7 @@ cudaError_t atlas_ensure(Atlas& at, int w, int h, int depth, int fmt)
     cudaTextureDesc td = {};
     td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
     td.filterMode = cudaFilterModeLinear;
-    td.readMode = cudaReadModeElementType;
+    td.readMode = fmt >= 2 ? cudaReadModeNormalizedFloat : cudaReadModeElementType;
     td.normalizedCoords = 0;
     e = cudaCreateTextureObject(&at.tex, &rd, &td, nullptr);
     if (e == cudaSuccess) e = cudaCreateSurfaceObject(&at.surf, &rd);
@@ -97,16 +102,33 @@ cudaError_t atlas_ensure(Atlas& at, int w, int h, int depth, int fmt)
 
 // ---------------------------------------------------------------- packers
 
+// unorm code of a value in [0, 1] with `levels` = 2^bits - 1, round to nearest
+__device__ __forceinline__ unsigned unorm_code(float v, float levels)
+{
+    const float x = fminf(fmaxf(v, 0.f), 1.f) * levels;
+    return (unsigned)__float2uint_rn(x);
+}
+
 __device__ __forceinline__ void put(cudaSurfaceObject_t s, int fmt, int x, int y, int z, bool is3d, float4 v)
 {
     if (fmt == 0) {
         if (is3d) surf3Dwrite(v, s, x * 16, y, z);
         else surf2Dwrite(v, s, x * 16, y);
-    } else {
+    } else if (fmt == 1) {
         const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
         const uint2 bits = make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
         if (is3d) surf3Dwrite(bits, s, x * 8, y, z);
         else surf2Dwrite(bits, s, x * 8, y);
+    } else if (fmt == 2) {
+        const ushort4 u = make_ushort4(unorm_code(v.x, 65535.f), unorm_code(v.y, 65535.f), unorm_code(v.z, 65535.f),
+                                       unorm_code(v.w, 65535.f));
+        if (is3d) surf3Dwrite(u, s, x * 8, y, z);
+        else surf2Dwrite(u, s, x * 8, y);
+    } else {
+        const uchar4 u = make_uchar4(unorm_code(v.x, 255.f), unorm_code(v.y, 255.f), unorm_code(v.z, 255.f),
+                                     unorm_code(v.w, 255.f));
+        if (is3d) surf3Dwrite(u, s, x * 4, y, z);
+        else surf2Dwrite(u, s, x * 4, y);
     }
 }
 
@@ -169,6 +191,65 @@ __device__ void seiler_terms_peeled(const float4* b, int d, float4 (&lo)[4], flo
     }
 }
 
+__device__ __forceinline__ float4 min4(float4 a, float4 b)
+{
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+}
+__device__ __forceinline__ float4 max4(float4 a, float4 b)
+{
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
+// Texels of curve c's tile: emit(x, y, z, value) for every texel.
+template <int KIND, class Emit>
+__device__ __forceinline__ void tile_texels(const float4* b, int d, int wt, Emit&& emit)
+{
+    if (KIND == TK_DC3 || KIND == TK_DCN) {
+        for (int z = 0; z < 2; ++z)
+            for (int y = 0; y < 2; ++y)
+                for (int x = 0; x < wt; ++x) emit(x, y, z, b[min(x + y + z, d)]);
+    } else if (KIND == TK_HYB3 || KIND == TK_HYBN) {
+        for (int y = 0; y < 2; ++y)
+            for (int x = 0; x < wt; ++x) emit(x, y, 0, b[min(x + y, d)]);
+    } else if (KIND == TK_SEIL3Q) {
+        float4 lo[4], hi[4];
+        seiler_terms_peeled(b, d, lo, hi);
+        const float4 z0y1l = add4(lo[0], scale4(0.25f, lo[1])), z0y1h = add4(hi[0], scale4(0.25f, hi[1]));
+        emit(0, 0, 0, lo[0]);
+        emit(1, 0, 0, hi[0]);
+        emit(0, 1, 0, z0y1l);
+        emit(1, 1, 0, z0y1h);
+        emit(0, 0, 1, add4(lo[0], scale4(0.0625f, lo[2])));
+        emit(1, 0, 1, add4(hi[0], scale4(0.0625f, hi[2])));
+        emit(0, 1, 1, add4(z0y1l, add4(scale4(0.0625f, lo[2]), scale4(0.015625f, lo[3]))));
+        emit(1, 1, 1, add4(z0y1h, add4(scale4(0.0625f, hi[2]), scale4(0.015625f, hi[3]))));
+    } else {
+        float4 d1, dl, d2, dl2;
+        seiler_terms(b, d, d1, dl, d2, dl2);
+        if (KIND == TK_SEIL2) {
+            emit(0, 0, 0, b[0]);
+            emit(1, 0, 0, b[d]);
+            emit(0, 1, 0, add4(b[0], d1));
+            emit(1, 1, 0, add4(b[d], dl));
+        } else {
+            emit(0, 0, 0, b[0]);
+            emit(1, 0, 0, b[d]);
+            emit(0, 1, 0, b[0]);
+            emit(1, 1, 0, b[d]);
+            const float4 s1 = add4(b[0], d1), s2 = add4(b[d], dl);
+            emit(0, 0, 1, s1);
+            emit(1, 0, 1, s2);
+            emit(0, 1, 1, add4(s1, d2));
+            emit(1, 1, 1, add4(s2, dl2));
+        }
+    }
+}
+
+// One thread per curve: its tile's texels into the atlas.  Unorm formats
+// (Sec. 2.3: low-bit-depth texels hold [0, 1]) store (v - lo) / scale with
+// lo and scale the tile's per-component minimum and range, recorded in
+// ta.rescale for the evaluator, which maps the filtered value back by
+// lo + scale * f (filtering is affine, so this commutes with it).
 template <int KIND>
 __global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, int fmt)
 {
@@ -182,48 +263,26 @@ __global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, 
         b[i] = make_float4(v[0], v[1], v[2], v[3]);
     }
     const int x0 = (int)(c % ta.tw) * ta.wt, y0 = (int)(c / ta.tw) * 2;
-    if (KIND == TK_DC3 || KIND == TK_DCN) {
-        for (int z = 0; z < 2; ++z)
-            for (int y = 0; y < 2; ++y)
-                for (int x = 0; x < ta.wt; ++x) put(surf, fmt, x0 + x, y0 + y, z, true, b[min(x + y + z, d)]);
-    } else if (KIND == TK_HYB3 || KIND == TK_HYBN) {
-        for (int y = 0; y < 2; ++y)
-            for (int x = 0; x < ta.wt; ++x) put(surf, fmt, x0 + x, y0 + y, 0, false, b[min(x + y, d)]);
-    } else if (KIND == TK_SEIL3Q) {
-        float4 lo[4], hi[4];
-        seiler_terms_peeled(b, d, lo, hi);
-        const float4 z0y1l = add4(lo[0], scale4(0.25f, lo[1])), z0y1h = add4(hi[0], scale4(0.25f, hi[1]));
-        const float4 z1y0l = add4(lo[0], scale4(0.0625f, lo[2])), z1y0h = add4(hi[0], scale4(0.0625f, hi[2]));
-        const float4 z1y1l = add4(z0y1l, add4(scale4(0.0625f, lo[2]), scale4(0.015625f, lo[3])));
-        const float4 z1y1h = add4(z0y1h, add4(scale4(0.0625f, hi[2]), scale4(0.015625f, hi[3])));
-        put(surf, fmt, x0, y0, 0, true, lo[0]);
-        put(surf, fmt, x0 + 1, y0, 0, true, hi[0]);
-        put(surf, fmt, x0, y0 + 1, 0, true, z0y1l);
-        put(surf, fmt, x0 + 1, y0 + 1, 0, true, z0y1h);
-        put(surf, fmt, x0, y0, 1, true, z1y0l);
-        put(surf, fmt, x0 + 1, y0, 1, true, z1y0h);
-        put(surf, fmt, x0, y0 + 1, 1, true, z1y1l);
-        put(surf, fmt, x0 + 1, y0 + 1, 1, true, z1y1h);
-    } else {
-        float4 d1, dl, d2, dl2;
-        seiler_terms(b, d, d1, dl, d2, dl2);
-        if (KIND == TK_SEIL2) {
-            put(surf, fmt, x0, y0, 0, false, b[0]);
-            put(surf, fmt, x0 + 1, y0, 0, false, b[d]);
-            put(surf, fmt, x0, y0 + 1, 0, false, add4(b[0], d1));
-            put(surf, fmt, x0 + 1, y0 + 1, 0, false, add4(b[d], dl));
-        } else {
-            put(surf, fmt, x0, y0, 0, true, b[0]);
-            put(surf, fmt, x0 + 1, y0, 0, true, b[d]);
-            put(surf, fmt, x0, y0 + 1, 0, true, b[0]);
-            put(surf, fmt, x0 + 1, y0 + 1, 0, true, b[d]);
-            const float4 s1 = add4(b[0], d1), s2 = add4(b[d], dl);
-            put(surf, fmt, x0, y0, 1, true, s1);
-            put(surf, fmt, x0 + 1, y0, 1, true, s2);
-            put(surf, fmt, x0, y0 + 1, 1, true, add4(s1, d2));
-            put(surf, fmt, x0 + 1, y0 + 1, 1, true, add4(s2, dl2));
-        }
+    const bool is3d = KIND == TK_DC3 || KIND == TK_DCN || KIND == TK_SEIL3 || KIND == TK_SEIL3Q;
+    if (fmt < 2) {
+        tile_texels<KIND>(b, d, ta.wt, [&](int x, int y, int z, float4 v) { put(surf, fmt, x0 + x, y0 + y, z, is3d, v); });
+        return;
     }
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, INFINITY), hi = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+    tile_texels<KIND>(b, d, ta.wt, [&](int, int, int, float4 v) {
+        lo = min4(lo, v);
+        hi = max4(hi, v);
+    });
+    float4 sc = sub4(hi, lo);
+    // a constant component maps to code 0; its scale is irrelevant but must not divide by 0
+    sc = make_float4(sc.x > 0.f ? sc.x : 1.f, sc.y > 0.f ? sc.y : 1.f, sc.z > 0.f ? sc.z : 1.f, sc.w > 0.f ? sc.w : 1.f);
+    ta.rescale[2 * c] = lo;
+    ta.rescale[2 * c + 1] = sc;
+    tile_texels<KIND>(b, d, ta.wt, [&](int x, int y, int z, float4 v) {
+        const float4 u = make_float4(__fdiv_rn(v.x - lo.x, sc.x), __fdiv_rn(v.y - lo.y, sc.y), __fdiv_rn(v.z - lo.z, sc.z),
+                                     __fdiv_rn(v.w - lo.w, sc.w));
+        put(surf, fmt, x0 + x, y0 + y, z, is3d, u);
+    });
 }
 
 // ---------------------------------------------------------------- evaluators
@@ -282,12 +341,30 @@ __device__ __forceinline__ float seg_len4(float4 p, float4 q)
     return sqrt_approx(fmaf(ew, ew, fmaf(ez, ez, fmaf(ey, ey, ex * ex))));
 }
 
+// per-curve (offset, scale) of a unorm tile; identity for float / half texels
+struct Rescale {
+    float4 lo, sc;
+    bool on;
+    __device__ __forceinline__ Rescale(const TexArgs& ta, int64_t c) : on(ta.rescale != nullptr)
+    {
+        if (on) {
+            lo = ta.rescale[2 * c];
+            sc = ta.rescale[2 * c + 1];
+        }
+    }
+    __device__ __forceinline__ float4 operator()(float4 f) const
+    {
+        if (!on) return f;
+        return make_float4(fmaf(sc.x, f.x, lo.x), fmaf(sc.y, f.y, lo.y), fmaf(sc.z, f.z, lo.z), fmaf(sc.w, f.w, lo.w));
+    }
+};
+
 template <int KIND, int TM>
 __device__ __forceinline__ float4 tex_eval(const CurveArgs& a, const TexArgs& ta, int64_t c, int j, uint32_t kc,
-                                           float xb, float yb)
+                                           float xb, float yb, const Rescale& rs)
 {
     const float t = param<TM>(a, c, j, kc);
-    float4 P = tex_point<KIND>(ta, xb, yb, t);
+    float4 P = rs(tex_point<KIND>(ta, xb, yb, t));
     if (TM == TM_ARRAY && t != t) P = make_float4(t, t, t, t);  // NaN parameter -> NaN point
     return P;
 }
@@ -304,13 +381,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex(const CurveArgs a, const Te
         const float xb = (float)((int)(c % ta.tw) * ta.wt) + 0.5f;
         const float yb = (float)((int)(c / ta.tw) * 2) + 0.5f;
         const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
+        const Rescale rs(ta, c);
         const int n_t = a.n_t;
         if (OM == OM_POINTS) {
             float* stage = s_stage + wib * 32 * 4;
             for (int j0 = 0; j0 < n_t; j0 += 32) {
                 const int j = j0 + lane;
                 float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < n_t) P = tex_eval<KIND, TM>(a, ta, c, j, kc, xb, yb);
+                if (j < n_t) P = tex_eval<KIND, TM>(a, ta, c, j, kc, xb, yb, rs);
                 const float pv[4] = {P.x, P.y, P.z, P.w};
                 for (int k = 0; k < dim; ++k) stage[lane * dim + k] = pv[k];
                 __syncwarp();
@@ -326,10 +404,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex(const CurveArgs a, const Te
             float acc = 0.f;
             float4 first = make_float4(0.f, 0.f, 0.f, 0.f), prev = first;
             if (jb < je) {
-                first = prev = tex_eval<KIND, TM>(a, ta, c, jb, kc, xb, yb);
+                first = prev = tex_eval<KIND, TM>(a, ta, c, jb, kc, xb, yb, rs);
 #pragma unroll 4
                 for (int j = jb + 1; j < je; ++j) {
-                    const float4 P = tex_eval<KIND, TM>(a, ta, c, j, kc, xb, yb);
+                    const float4 P = tex_eval<KIND, TM>(a, ta, c, j, kc, xb, yb, rs);
                     acc += seg_len4(P, prev);
                     prev = P;
                 }
@@ -349,10 +427,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex(const CurveArgs a, const Te
 // ---------------------------------------------------------------- dispatch
 
 template <int KIND>
-LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, int wt, cudaStream_t s,
+LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, int wt, float4* rescale, cudaStream_t s,
                          const LaunchHooks& h)
 {
-    TexArgs ta{at.tex, tw, wt, a.degree};
+    TexArgs ta{at.tex, tw, wt, a.degree, rescale};
     h.count(h.self);
     k_pack<KIND><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, at.surf, at.fmt);
     cudaError_t err = cudaGetLastError();
@@ -386,11 +464,39 @@ static int tiles_per_row(int64_t n, int wt, int max_w)
     return tw;
 }
 
-LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, TexState& ts, cudaStream_t s,
-                              const LaunchHooks& h)
+// texel format of a call: float4 / half4 by the control-point type, or the
+// requested unorm format
+static int texel_format(const CurveArgs& a, int tex_format)
+{
+    return tex_format == 1 ? 2 : tex_format == 2 ? 3 : (a.dtype == 1 ? 1 : 0);
+}
+
+// per-curve rescale pairs of unorm tiles (context scratch, grown on demand)
+static cudaError_t rescale_buffer(TexState& ts, int fmt, int64_t n, float4** out)
+{
+    *out = nullptr;
+    if (fmt < 2) return cudaSuccess;
+    if (ts.rescale_cap < n) {
+        if (ts.rescale) {
+            cudaError_t e = cudaDeviceSynchronize();  // the old buffer may still be read
+            if (e != cudaSuccess) return e;
+            cudaFree(ts.rescale);
+            ts.rescale = nullptr;
+            ts.rescale_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&ts.rescale, (size_t)n * 2 * sizeof(float4));
+        if (e != cudaSuccess) return e;
+        ts.rescale_cap = n;
+    }
+    *out = ts.rescale;
+    return cudaSuccess;
+}
+
+LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, int tex_format, TexState& ts,
+                              cudaStream_t s, const LaunchHooks& h)
 {
     const int d = a.degree;
-    const int fmt = a.dtype == 1 ? 1 : 0;
+    const int fmt = texel_format(a, tex_format);
     int kind, wt;
     bool is3d;
     if (variant == 6) {  // BEZ_VAR_TEX_DECASTELJAU
@@ -416,14 +522,16 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, T
                 : kind == TK_SEIL2 ? ts.seil2 : ts.seil3;   // SEIL3 and SEIL3Q share the 2x2x2 atlas
     cudaError_t e = atlas_ensure(at, tw * wt, (int)h_needed, is3d ? 2 : 0, fmt);
     if (e != cudaSuccess) return {0, e};
+    float4* rs = nullptr;
+    if ((e = rescale_buffer(ts, fmt, a.n_curves, &rs)) != cudaSuccess) return {0, e};
     switch (kind) {
-    case TK_DC3: return launch_kind<TK_DC3>(a, tm, om, at, tw, wt, s, h);
-    case TK_DCN: return launch_kind<TK_DCN>(a, tm, om, at, tw, wt, s, h);
-    case TK_HYB3: return launch_kind<TK_HYB3>(a, tm, om, at, tw, wt, s, h);
-    case TK_HYBN: return launch_kind<TK_HYBN>(a, tm, om, at, tw, wt, s, h);
-    case TK_SEIL2: return launch_kind<TK_SEIL2>(a, tm, om, at, tw, wt, s, h);
-    case TK_SEIL3: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, s, h);
-    default: return launch_kind<TK_SEIL3Q>(a, tm, om, at, tw, wt, s, h);
+    case TK_DC3: return launch_kind<TK_DC3>(a, tm, om, at, tw, wt, rs, s, h);
+    case TK_DCN: return launch_kind<TK_DCN>(a, tm, om, at, tw, wt, rs, s, h);
+    case TK_HYB3: return launch_kind<TK_HYB3>(a, tm, om, at, tw, wt, rs, s, h);
+    case TK_HYBN: return launch_kind<TK_HYBN>(a, tm, om, at, tw, wt, rs, s, h);
+    case TK_SEIL2: return launch_kind<TK_SEIL2>(a, tm, om, at, tw, wt, rs, s, h);
+    case TK_SEIL3: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, rs, s, h);
+    default: return launch_kind<TK_SEIL3Q>(a, tm, om, at, tw, wt, rs, s, h);
     }
 }
 
@@ -439,14 +547,14 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, T
 template <int S, bool FIRST, bool FULL>
 __device__ __forceinline__ void coissue_group(const Eval<VAR_HORNER_CENTRED, 3, 3>& e, const TexArgs& ta, float xb,
                                               float yb, uint32_t kg, int n, float (&first)[3], float (&last)[3],
-                                              float& acc)
+                                              float& acc, const Rescale& rs)
 {
     float4 T[S];
 #pragma unroll
     for (int i = 0; i < S; ++i) {
         if (FULL || i < n) {
             const float t = hash_one_plus(lowbias32_premixed(kg ^ (uint32_t)i, 0u)) - 1.0f;
-            T[i] = tex2D<float4>(ta.tex, xb + t, yb + fmaf(-t, t, t));
+            T[i] = rs(tex2D<float4>(ta.tex, xb + t, yb + fmaf(-t, t, t)));
         }
     }
 #pragma unroll
@@ -491,6 +599,7 @@ __global__ void __launch_bounds__(kWarps * 32, S <= 1 ? 5 : 4) k_coissue(const C
         const uint32_t km = curve_key<TM_HASH16>(a, c);
         const float xb = (float)((int)(c % ta.tw) * ta.wt) + 0.5f;
         const float yb = (float)((int)(c / ta.tw) * 2) + 0.5f;
+        const Rescale rs(ta, c);
         const int n_t = a.n_t;
         // 8-aligned runs: sample g + i of a group starting at g has index g ^ i
         const int chunk = ((n_t + 31) / 32 + 7) & ~7;
@@ -499,10 +608,11 @@ __global__ void __launch_bounds__(kWarps * 32, S <= 1 ? 5 : 4) k_coissue(const C
         float acc = 0.f;
         float first[3] = {0.f, 0.f, 0.f}, last[3] = {0.f, 0.f, 0.f};
         if (jb < je) {
-            coissue_group<S, true, false>(e, ta, xb, yb, km ^ (uint32_t)jb, je - jb, first, last, acc);
+            coissue_group<S, true, false>(e, ta, xb, yb, km ^ (uint32_t)jb, je - jb, first, last, acc, rs);
             int g = jb + 8;
-            for (; g + 8 <= je; g += 8) coissue_group<S, false, true>(e, ta, xb, yb, km ^ (uint32_t)g, 8, first, last, acc);
-            if (g < je) coissue_group<S, false, false>(e, ta, xb, yb, km ^ (uint32_t)g, je - g, first, last, acc);
+            for (; g + 8 <= je; g += 8)
+                coissue_group<S, false, true>(e, ta, xb, yb, km ^ (uint32_t)g, 8, first, last, acc, rs);
+            if (g < je) coissue_group<S, false, false>(e, ta, xb, yb, km ^ (uint32_t)g, je - g, first, last, acc, rs);
         }
         float pl[3];
 #pragma unroll
@@ -513,16 +623,19 @@ __global__ void __launch_bounds__(kWarps * 32, S <= 1 ? 5 : 4) k_coissue(const C
     }
 }
 
-LaunchResult launch_tex_coissue(const CurveArgs& a, int share, TexState& ts, cudaStream_t s, const LaunchHooks& h)
+LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, TexState& ts, cudaStream_t s,
+                                const LaunchHooks& h)
 {
     const int wt = 2;
     const int tw = tiles_per_row(a.n_curves, wt, ts.max2d_w);
     const int64_t rows = (a.n_curves + tw - 1) / tw;
     if (rows * 2 > ts.max2d_h) return {0, cudaErrorInvalidValue};
-    const int fmt = a.dtype == 1 ? 1 : 0;
+    const int fmt = texel_format(a, tex_format);
     cudaError_t e = atlas_ensure(ts.seil2, tw * wt, (int)(rows * 2), 0, fmt);
     if (e != cudaSuccess) return {0, e};
-    TexArgs ta{ts.seil2.tex, tw, wt, 3};
+    float4* rs = nullptr;
+    if ((e = rescale_buffer(ts, fmt, a.n_curves, &rs)) != cudaSuccess) return {0, e};
+    TexArgs ta{ts.seil2.tex, tw, wt, 3, rs};
     h.count(h.self);
     k_pack<TK_SEIL2><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, ts.seil2.surf, fmt);
     e = cudaGetLastError();

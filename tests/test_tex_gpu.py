@@ -29,7 +29,7 @@ WERR = 2.0 ** -8 + 2.0 ** -11
 
 
 def _run(torch, ctrl, t=None, n_t=None, variant="TEX_DECASTELJAU", out_mode="POINTS", t_mode=None, seed=0,
-         stream_id=0, half=False, tex_share=0):
+         stream_id=0, half=False, tex_share=0, tex_format="AUTO"):
     from paper_2603_15447_gb300 import bez
     c = torch.from_numpy(ctrl).cuda()
     if half:
@@ -37,7 +37,7 @@ def _run(torch, ctrl, t=None, n_t=None, variant="TEX_DECASTELJAU", out_mode="POI
     tt = None if t is None else torch.from_numpy(np.ascontiguousarray(t, np.float32)).cuda()
     out = bez.bez_eval(c, tt, n_t=n_t, variant=bez.Variant[variant], out_mode=bez.OutMode[out_mode],
                        t_mode=None if t_mode is None else bez.TMode[t_mode], seed=seed, stream_id=stream_id,
-                       tex_share=tex_share)
+                       tex_share=tex_share, tex_format=bez.TexFormat[tex_format])
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -93,20 +93,23 @@ def _seiler_terms_peeled(b):
     return lo, hi
 
 
-def texture_bound(variant, ctrl, texel_eps=U):
+def texture_bound(variant, ctrl, texel_eps=U, texel_q=0.0):
     """Per-curve bound on |P_tex - C| (see module doc).  texel_eps: relative
-    rounding of a stored texel (2^-24 float, 2^-11 half)."""
+    rounding of a stored texel (2^-24 float, 2^-11 half); texel_q: rounding
+    of a unorm texel as a fraction of its tile's range (half a code)."""
     b = ctrl.astype(np.float64)
     B, d1_, dim = b.shape
     d = d1_ - 1
     if variant == "TEX_DECASTELJAU":
         # tile of window i holds b_i..b_(i+3) (degree <= 2: b_0..b_d)
         w = min(d, 3)
-        bound = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0) * w * WERR
+        R = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0)
+        bound = R * (w * WERR + texel_q)
         tex_mag = np.abs(b).max(axis=(1, 2))
     elif variant == "TEX_HYBRID":
         w = min(d, 2)
-        bound = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0) * w * WERR
+        R = np.max([_range(b[:, i:i + w + 1]) for i in range(d - w + 1)], axis=0)
+        bound = R * (w * WERR + texel_q)
         tex_mag = np.abs(b).max(axis=(1, 2))
     elif d >= 6:
         # degree 6, 7 tile: corners L0, L0 + L1/4, L0 + L2/16, L0 + L1/4 + L2/16 + L3/64
@@ -116,7 +119,7 @@ def texture_bound(variant, ctrl, texel_eps=U):
         c2 = lo[0] + lo[2] / 16, hi[0] + hi[2] / 16
         c3 = c1[0] + lo[2] / 16 + lo[3] / 64, c1[1] + hi[2] / 16 + hi[3] / 64
         tiles = np.stack([*c0, *c1, *c2, *c3], 1)
-        bound = 3 * WERR * _range(tiles)
+        bound = (3 * WERR + texel_q) * _range(tiles)
         tex_mag = np.abs(tiles).max(axis=(1, 2))
     else:
         d1, dl, d2, dl2 = _seiler_terms(b)
@@ -128,7 +131,7 @@ def texture_bound(variant, ctrl, texel_eps=U):
         else:
             tiles = np.stack([b0, bd, s1, s2, s1 + d2, s2 + dl2], 1)
             axes = 3
-        bound = axes * WERR * _range(tiles)
+        bound = (axes * WERR + texel_q) * _range(tiles)
         tex_mag = np.abs(tiles).max(axis=(1, 2))
     # texel rounding (Seiler sums, half texels), filter and register-lerp rounding
     slack = (4 * texel_eps + (d + 12) * U) * tex_mag * np.sqrt(dim)
@@ -338,3 +341,44 @@ def test_coissue_default_share_and_unsupported():
         with pytest.raises(bez.BezError) as e:
             bez.bez_eval(args.pop("ctrl"), None, **co, **args)
         assert e.value.status == status
+
+
+@pytest.mark.parametrize("fmt,levels", [("UNORM16", 65535.0), ("UNORM8", 255.0)])
+@pytest.mark.parametrize("variant,d", [("TEX_DECASTELJAU", 3), ("TEX_DECASTELJAU", 5), ("TEX_HYBRID", 3),
+                                       ("TEX_HYBRID", 4), ("TEX_SEILER", 3), ("TEX_SEILER", 5), ("TEX_SEILER", 7)])
+def test_texture_unorm_formats(fmt, levels, variant, d):
+    # Sec. 2.3: unorm texels hold [0, 1]; each tile is stored as
+    # (texel - lo) / scale with its own minimum and range and mapped back
+    # after filtering, so the bound gains half a code of the tile's range
+    # (filtering and the register lerps after it are convex).
+    torch = need_gpu()
+    rng = np.random.default_rng(80 + d)
+    ctrl = rng.uniform(-1, 1, size=(777, d + 1, 3)).astype(np.float32)
+    t = rng.uniform(0, 1, 53).astype(np.float32)
+    got = _run(torch, ctrl, t, variant=variant, tex_format=fmt)
+    ref = oracle.bezier(ctrl, t)
+    err = np.linalg.norm(got - ref, axis=-1).max(axis=1)
+    bound = texture_bound(variant, ctrl, texel_q=0.5 / levels) + 8 * U * np.abs(ctrl).max(axis=(1, 2))
+    assert np.all(err <= bound), (err / bound).max()
+    print(f"\n{variant} d={d} {fmt}: max normalised error {normalised_error(got, ref).max():.3g}")
+
+
+def test_texture_unorm_length_and_unsupported():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(81)
+    ctrl = rng.uniform(-1, 1, size=(64, 4, 3)).astype(np.float32)
+    # the length path applies the same rescale: close to the float-texel length
+    kw = dict(n_t=512, variant="TEX_SEILER", out_mode="POLYLINE_LENGTH", t_mode="HASH", seed=3)
+    l32 = _run(torch, ctrl, **kw)
+    l16 = _run(torch, ctrl, **kw, tex_format="UNORM16")
+    assert np.all(np.abs(l16 - l32) <= 2e-3 * l32)
+    c = torch.from_numpy(ctrl).cuda()
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_piecewise(torch.zeros((2, 9, 3), device="cuda"), 4, 2, n_t=8, t_mode=bez.TMode.UNIFORM,
+                               variant=bez.Variant.TEX_DECASTELJAU, tex_format=bez.TexFormat.UNORM8)
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval(c, None, n_t=8, t_mode=bez.TMode.UNIFORM, variant=bez.Variant.TEX_SEILER, tex_format=7)
+    assert e.value.status == bez.Status.INVALID_ARG
+
