@@ -64,8 +64,10 @@ typedef enum bez_variant {
     BEZ_VAR_TEX_HYBRID = 8,      /* two bilinear reads + FP32 lerp (cubic)               */
     BEZ_VAR_TENSOR = 9,          /* reserved (tensor-core grid contraction, not built:   *
                                   * the grid kernels are bound by their stores)          */
-    BEZ_VAR_COISSUE = 10         /* tex2D Seiler for opts->tex_share of every 8 samples, *
+    BEZ_VAR_COISSUE = 10,        /* tex2D Seiler for opts->tex_share of every 8 samples, *
                                   * centred Horner for the rest, in one kernel           */
+    BEZ_VAR_HALF2 = 11           /* centred Horner in half2 arithmetic (FP16 math, two   *
+                                  * samples per instruction), dim 3, degree 1..7         */
 } bez_variant;
 
 typedef enum bez_dtype { BEZ_F32 = 0, BEZ_F16 = 1, BEZ_BF16 = 2 } bez_dtype;
@@ -162,6 +164,12 @@ bez_status bez_reset_stats(bez_ctx ctx);
  *   h = H(H(key ^ c) ^ j),  key = H(lo(seed) ^ H(hi(seed) ^ H(stream_id))),
  *   H = lowbias32 (Wellons 2018: x^=x>>16; x*=0x7feb352d; x^=x>>15;
  *   x*=0x846ca68b; x^=x>>16), c < 2^32, j < 2^32.
+ *
+ * BEZ_VAR_HALF2: the centred power basis (FP32 setup, FP64 from degree 5)
+ * rounded to half; a lane evaluates two samples per HFMA2.  Parameters are
+ * drawn and lengths accumulated in FP32.  Accuracy is that of 11-bit
+ * arithmetic (about 1e-3 of the curve size for cubics), far from the FP32
+ * forms; dim 3 and degrees 1..7 only (else BEZ_ERR_UNSUPPORTED).
  *
  * BEZ_VAR_COISSUE (Sec. 5: a texture read pays off when it overlaps
  * arithmetic): cubic 3D curves, POLYLINE_LENGTH, BEZ_T_HASH with

@@ -40,6 +40,7 @@ class Variant(enum.IntEnum):
     TEX_HYBRID = 8
     TENSOR = 9
     COISSUE = 10
+    HALF2 = 11
 
 
 class DType(enum.IntEnum):

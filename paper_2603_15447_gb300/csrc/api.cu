@@ -186,7 +186,7 @@ bez_status check_common(bez_ctx c, const bez_opts* o)
     if (o->out_mode < BEZ_OUT_POINTS || o->out_mode > BEZ_OUT_POLYLINE_LENGTH)
         return fail(BEZ_ERR_INVALID_ARG, "bad out_mode %d", o->out_mode);
     if (o->t_mode < BEZ_T_SHARED || o->t_mode > BEZ_T_HASH) return fail(BEZ_ERR_INVALID_ARG, "bad t_mode %d", o->t_mode);
-    if (o->variant < BEZ_VAR_AUTO || o->variant > BEZ_VAR_COISSUE)
+    if (o->variant < BEZ_VAR_AUTO || o->variant > BEZ_VAR_HALF2)
         return fail(BEZ_ERR_INVALID_ARG, "bad variant %d", o->variant);
     if (o->tex_format < BEZ_TEX_AUTO || o->tex_format > BEZ_TEX_UNORM8)
         return fail(BEZ_ERR_INVALID_ARG, "bad tex_format %d", o->tex_format);
@@ -331,8 +331,11 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     const bool coissue = var == BEZ_VAR_COISSUE;
     const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER || var == BEZ_VAR_TEX_HYBRID ||
                      coissue;
-    if (var > BEZ_VAR_TEX_HYBRID && !coissue)
+    const bool half2 = var == BEZ_VAR_HALF2;
+    if (var > BEZ_VAR_TEX_HYBRID && !coissue && !half2)
         return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for bez_eval", var);
+    if (half2 && (dim != 3 || degree > 7))
+        return fail(BEZ_ERR_UNSUPPORTED, "half2 arithmetic evaluates 3D curves of degree 1..7");
     if (coissue) {
         if (degree != 3 || dim != 3 || o->out_mode != BEZ_OUT_POLYLINE_LENGTH || o->t_mode != BEZ_T_HASH ||
             n_t > 65536)
@@ -402,6 +405,7 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     case BEZ_VAR_HORNER_CENTRED: r = launch_curve_horner_centred(a, tm, om, s, h); break;
     case BEZ_VAR_BERNSTEIN: r = launch_curve_bernstein(a, tm, om, s, h); break;
     case BEZ_VAR_DECASTELJAU: r = launch_curve_decasteljau(a, tm, om, s, h); break;
+    case BEZ_VAR_HALF2: r = launch_curve_half2(a, tm, om, s, h); break;
     default: r = launch_curve_seiler(a, tm, om, s, h); break;
     }
     if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");

@@ -35,17 +35,23 @@ __host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x)
     return x;
 }
 
+constexpr uint32_t kLowbiasMul1 = 0x7feb352du;
+
+// lowbias32 from its first product on: y = (x ^ (x >> 16)) * 0x7feb352d
+__device__ __forceinline__ uint32_t lowbias32_tail(uint32_t y)
+{
+    y ^= y >> 15;
+    y *= 0x846ca68bu;
+    y ^= y >> 16;
+    return y;
+}
+
 // lowbias32(k ^ j) for j < 2^16, given km = k ^ (k >> 16): the first
 // xorshift distributes over the xor and j >> 16 == 0, so
 // (k ^ j) ^ ((k ^ j) >> 16) == km ^ j.  Same value, two instructions fewer.
 __device__ __forceinline__ uint32_t lowbias32_premixed(uint32_t km, uint32_t j)
 {
-    uint32_t x = km ^ j;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
+    return lowbias32_tail((km ^ j) * kLowbiasMul1);
 }
 
 // 1 + (23 high bits of h) 2^-23, in [1,2): (0x7f : h) >> 9 == 0x3f800000 | (h >> 9),

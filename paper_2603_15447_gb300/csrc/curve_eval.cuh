@@ -484,43 +484,47 @@ __device__ __forceinline__ float seg_len(const float (&p)[DIM], const float (&q)
 // Evaluate at the pre-mixed draw of sample index x = kg ^ i (TM_HASH16).  The
 // centred form takes u = 1.m - 3/2 in one subtraction: 1.m - 1 and then - 1/2
 // are both exact, so the value is the same as eval(t).
+// `at` takes the draw's first product y = (km ^ j) * 0x7feb352d.
 template <class E>
 struct DrawEval {
     template <int DIM>
-    __device__ __forceinline__ static void at(const E& e, uint32_t x, float (&P)[DIM])
+    __device__ __forceinline__ static void at(const E& e, uint32_t y, float (&P)[DIM])
     {
-        e.eval(hash_one_plus(lowbias32_premixed(x, 0u)) - 1.0f, P);
+        e.eval(hash_one_plus(lowbias32_tail(y)) - 1.0f, P);
     }
 };
 template <int D, int DIM0>
 struct DrawEval<Eval<VAR_HORNER_CENTRED, D, DIM0>> {
     template <int DIM>
-    __device__ __forceinline__ static void at(const Eval<VAR_HORNER_CENTRED, D, DIM0>& e, uint32_t x,
+    __device__ __forceinline__ static void at(const Eval<VAR_HORNER_CENTRED, D, DIM0>& e, uint32_t y,
                                               float (&P)[DIM])
     {
-        e.eval_u(hash_one_plus(lowbias32_premixed(x, 0u)) - 1.5f, P);
+        e.eval_u(hash_one_plus(lowbias32_tail(y)) - 1.5f, P);
     }
 };
 
 // Polyline length over the samples [jb, je) of one lane with the pre-mixed
 // draw.  jb is a multiple of 4, so sample jb + i (i < 4) has index
 // (jb + i) == (g ^ i) for its group start g and km ^ (g ^ i) == (km ^ g) ^ i:
-// one xor per sample gives the draw's input.  `first` and `last` return the
-// run's end points for the join with the neighbouring lanes.
+// one xor per sample gives the draw's input.  (Splitting the draw's first
+// product into a per-group and a per-curve term saves that multiply but
+// needs four more registers per lane, and measured slower.)  `first` and
+// `last` return the run's end points for the join with the neighbouring
+// lanes.
 template <class E, int DIM>
 __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb, int je, float (&first)[DIM],
                                                 float (&last)[DIM])
 {
     float acc = 0.f;
     const uint32_t k0 = km ^ (uint32_t)jb;
-    DrawEval<E>::at(e, k0, first);
+    DrawEval<E>::at(e, k0 * kLowbiasMul1, first);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) last[k] = first[k];
 #pragma unroll
     for (int i = 1; i < 4; ++i) {
         if (jb + i < je) {
             float P[DIM];
-            DrawEval<E>::at(e, k0 ^ (uint32_t)i, P);
+            DrawEval<E>::at(e, (k0 ^ (uint32_t)i) * kLowbiasMul1, P);
             acc += seg_len<DIM>(P, last);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) last[k] = P[k];
@@ -533,7 +537,7 @@ __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb,
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float P[DIM];
-            DrawEval<E>::at(e, kg ^ (uint32_t)i, P);
+            DrawEval<E>::at(e, (kg ^ (uint32_t)i) * kLowbiasMul1, P);
             acc += seg_len<DIM>(P, last);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) last[k] = P[k];
@@ -545,7 +549,7 @@ __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb,
         for (int i = 0; i < 3; ++i) {
             if (g + i < je) {
                 float P[DIM];
-                DrawEval<E>::at(e, kg ^ (uint32_t)i, P);
+                DrawEval<E>::at(e, (kg ^ (uint32_t)i) * kLowbiasMul1, P);
                 acc += seg_len<DIM>(P, last);
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) last[k] = P[k];
@@ -587,7 +591,7 @@ struct CtrlRegs {
 };
 
 template <int VAR, int D, int DIM, int TM, int OM>
-__global__ void __launch_bounds__(kWarps * 32, 6) k_curve(const CurveArgs a)
+__global__ void __launch_bounds__(kWarps * 32, 5) k_curve(const CurveArgs a)
 {
     using E = typename Pick<VAR, D, DIM>::type;
     constexpr int N = E::N;

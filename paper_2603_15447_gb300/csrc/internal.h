@@ -46,6 +46,8 @@ LaunchResult launch_curve_horner_centred(const CurveArgs& a, int tm, int om, cud
 LaunchResult launch_curve_bernstein(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_curve_decasteljau(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_curve_seiler(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
+// centred Horner in half2 arithmetic (dim 3, degree 1..7)
+LaunchResult launch_curve_half2(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 
 // ---------------------------------------------------------------- textures
 

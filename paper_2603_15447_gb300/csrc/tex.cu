@@ -566,7 +566,7 @@ __device__ __forceinline__ void coissue_group(const Eval<VAR_HORNER_CENTRED, 3, 
                 P[1] = T[i < S ? i : 0].y;
                 P[2] = T[i < S ? i : 0].z;
             } else {
-                DrawEval<Eval<VAR_HORNER_CENTRED, 3, 3>>::at(e, kg ^ (uint32_t)i, P);
+                DrawEval<Eval<VAR_HORNER_CENTRED, 3, 3>>::at(e, (kg ^ (uint32_t)i) * kLowbiasMul1, P);
             }
             if (FIRST && i == 0) {
 #pragma unroll

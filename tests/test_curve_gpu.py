@@ -246,3 +246,72 @@ def test_launch_accounting_and_timing():
     s = ctx.stats()
     ctx.set_timing(False)
     assert s["launches"] == 3 and s["timed_launches"] == 3 and s["timed_ms"] > 0
+
+
+def _centred_coeffs(ctrl):
+    """Power coefficients about t = 1/2 of each Bezier curve, FP64 [B][d+1][dim]."""
+    from math import comb
+    from numpy.polynomial import polynomial as Pn
+    B, d1, dim = ctrl.shape
+    d = d1 - 1
+    out = np.zeros((B, d1, dim))
+    shift = np.array([0.5, 1.0])  # t = u + 1/2
+    for c in range(B):
+        for k in range(dim):
+            poly = np.zeros(d1)
+            for i in range(d1):
+                basis = comb(d, i) * Pn.polymul(Pn.polypow([1.0, -1.0], d - i), Pn.polypow([0.0, 1.0], i))
+                poly = Pn.polyadd(poly, float(ctrl[c, i, k]) * basis)[:d1]
+            comp = np.zeros(1)
+            for i in reversed(range(d1)):          # Horner composition poly(u + 1/2)
+                comp = Pn.polyadd(Pn.polymul(comp, shift), [poly[i]])
+            out[c, :, k] = np.pad(comp, (0, d1 - len(comp)))[:d1]
+    return out
+
+
+@pytest.mark.parametrize("d", [1, 3, 5, 7])
+@pytest.mark.parametrize("t_mode", ["SHARED", "HASH"])
+def test_half2_arithmetic_points(d, t_mode):
+    # Centred Horner in half2: coefficients rounded to half (2^-11), u = t - 1/2
+    # rounded to half (2^-13 absolute, times |C'|), and 2d half FMAs, each
+    # rounding by 2^-11 of a partial sum bounded by S = sum_i |c_i| |u|^i.
+    torch = need_gpu()
+    rng = np.random.default_rng(300 + d)
+    n = 257
+    ctrl = _ctrl(rng, n, d, 3)
+    if t_mode == "SHARED":
+        t = rng.uniform(0, 1, 131).astype(np.float32)
+        got = _run(torch, ctrl, t, variant="HALF2")
+        tt = np.broadcast_to(t, (n, t.size))
+    else:
+        got = _run(torch, ctrl, n_t=131, variant="HALF2", t_mode="HASH", seed=4, stream_id=1)
+        tt = oracle.hash_t(4, 1, 0, n, 131)
+    ref = oracle.bezier(ctrl, tt if t_mode == "HASH" else t)
+    c = _centred_coeffs(ctrl.astype(np.float64))                       # [n][d+1][3]
+    u = np.abs(tt.astype(np.float64) - 0.5)                            # [n][n_t]
+    S = np.einsum("nik,nti->ntk", np.abs(c), u[..., None] ** np.arange(d + 1))
+    dmax = np.abs(np.diff(ctrl.astype(np.float64), axis=1)).max(axis=1)   # [n][3]
+    tol = (2 * d + 4) * 2.0 ** -11 * S + 2.0 ** -12 * d * dmax[:, None, :] + 1e-6
+    assert np.all(np.abs(got - ref) <= tol)
+    print(f"\nHALF2 d={d} {t_mode}: max normalised error {normalised_error(got, ref).max():.3g}")
+
+
+@pytest.mark.parametrize("n_t", [1024, 77, 1])
+def test_half2_length_is_polyline_of_its_points(n_t):
+    torch = need_gpu()
+    rng = np.random.default_rng(310)
+    ctrl = _ctrl(rng, 129, 3, 3)
+    kw = dict(n_t=n_t, variant="HALF2", t_mode="HASH", seed=8, stream_id=2)
+    L = _run(torch, ctrl, out_mode="POLYLINE_LENGTH", **kw)
+    pts = _run(torch, ctrl, **kw).astype(np.float64)
+    want = oracle.polyline_length(pts)
+    assert np.all(np.abs(L - want) <= (n_t / 32 + 12) * 2.0 ** -24 * want + 1e-7)
+
+
+def test_half2_unsupported():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    for shape in [(4, 4, 2), (4, 9, 3)]:
+        with pytest.raises(bez.BezError) as e:
+            bez.bez_eval(torch.zeros(shape, device="cuda"), torch.zeros(3, device="cuda"), variant=bez.Variant.HALF2)
+        assert e.value.status == bez.Status.UNSUPPORTED
