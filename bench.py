@@ -55,10 +55,10 @@ T_OPS, LEN_OPS = 9, 8
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels, per unit of work; null in the JSON line for other kernels.  The
-# curve kernel was captured on 131,072 curves (6,305,280 B: the control
+# curve kernel was captured on 131,072 curves (6,308,352 B: the control
 # points; the 4 B lengths stay in L2) and scales with the curve count; the
 # surface kernel on the full 65,536-patch tensor workload.
-TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6305280 / 131072}
+TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6308352 / 131072}
 TRAFFIC_SURFACE_65536 = 12626688 + 743121664
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
             "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
@@ -535,6 +535,10 @@ def run_tensor(args):
     tex = bez.Variant.TEX_DECASTELJAU
     ms_t, st_t = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=tex, out=so, ctx=ctx), args.steps,
                            args.warmup)
+    texs = bez.Variant.TEX_SEILER
+    ms_ts, st_ts = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx), args.steps,
+                             args.warmup)
+    kts = st_ts["timed_ms"] / st_ts["timed_launches"]
     n_s, n_v = 65536 * 1024, 4096 * 4096
     ks = st_s["timed_ms"] / st_s["timed_launches"]
     kv = st_v["timed_ms"] / st_v["timed_launches"]
@@ -558,7 +562,11 @@ def run_tensor(args):
                       "surface_max_norm_err": surf_err(bez.Variant.AUTO),
                       "surface_tex": {"points_per_s": n_s * args.steps / (ms_t * 1e-3), "kernel_ms": kt,
                                       "gbs": n_s * 12 / (kt * 1e-3) / 1e9, "max_norm_err": surf_err(tex),
-                                      "kernel": "k_surface_tex<3> (one trilinear read per row and coordinate)"}},
+                                      "kernel": "k_surface_tex<3> (one trilinear read per row and coordinate)"},
+                      "surface_tex_seiler": {"points_per_s": n_s * args.steps / (ms_ts * 1e-3), "kernel_ms": kts,
+                                             "gbs": n_s * 12 / (kts * 1e-3) / 1e9, "max_norm_err": surf_err(texs),
+                                             "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
+                                                       "coordinate)"}},
                      traffic=TRAFFIC_SURFACE_65536)
 
 

@@ -261,6 +261,9 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
  *   storage): per patch and coordinate a 2x2x2 RGBA texture tile holds the
  *   four column cubics (Sec. 2.2); one trilinear read at (u,u,u) per grid
  *   row gives the isoline control points, the cubic in v runs in FP32.
+ *   variant TEX_SEILER (same limits): the four column cubics in the 2x2
+ *   cubic Seiler layout (Sec. 4), one per channel of a 2D tile, read
+ *   bilinearly at (u, u (1 - u)).
  *   Accuracy is that of 8-bit filter weights (about 3 x 2^-8 of the column
  *   range); the tiles live in a context-owned atlas, so texture calls of one
  *   context are ordered on the device.  Other combinations return

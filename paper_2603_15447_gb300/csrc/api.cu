@@ -273,6 +273,7 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.chain);
     atlas_free(c->tex.probe);
     atlas_free(c->tex.surf3);
+    atlas_free(c->tex.surf2);
     cudaFree(c->tex.rescale);
     if (c->tex_done) cudaEventDestroy(c->tex_done);
     delete c;
@@ -606,11 +607,11 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     if (nu > 256 || nv > 256 || nw > 256) return fail(BEZ_ERR_UNSUPPORTED, "grids above 256 per axis");
     if (o->out_mode != BEZ_OUT_POINTS) return fail(BEZ_ERR_UNSUPPORTED, "surfaces and volumes output points");
     const int var = o->variant;
-    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU;
+    const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER;
     if (var != BEZ_VAR_AUTO && var != BEZ_VAR_BERNSTEIN && !tex)
         return fail(BEZ_ERR_UNSUPPORTED,
                     "variant %d: grids run on CUDA cores (AUTO / BERNSTEIN) or, for bicubic surfaces, through "
-                    "texture tiles (TEX_DECASTELJAU)", var);
+                    "texture tiles (TEX_DECASTELJAU, TEX_SEILER)", var);
     if (tex && (vol || du != 3 || dv != 3))
         return fail(BEZ_ERR_UNSUPPORTED, "texture tiles hold bicubic surfaces only");
     if (tex && o->tex_format != BEZ_TEX_AUTO)
@@ -645,7 +646,7 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     if (tex) {
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        LaunchResult r = launch_tex_surface(t, c->tex, s, hooks_of(c));
+        LaunchResult r = launch_tex_surface(t, var == BEZ_VAR_TEX_SEILER, c->tex, s, hooks_of(c));
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "%lld patches do not fit one texture atlas", (long long)n);
         if (r.err != cudaSuccess) return cuda_fail(r.err, "texture surface launch");

@@ -106,13 +106,22 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s,
     }
     float yh[P + 1], yl[P + 1];  // Y_i ~ yh_i + yl_i
     if (spline) {
+        constexpr int S = kOpRowStride(P);
         const float2* M = a.op_pool + a.span_ops[a.op_off[c] + s];
 #pragma unroll
         for (int i = 0; i <= P; ++i) {
             float sh = 0.f, corr = 0.f;
+            float2 row[S];
+            const float4* r4 = reinterpret_cast<const float4*>(M + i * S);  // 16-byte aligned rows
+#pragma unroll
+            for (int q2 = 0; q2 < S / 2; ++q2) {
+                const float4 v = __ldg(r4 + q2);
+                row[2 * q2] = make_float2(v.x, v.y);
+                row[2 * q2 + 1] = make_float2(v.z, v.w);
+            }
 #pragma unroll
             for (int j = 0; j <= P; ++j) {
-                const float2 m = __ldg(M + i * (P + 1) + j);
+                const float2 m = row[j];
                 const float pr = __fmul_rn(m.x, xh[j]);
                 float e = fmaf(m.x, xh[j], -pr);       // exact: m.x xh_j = pr + e
                 e = fmaf(m.x, xl[j], e);               // lower-order terms
@@ -148,7 +157,7 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s,
 }
 
 // Span extraction, one thread per (curve, span, component).
-__global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a)
+__global__ void __launch_bounds__(256, 4) k_batch_setup(const BatchArgs a)
 {
     const int per = a.dim + 1;  // component slots per span (dim + 1 for homogeneous NURBS)
     const int64_t total = a.n_span_tab * per;

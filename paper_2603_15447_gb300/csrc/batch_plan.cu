@@ -363,8 +363,14 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
                     for (double v : M) mk.push_back(std::llround(v * 1099511627776.0));  // 2^40
                     auto mt = mat_index.find(mk);
                     if (mt == mat_index.end()) {
+                        // rows padded to an even length (zeros) so the device
+                        // reads each row as 16-byte pairs of entries
                         mt = mat_index.emplace(mk, (int64_t)ops.size()).first;
-                        ops.insert(ops.end(), M.begin(), M.end());
+                        const int stride = kOpRowStride(p);
+                        for (int i = 0; i <= p; ++i) {
+                            ops.insert(ops.end(), M.begin() + i * (p + 1), M.begin() + (i + 1) * (p + 1));
+                            ops.insert(ops.end(), (size_t)(stride - (p + 1)), 0.0);
+                        }
                     }
                     span_ops.push_back(mt->second);
                 }

@@ -72,6 +72,7 @@ struct TexState {
     Atlas chain;  // zig-zag C0 chain textures
     Atlas probe;  // 2x2x2 weight probe
     Atlas surf3;  // bicubic surface tiles: four column cubics per 2x2x2 RGBA tile
+    Atlas surf2;  // bicubic surface tiles in the 2x2 Seiler layout, one column cubic per channel
     float4* rescale = nullptr;  // unorm tiles: per curve (offset, scale)
     int64_t rescale_cap = 0;    // curves the rescale buffer holds
     int max3d = 16384, max2d_w = 131072, max2d_h = 65536;
@@ -136,7 +137,8 @@ struct TensorLaunch {
 LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const LaunchHooks& h);
 // Bicubic surfaces through 2x2x2 RGBA texture tiles (nu <= kSurfTexMaxRows).
 constexpr int kSurfTexMaxRows = 64;
-LaunchResult launch_tex_surface(const TensorLaunch& t, TexState& ts, cudaStream_t s, const LaunchHooks& h);
+LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, TexState& ts, cudaStream_t s,
+                                const LaunchHooks& h);
 size_t tensor_product_smem(const TensorLaunch& t);
 
 // ---------------------------------------------------------------- adjoint
@@ -191,7 +193,8 @@ struct BatchArgs {
     float* out_pool;
     float* span_pool;            // every curve's spans in the evaluation representation
     const int64_t* span_off;     // per curve, floats into span_pool
-    const float2* op_pool;       // span extraction operators of the splines, each entry hi + lo (FP64 -> 2 x FP32)
+    const float2* op_pool;       // span extraction operators of the splines, each entry hi + lo (FP64 -> 2 x FP32),
+                                 // row-major with rows padded to kOpRowStride(p) entries
     const int64_t* op_off;       // per curve, index of its first span in span_ops (splines only)
     const int64_t* span_ops;     // per spline span: offset of its operator matrix in op_pool
     const int2* span_tab;        // (curve, span) of every span: one setup thread each
@@ -205,6 +208,9 @@ struct BatchArgs {
     int32_t grab;                // items taken per atomic
     void* counter;               // one 8-byte work counter per class (atomic schedule)
 };
+// row stride (entries) of a degree-p extraction operator in the batch pool:
+// p + 1 rounded up to even, so every row starts on a 16-byte boundary
+__host__ __device__ constexpr int kOpRowStride(int p) { return (p + 1) + ((p + 1) & 1); }
 constexpr int kBatchClasses = 15;  // 7 degrees x {integral, rational} for 3D curves + generic
 int batch_item_class(const bez_curve_desc& d, int dim);
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,

@@ -9,6 +9,11 @@
 // the FP32 pipes: P[u][v][k] = sum_j B_j(v) X[j][k].  The read happens once
 // per grid row and coordinate and is shared by the nv points of the row.
 //
+// Seiler form (Sec. 4, applied per channel; surfaces are left as future work
+// in Sec. 6): the same four column cubics in the 2x2 cubic Seiler layout of a
+// 2D atlas, read bilinearly at (u, u (1 - u)); two filtered axes instead of
+// three, and a 2D fetch rate.
+//
 // Layout: tile q = p * dim + k sits at texel (2 (q mod tw), 2 (q div tw), 0)
 // of a float4 (or half4) 3D atlas of depth 2; coordinates are unnormalised
 // with texel centres at i + 0.5, so row u reads at (x0+0.5+u, y0+0.5+u,
@@ -35,7 +40,22 @@ __device__ __forceinline__ void put3(cudaSurfaceObject_t s, int fmt, int x, int 
     }
 }
 
-// one thread per tile (patch, coordinate)
+__device__ __forceinline__ void put2(cudaSurfaceObject_t s, int fmt, int x, int y, float4 v)
+{
+    if (fmt == 0) {
+        surf2Dwrite(v, s, x * 16, y);
+    } else {
+        const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+        surf2Dwrite(make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi)), s,
+                    x * 8, y);
+    }
+}
+
+// one thread per tile (patch, coordinate).  SEILER: the 2x2 cubic Seiler
+// layout (Sec. 4) of each column curve in its channel, [[b0, b3],
+// [b0 + d1, b3 + d2]] with d1 = 3 (b1 - b0) - (b3 - b0) and
+// d2 = 3 (b2 - b3) - (b0 - b3), read bilinearly at (u, u (1 - u)).
+template <bool SEILER>
 __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t surf, int fmt)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,6 +71,17 @@ __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t s
         b[i] = make_float4(load_elem(a.ctrl, a.dtype, base), load_elem(a.ctrl, a.dtype, base + dim),
                            load_elem(a.ctrl, a.dtype, base + 2 * dim), load_elem(a.ctrl, a.dtype, base + 3 * dim));
     }
+    if (SEILER) {
+        const float4 d1 = make_float4(3.f * (b[1].x - b[0].x) - (b[3].x - b[0].x), 3.f * (b[1].y - b[0].y) - (b[3].y - b[0].y),
+                                      3.f * (b[1].z - b[0].z) - (b[3].z - b[0].z), 3.f * (b[1].w - b[0].w) - (b[3].w - b[0].w));
+        const float4 d2 = make_float4(3.f * (b[2].x - b[3].x) - (b[0].x - b[3].x), 3.f * (b[2].y - b[3].y) - (b[0].y - b[3].y),
+                                      3.f * (b[2].z - b[3].z) - (b[0].z - b[3].z), 3.f * (b[2].w - b[3].w) - (b[0].w - b[3].w));
+        put2(surf, fmt, x0, y0, b[0]);
+        put2(surf, fmt, x0 + 1, y0, b[3]);
+        put2(surf, fmt, x0, y0 + 1, make_float4(b[0].x + d1.x, b[0].y + d1.y, b[0].z + d1.z, b[0].w + d1.w));
+        put2(surf, fmt, x0 + 1, y0 + 1, make_float4(b[3].x + d2.x, b[3].y + d2.y, b[3].z + d2.z, b[3].w + d2.w));
+        return;
+    }
 #pragma unroll
     for (int z = 0; z < 2; ++z)
 #pragma unroll
@@ -62,7 +93,7 @@ __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t s
 // One warp per patch: lanes read the isoline control points of their rows,
 // then the warp sweeps the grid a row segment of up to 32 points at a time
 // and stores it through a warp-private staging buffer as consecutive floats.
-template <int DIM>
+template <int DIM, bool SEILER>
 __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const TensorArgs a, const SurfTexArgs ta)
 {
     __shared__ float4 s_bv[kTensorMaxGrid];                   // Bv[b][0..3]
@@ -84,7 +115,8 @@ __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const Tensor
             for (int k = 0; k < DIM; ++k) {
                 const int64_t q = p * DIM + k;
                 const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
-                s_x[w][row * DIM + k] = tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
+                s_x[w][row * DIM + k] = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
+                                               : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
             }
         }
         __syncwarp();
@@ -121,7 +153,8 @@ static int surface_tiles_per_row(int64_t tiles, int max_w)
     return tw;
 }
 
-LaunchResult launch_tex_surface(const TensorLaunch& t, TexState& ts, cudaStream_t s, const LaunchHooks& h)
+LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, TexState& ts, cudaStream_t s,
+                                const LaunchHooks& h)
 {
     TensorArgs a{};
     a.ctrl = t.ctrl;
@@ -140,18 +173,27 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, TexState& ts, cudaStream_
     const int64_t rows = (tiles + tw - 1) / tw;
     if (rows * 2 > ts.max3d) return {0, cudaErrorInvalidValue};
     const int fmt = a.dtype == 1 ? 1 : 0;
-    cudaError_t e = atlas_ensure(ts.surf3, tw * 2, (int)(rows * 2), 2, fmt);
+    Atlas& at = seiler ? ts.surf2 : ts.surf3;
+    cudaError_t e = atlas_ensure(at, tw * 2, (int)(rows * 2), seiler ? 0 : 2, fmt);
     if (e != cudaSuccess) return {0, e};
     h.count(h.self);
-    k_pack_surface<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, ts.surf3.surf, fmt);
+    if (seiler) k_pack_surface<true><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt);
+    else k_pack_surface<false><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return {1, e};
-    const void* kern = a.dim == 1   ? (const void*)k_surface_tex<1>
-                       : a.dim == 2 ? (const void*)k_surface_tex<2>
-                       : a.dim == 3 ? (const void*)k_surface_tex<3>
-                                    : (const void*)k_surface_tex<4>;
+    const void* kern;
+    if (seiler)
+        kern = a.dim == 1   ? (const void*)k_surface_tex<1, true>
+               : a.dim == 2 ? (const void*)k_surface_tex<2, true>
+               : a.dim == 3 ? (const void*)k_surface_tex<3, true>
+                            : (const void*)k_surface_tex<4, true>;
+    else
+        kern = a.dim == 1   ? (const void*)k_surface_tex<1, false>
+               : a.dim == 2 ? (const void*)k_surface_tex<2, false>
+               : a.dim == 3 ? (const void*)k_surface_tex<3, false>
+                            : (const void*)k_surface_tex<4, false>;
     const int grid = persistent_grid(kern, kSurfWarps * 32, 0, h.sm_count, (a.n + kSurfWarps - 1) / kSurfWarps);
-    SurfTexArgs sa{ts.surf3.tex, tw};
+    SurfTexArgs sa{at.tex, tw};
     void* args[] = {(void*)&a, (void*)&sa};
     h.count(h.self);
     h.begin(h.self, s);

@@ -250,9 +250,10 @@ def test_texture_unsupported_combinations():
     assert e.value.status == bez.Status.UNSUPPORTED
 
 
+@pytest.mark.parametrize("variant", ["TEX_DECASTELJAU", "TEX_SEILER"])
 @pytest.mark.parametrize("dim,nu,nv,half", [(3, 32, 32, False), (1, 5, 20, False), (2, 64, 256, False),
                                             (4, 17, 9, False), (3, 1, 1, False), (3, 32, 32, True)])
-def test_texture_bicubic_surface(dim, nu, nv, half):
+def test_texture_bicubic_surface(variant, dim, nu, nv, half):
     # Sec. 2.2: a 2x2x2 RGBA tile per coordinate holds the four column cubics
     # C[.][j][k]; one trilinear read at (u,u,u) gives the isoline control
     # points of row u and the cubic in v runs in FP32.  The v stage is a convex
@@ -265,15 +266,25 @@ def test_texture_bicubic_surface(dim, nu, nv, half):
     c = torch.from_numpy(ctrl).cuda()
     if half:
         c = c.half()
-    got = bez.bez_eval_surface(c, nu, nv, variant=bez.Variant.TEX_DECASTELJAU).cpu().numpy().astype(np.float64)
+    got = bez.bez_eval_surface(c, nu, nv, variant=bez.Variant[variant]).cpu().numpy().astype(np.float64)
     src = c.float().cpu().numpy()
     ref = oracle.surface(src, nu, nv)
-    col_range = (src.max(axis=1) - src.min(axis=1)).max(axis=1)            # [n][dim]: max over columns j
-    tol = 3 * WERR * col_range + 8 * U * np.abs(src).max(axis=(1, 2))      # [n][dim]
+    if variant == "TEX_DECASTELJAU":
+        col_range = (src.max(axis=1) - src.min(axis=1)).max(axis=1)        # [n][dim]: max over columns j
+        axes, mag = 3, np.abs(src).max(axis=(1, 2))
+    else:
+        # the column's 2x2 Seiler tile (Sec. 4 cubic layout), per channel j
+        b = src.astype(np.float64)                                         # [n][i][j][k]
+        d1 = 3 * (b[:, 1] - b[:, 0]) - (b[:, 3] - b[:, 0])
+        d2 = 3 * (b[:, 2] - b[:, 3]) - (b[:, 0] - b[:, 3])
+        tile = np.stack([b[:, 0], b[:, 3], b[:, 0] + d1, b[:, 3] + d2], 1)  # [n][4][j][k]
+        col_range = (tile.max(axis=1) - tile.min(axis=1)).max(axis=1)
+        axes, mag = 2, np.abs(tile).max(axis=(1, 2))
+    tol = axes * WERR * col_range + 8 * U * mag                           # [n][dim]
     if half:
         ref_true = oracle.surface(ctrl, nu, nv)
         err_true = np.abs(got - ref_true).max()
-        assert err_true <= (3 * WERR * 2 + 2.0 ** -10)                  # storage rounding on top, |C| <= 1
+        assert err_true <= (axes * WERR * col_range.max() + 2.0 ** -10 * max(1.0, mag.max()))
     err = np.abs(got - ref)                                                # [n][nu][nv][dim]
     assert np.all(err <= tol[:, None, None, :])
     if not half:
