@@ -184,6 +184,43 @@ __global__ void __launch_bounds__(256, 4) k_batch_setup(const BatchArgs a)
 
 // ---------------------------------------------------------------- evaluation
 
+// Grid values t_j = fl32(j) / fl32(n - 1), the IEEE quotient.  For
+// n - 1 < 2^16 without a division: q0 = RN(j r) with r = RN(1 / (n - 1)),
+// then one correction step q0 + RN(j - q0 (n - 1)) r with both steps fused
+// (Markstein's reciprocal-based division, 1990).  For every 0 <= j <= n - 1
+// < 2^16 this equals the IEEE quotient (checked exhaustively, and the exact
+// x = t of a degree-1 test curve is compared bit for bit on the GPU); larger
+// grids divide.
+struct GridDiv {
+    float den, r;
+    bool fast;
+    __device__ __forceinline__ void init(int n)
+    {
+        den = (float)(n - 1);
+        r = __frcp_rn((float)(n > 1 ? n - 1 : 1));
+        fast = n > 1 && n - 1 < 65536;
+    }
+    __device__ __forceinline__ float operator()(int j) const
+    {
+        const float fj = (float)j;
+        if (!fast) return den > 0.f ? __fdiv_rn(fj, den) : 0.f;
+        const float q0 = __fmul_rn(fj, r);
+        return fmaf(fmaf(-q0, den, fj), r, q0);
+    }
+};
+
+// Span of t given the span s of an earlier, smaller parameter of the same
+// run: the residual fma(t, ns, -s) is >= 0 with its exact sign, so s stands
+// unless it reaches 1, when the full selection runs.  Same s and tau as
+// uniform_span(t, ns, tau).
+__device__ __forceinline__ int next_span(float t, int ns, int s, float& tau)
+{
+    const float r = fmaf(t, (float)ns, -(float)s);
+    if (r >= 1.f && s < ns - 1) return uniform_span(t, ns, tau);
+    tau = r;
+    return s;
+}
+
 template <int P, int C, int REPR>
 __device__ __forceinline__ void span_eval(const float (&k)[P + 1][C], float tau, float (&out)[C])
 {
@@ -224,19 +261,23 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
     const int n_spans = it.n_spans;
     const int j0 = it.j0, j1 = it.j1;
     const float* base = a.span_pool + it.span_base;
-    const float den = (float)(n - 1);
+    GridDiv grid;
+    grid.init(n);
     float coef[P + 1][C];
     int cached = -1;
     float* out = a.out_pool + it.out_off;
     for (int tb = j0; tb < j1; tb += kTile) {
         const int my0 = tb + lane * kRun;
+        int s_run = -1;  // span of this lane's previous sample in the run
 #pragma unroll 2
         for (int r = 0; r < kRun; ++r) {
             const int j = my0 + r;
             if (j < j1) {
-                const float t = n > 1 ? __fdiv_rn((float)j, den) : 0.f;
+                const float t = grid(j);
                 float tau = t;
-                const int s = spline ? uniform_span(t, n_spans, tau) : 0;
+                int s = 0;
+                if (spline) s = s_run < 0 ? uniform_span(t, n_spans, tau) : next_span(t, n_spans, s_run, tau);
+                s_run = s;
                 if (s != cached) {
                     const float* src = base + (int64_t)s * (P + 1) * C;
 #pragma unroll
@@ -288,16 +329,20 @@ __device__ void item_generic(const BatchArgs& a, const BatchItem& it, float* sta
     const int comps = rat ? dim + 1 : dim;
     const int n = it.n_samples;
     const int LS = kRun * dim + 1;
-    const float den = (float)(n - 1);
+    GridDiv grid;
+    grid.init(n);
     float* out = a.out_pool + it.out_off;
     for (int tb = j0; tb < j1; tb += kTile) {
         const int my0 = tb + lane * kRun;
+        int s_run = -1;
         for (int r = 0; r < kRun; ++r) {
             const int j = my0 + r;
             if (j >= j1) break;
-            const float t = n > 1 ? __fdiv_rn((float)j, den) : 0.f;
+            const float t = grid(j);
             float tau = t;
-            const int s = spline ? uniform_span(t, n_spans, tau) : 0;
+            int s = 0;
+            if (spline) s = s_run < 0 ? uniform_span(t, n_spans, tau) : next_span(t, n_spans, s_run, tau);
+            s_run = s;
             const float* src = base + (int64_t)s * (p + 1) * comps;
             float pt[kBatchMaxComps];
             for (int q = 0; q < comps; ++q) {

@@ -164,3 +164,34 @@ def test_batch_rejects_bad_descriptors(workload):
     with pytest.raises(bez.BezError) as e:
         bez.bez_eval_batch(_desc(w)[:5], w["dim"], ctrl.cpu(), wts, out)
     assert e.value.status == bez.Status.INVALID_ARG
+
+
+@pytest.mark.parametrize("repr", [0, 1])
+def test_batch_grid_values_are_exact_quotients(repr):
+    # Degree-1 Bezier curves from (0, 0, 0) to (1, 1, 1): with Bezier-point
+    # spans (de Casteljau) every coordinate is lerp(0, 1, t) = t exactly, so
+    # the output is the sample grid t_j = fl32(j) / fl32(n - 1) bit for bit
+    # (the kernels form it without a division for n - 1 < 2^16, by division
+    # above).  The centred power basis gives 1/2 + (t - 1/2): compared at 1e-7.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    ns = np.array([1, 2, 3, 7, 255, 256, 1000, 4097, 65536, 65537, 70001], np.int32)
+    n = len(ns)
+    ctrl = np.tile(np.array([0, 0, 0, 1, 1, 1], np.float32), n)
+    out_off = np.concatenate([[0], np.cumsum(ns.astype(np.int64) * 3)])
+    d = bez.descriptors(np.zeros(n, np.int32), np.ones(n, np.int32), np.full(n, 2, np.int32), ns,
+                        np.arange(n, dtype=np.int64) * 6, np.zeros(n, np.int64), out_off[:-1])
+    out = torch.zeros(int(out_off[-1]), device="cuda")
+    b = bez.Batch(d, 3, torch.from_numpy(ctrl).cuda(), torch.zeros(1, device="cuda"), out, repr=repr)
+    b.launch()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for c in range(n):
+        m = int(ns[c])
+        t = oracle.grid(m).astype(np.float32)
+        pts = got[out_off[c]: out_off[c + 1]].reshape(m, 3)
+        if repr == 0:
+            for k in range(3):
+                np.testing.assert_array_equal(pts[:, k], t)
+        else:
+            assert np.abs(pts - t[:, None]).max() <= 1e-7
