@@ -142,7 +142,7 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s,
             yl[i] = xl[i];
         }
     }
-    float* dst = a.span_pool + a.span_off[c] + (int64_t)s * (P + 1) * comps;
+    float* dst = a.span_pool + a.span_off[c] + (int64_t)s * kSpanStride(P, comps);
     if (a.repr == 1) {
         double Y[P + 1];
 #pragma unroll
@@ -279,11 +279,22 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
                 if (spline) s = s_run < 0 ? uniform_span(t, n_spans, tau) : next_span(t, n_spans, s_run, tau);
                 s_run = s;
                 if (s != cached) {
-                    const float* src = base + (int64_t)s * (P + 1) * C;
+                    // the span's (P + 1) C floats as whole float4s (16-byte aligned)
+                    constexpr int S4 = kSpanStride(P, C) / 4;
+                    const float4* src = reinterpret_cast<const float4*>(base + (int64_t)s * kSpanStride(P, C));
+                    float v[4 * S4];
+#pragma unroll
+                    for (int m = 0; m < S4; ++m) {
+                        const float4 x = __ldg(src + m);
+                        v[4 * m] = x.x;
+                        v[4 * m + 1] = x.y;
+                        v[4 * m + 2] = x.z;
+                        v[4 * m + 3] = x.w;
+                    }
 #pragma unroll
                     for (int i = 0; i <= P; ++i)
 #pragma unroll
-                        for (int q = 0; q < C; ++q) coef[i][q] = __ldg(src + i * C + q);
+                        for (int q = 0; q < C; ++q) coef[i][q] = v[i * C + q];
                     cached = s;
                 }
                 float pt[C];
@@ -343,7 +354,7 @@ __device__ void item_generic(const BatchArgs& a, const BatchItem& it, float* sta
             int s = 0;
             if (spline) s = s_run < 0 ? uniform_span(t, n_spans, tau) : next_span(t, n_spans, s_run, tau);
             s_run = s;
-            const float* src = base + (int64_t)s * (p + 1) * comps;
+            const float* src = base + (int64_t)s * kSpanStride(p, comps);
             float pt[kBatchMaxComps];
             for (int q = 0; q < comps; ++q) {
                 float w[kMaxDegree + 1];

@@ -346,7 +346,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
         const int comps = d.type == BEZ_CURVE_NURBS ? dim + 1 : dim;
         const int n_spans = d.type == BEZ_CURVE_BEZIER ? 1 : d.n_ctrl - d.degree;
         span_off[(size_t)i] = spans;
-        spans += (int64_t)n_spans * (d.degree + 1) * comps;
+        spans += (int64_t)n_spans * kSpanStride(d.degree, comps);  // stays a multiple of 4 floats
         if (d.type != BEZ_CURVE_BEZIER) {
             // knot insertion once per distinct (n_ctrl, degree), in FP64
             const auto key = std::make_pair(d.n_ctrl, d.degree);

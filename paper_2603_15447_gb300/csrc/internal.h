@@ -211,6 +211,10 @@ struct BatchArgs {
 // row stride (entries) of a degree-p extraction operator in the batch pool:
 // p + 1 rounded up to even, so every row starts on a 16-byte boundary
 __host__ __device__ constexpr int kOpRowStride(int p) { return (p + 1) + ((p + 1) & 1); }
+// floats per span of degree p with `comps` components in the batch span pool:
+// (p + 1) comps rounded up to a multiple of 4, so spans (whose pool offsets
+// are multiples of 4 floats) load as whole float4s
+__host__ __device__ constexpr int kSpanStride(int p, int comps) { return ((p + 1) * comps + 3) & ~3; }
 constexpr int kBatchClasses = 15;  // 7 degrees x {integral, rational} for 3D curves + generic
 int batch_item_class(const bez_curve_desc& d, int dim);
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
