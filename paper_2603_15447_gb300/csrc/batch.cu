@@ -33,49 +33,19 @@ constexpr int kItemsPerWarp = 4;  // static schedule: items per warp of a block
 
 // ---------------------------------------------------------------- setup
 
-// Bezier points b[0..P] (FP64, registers) -> power coefficients about 1/2,
-// in place: c_m = binom(P,m) * (Bernstein value at 1/2 of the m-th forward
-// differences)
-template <int P>
-__device__ __forceinline__ void bezier_to_centred_fixed(double (&b)[P + 1])
-{
-    double w[P + 1], c[P + 1];
-#pragma unroll
-    for (int i = 0; i <= P; ++i) w[i] = b[i];
-    double bin = 1.0;
-#pragma unroll
-    for (int m = 0; m <= P; ++m) {
-        double h[P + 1];
-#pragma unroll
-        for (int i = 0; i <= P; ++i) h[i] = w[i];
-#pragma unroll
-        for (int r = 1; r <= P; ++r)
-#pragma unroll
-            for (int i = 0; i < P; ++i)
-                if (r <= P - m && i <= P - m - r) h[i] = 0.5 * (h[i] + h[i + 1]);
-        c[m] = bin * h[0];
-        bin = bin * (double)(P - m) / (double)(m + 1);
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-            if (i < P - m) w[i] = w[i + 1] - w[i];
-    }
-#pragma unroll
-    for (int i = 0; i <= P; ++i) b[i] = c[i];
-}
-
-// Component q of one span of degree P.  The span's Bezier points are its
-// extraction operator (splines; NURBS in homogeneous form) applied to the de
-// Boor points in compensated FP32: each operator entry is an unevaluated sum
-// hi + lo of two floats (48 significant bits), each homogeneous point w P an
-// exact sum (the product's error by one fma), and every row is a Dot2-style
-// compensated dot product (Ogita, Rump & Oishi 2005): products split exactly
-// by fma, partial sums by Knuth's TwoSum, the lower-order terms collected in
-// a correction that is added once at the end.  The result is as accurate as
-// a dot product in twice the working precision, then rounded: the FP64
-// operator's result to within a few units of 2^-48, at FP32 instruction rates
-// (GB300 runs FP64 at a small fraction of FP32).  The power basis about 1/2
-// is then formed in FP64 from the compensated sums.  Results are rounded once
-// to FP32.
+// Component q of one span of degree P in its evaluation representation:
+// Y = A X with A the span's operator -- its extraction operator M (splines;
+// NURBS in homogeneous form), or T_p M / T_p for the power basis about 1/2
+// (T_p, the Bezier -> centred map, is folded into the operators in FP64 on
+// the host), or nothing for a Bezier curve in Bezier points.  Each operator
+// entry is an unevaluated sum hi + lo of two floats (48 significant bits),
+// each homogeneous point w P an exact sum (the product's error by one fma),
+// and every row is a Dot2-style compensated dot product (Ogita, Rump & Oishi
+// 2005): products split exactly by fma, partial sums by Knuth's TwoSum, the
+// lower-order terms collected in a correction added once at the end.  The
+// result is as accurate as a dot product in twice the working precision,
+// then rounded once to FP32, at FP32 instruction rates (GB300 runs FP64 at a
+// small fraction of FP32).
 template <int P>
 __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s, int q, int comps,
                                            const bez_curve_desc& dsc)
@@ -104,60 +74,44 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s,
             xl[i] = 0.f;
         }
     }
-    float yh[P + 1], yl[P + 1];  // Y_i ~ yh_i + yl_i
-    if (spline) {
-        constexpr int S = kOpRowStride(P);
-        const float2* M = a.op_pool + a.span_ops[a.op_off[c] + s];
-#pragma unroll
-        for (int i = 0; i <= P; ++i) {
-            float sh = 0.f, corr = 0.f;
-            float2 row[S];
-            const float4* r4 = reinterpret_cast<const float4*>(M + i * S);  // 16-byte aligned rows
-#pragma unroll
-            for (int q2 = 0; q2 < S / 2; ++q2) {
-                const float4 v = __ldg(r4 + q2);
-                row[2 * q2] = make_float2(v.x, v.y);
-                row[2 * q2 + 1] = make_float2(v.z, v.w);
-            }
-#pragma unroll
-            for (int j = 0; j <= P; ++j) {
-                const float2 m = row[j];
-                const float pr = __fmul_rn(m.x, xh[j]);
-                float e = fmaf(m.x, xh[j], -pr);       // exact: m.x xh_j = pr + e
-                e = fmaf(m.x, xl[j], e);               // lower-order terms
-                e = fmaf(m.y, xh[j], e);
-                const float t = __fadd_rn(sh, pr);     // TwoSum: sh + pr = t + err exactly
-                const float bv = __fsub_rn(t, sh);
-                const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(pr, bv));
-                sh = t;
-                corr = __fadd_rn(corr, __fadd_rn(err, e));
-            }
-            yh[i] = sh;
-            yl[i] = corr;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i <= P; ++i) {
-            yh[i] = xh[i];
-            yl[i] = xl[i];
-        }
-    }
     float* dst = a.span_pool + a.span_off[c] + (int64_t)s * kSpanStride(P, comps);
-    if (a.repr == 1) {
-        double Y[P + 1];
+    if (!spline && a.repr == 0) {
 #pragma unroll
-        for (int i = 0; i <= P; ++i) Y[i] = (double)yh[i] + (double)yl[i];
-        bezier_to_centred_fixed<P>(Y);
+        for (int i = 0; i <= P; ++i) dst[i * comps + q] = xh[i];
+        return;
+    }
+    constexpr int S = kOpRowStride(P);
+    const float2* M = a.op_pool + (spline ? a.span_ops[a.op_off[c] + s] : a.tpow_off[P]);
 #pragma unroll
-        for (int i = 0; i <= P; ++i) dst[i * comps + q] = (float)Y[i];
-    } else {
+    for (int i = 0; i <= P; ++i) {
+        float sh = 0.f, corr = 0.f;
+        float2 row[S];
+        const float4* r4 = reinterpret_cast<const float4*>(M + i * S);  // 16-byte aligned rows
 #pragma unroll
-        for (int i = 0; i <= P; ++i) dst[i * comps + q] = __fadd_rn(yh[i], yl[i]);
+        for (int q2 = 0; q2 < S / 2; ++q2) {
+            const float4 v = __ldg(r4 + q2);
+            row[2 * q2] = make_float2(v.x, v.y);
+            row[2 * q2 + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int j = 0; j <= P; ++j) {
+            const float2 m = row[j];
+            const float pr = __fmul_rn(m.x, xh[j]);
+            float e = fmaf(m.x, xh[j], -pr);       // exact: m.x xh_j = pr + e
+            e = fmaf(m.x, xl[j], e);               // lower-order terms
+            e = fmaf(m.y, xh[j], e);
+            const float t = __fadd_rn(sh, pr);     // TwoSum: sh + pr = t + err exactly
+            const float bv = __fsub_rn(t, sh);
+            const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(pr, bv));
+            sh = t;
+            corr = __fadd_rn(corr, __fadd_rn(err, e));
+        }
+        dst[i * comps + q] = __fadd_rn(sh, corr);
     }
 }
 
 // Span extraction, one thread per (curve, span, component).
-__global__ void __launch_bounds__(256, 4) k_batch_setup(const BatchArgs a)
+__global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a)
 {
     const int per = a.dim + 1;  // component slots per span (dim + 1 for homogeneous NURBS)
     const int64_t total = a.n_span_tab * per;

@@ -99,7 +99,8 @@ struct bez_batch_s {
     std::vector<bez_curve_desc> hdesc;
     bez_curve_desc* d_desc = nullptr;
     int64_t* d_span_off = nullptr;
-    float2* d_ops = nullptr;
+    float2* d_ops = nullptr;    // span operators M (Bezier-point representation)
+    float2* d_ops_c = nullptr;  // T_p M (centred power-basis representation)
     int64_t* d_span_ops = nullptr;
     int64_t* d_op_off = nullptr;
     int2* d_span_tab = nullptr;
@@ -120,6 +121,28 @@ struct bez_batch_s {
 };
 
 namespace {
+
+// T[m][i]: coefficient of Bezier point b_i in the power coefficient c_m about
+// t = 1/2 (degree p), c_m = binom(p, m) * (Bernstein value at 1/2 of the m-th
+// forward differences), by applying the conversion to unit vectors in FP64
+// (entries are small integers over powers of two, exact in FP64).
+void centred_matrix(int p, double (&T)[8][8])
+{
+    for (int i = 0; i <= p; ++i) {
+        double w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        w[i] = 1.0;
+        double bin = 1.0;
+        for (int m = 0; m <= p; ++m) {
+            double h[8];
+            for (int k = 0; k <= p - m; ++k) h[k] = w[k];
+            for (int r = 1; r <= p - m; ++r)
+                for (int k = 0; k <= p - m - r; ++k) h[k] = 0.5 * (h[k] + h[k + 1]);
+            T[m][i] = bin * h[0];
+            bin = bin * (double)(p - m) / (double)(m + 1);
+            for (int k = 0; k < p - m; ++k) w[k] = w[k + 1] - w[k];
+        }
+    }
+}
 
 const BatchStreams* streams_of(bez_batch b) { return b->have_streams ? &b->streams : nullptr; }
 
@@ -198,6 +221,7 @@ bez_status apply_shape(bez_batch b, const Shape& sh, cudaStream_t s)
     b->a.schedule = sh.schedule;
     b->a.grab = 4;
     b->a.repr = sh.repr;
+    b->a.op_pool = sh.repr == 1 ? b->d_ops_c : b->d_ops;
     b->shape = sh;
     if (repr_changed || !b->spans_ready) return run_setup(b, s);
     return BEZ_OK;
@@ -276,6 +300,7 @@ void free_batch(bez_batch b)
     cudaFree(b->d_desc);
     cudaFree(b->d_span_off);
     cudaFree(b->d_ops);
+    cudaFree(b->d_ops_c);
     cudaFree(b->d_span_ops);
     cudaFree(b->d_op_off);
     cudaFree(b->d_span_tab);
@@ -323,6 +348,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     std::map<std::vector<long long>, int64_t> mat_index;  // distinct matrices -> offset into ops
     std::vector<int64_t> span_ops;                       // per span: offset of its matrix in ops
     std::vector<double> ops;
+    std::vector<std::pair<int64_t, int>> mats;           // (offset, degree) of every distinct matrix
     int64_t spans = 0, total_samples = 0, n_type[3] = {0, 0, 0}, deg_sum = 0;
     for (int64_t i = 0; i < n_curves; ++i) {
         const bez_curve_desc& d = b->hdesc[(size_t)i];
@@ -366,6 +392,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
                         // rows padded to an even length (zeros) so the device
                         // reads each row as 16-byte pairs of entries
                         mt = mat_index.emplace(mk, (int64_t)ops.size()).first;
+                        mats.emplace_back((int64_t)ops.size(), p);
                         const int stride = kOpRowStride(p);
                         for (int i = 0; i <= p; ++i) {
                             ops.insert(ops.end(), M.begin() + i * (p + 1), M.begin() + (i + 1) * (p + 1));
@@ -386,13 +413,47 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     };
     alloc((void**)&b->d_desc, (size_t)n_curves * sizeof(bez_curve_desc));
     alloc((void**)&b->d_span_off, (size_t)n_curves * sizeof(int64_t));
-    // operators as unevaluated float pairs hi + lo: hi = fl32(M), lo = fl32(M - hi)
-    std::vector<float2> ops2(ops.size());
-    for (size_t k = 0; k < ops.size(); ++k) {
-        const float hi = (float)ops[k];
-        ops2[k] = make_float2(hi, (float)(ops[k] - (double)hi));
+    // Centred representation: the Bezier -> power-basis-about-1/2 map is a
+    // fixed matrix T_p per degree, so each span operator M becomes T_p M (FP64
+    // here) and a Bezier curve's span uses T_p itself; the device then forms
+    // either representation with the same compensated dot products.  Both
+    // pools share one layout: the distinct M, then T_1 .. T_7.
+    std::vector<double> ops_c(ops.size(), 0.0);
+    for (const auto& mp : mats) {
+        const int p = mp.second, st = kOpRowStride(p);
+        double T[8][8];
+        centred_matrix(p, T);
+        for (int i = 0; i <= p; ++i)
+            for (int j = 0; j <= p; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k <= p; ++k) acc += T[i][k] * ops[(size_t)(mp.first + (int64_t)k * st + j)];
+                ops_c[(size_t)(mp.first + (int64_t)i * st + j)] = acc;
+            }
     }
+    for (int p = 1; p <= 7; ++p) {
+        const int st = kOpRowStride(p);
+        b->a.tpow_off[p] = (int64_t)ops.size();
+        double T[8][8];
+        centred_matrix(p, T);
+        for (int i = 0; i <= p; ++i)
+            for (int j = 0; j < st; ++j) {
+                ops.push_back(j == i ? 1.0 : 0.0);  // unused in the Bezier-point pool
+                ops_c.push_back(j <= p ? T[i][j] : 0.0);
+            }
+    }
+    b->a.tpow_off[0] = 0;
+    // operators as unevaluated float pairs hi + lo: hi = fl32(M), lo = fl32(M - hi)
+    auto split = [](const std::vector<double>& v) {
+        std::vector<float2> r(v.size());
+        for (size_t k = 0; k < v.size(); ++k) {
+            const float hi = (float)v[k];
+            r[k] = make_float2(hi, (float)(v[k] - (double)hi));
+        }
+        return r;
+    };
+    const std::vector<float2> ops2 = split(ops), ops2c = split(ops_c);
     alloc((void**)&b->d_ops, ops2.size() * sizeof(float2));
+    alloc((void**)&b->d_ops_c, ops2c.size() * sizeof(float2));
     alloc((void**)&b->d_span_ops, span_ops.size() * sizeof(int64_t));
     alloc((void**)&b->d_op_off, (size_t)n_curves * sizeof(int64_t));
     alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
@@ -417,6 +478,8 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
         e = cudaMemcpy(b->d_span_off, span_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ops.empty())
         e = cudaMemcpy(b->d_ops, ops2.data(), ops2.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ops2c.empty())
+        e = cudaMemcpy(b->d_ops_c, ops2c.data(), ops2c.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !span_ops.empty())
         e = cudaMemcpy(b->d_span_ops, span_ops.data(), span_ops.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_curves > 0)

@@ -193,10 +193,11 @@ struct BatchArgs {
     float* out_pool;
     float* span_pool;            // every curve's spans in the evaluation representation
     const int64_t* span_off;     // per curve, floats into span_pool
-    const float2* op_pool;       // span extraction operators of the splines, each entry hi + lo (FP64 -> 2 x FP32),
+    const float2* op_pool;       // span operators M (repr 0) or T_p M (repr 1), each entry hi + lo (FP64 -> 2 x FP32),
                                  // row-major with rows padded to kOpRowStride(p) entries
     const int64_t* op_off;       // per curve, index of its first span in span_ops (splines only)
     const int64_t* span_ops;     // per spline span: offset of its operator matrix in op_pool
+    int64_t tpow_off[8];         // offset of T_p (Bezier -> centred power basis) in the centred op_pool
     const int2* span_tab;        // (curve, span) of every span: one setup thread each
     int64_t n_span_tab;
     int32_t repr;                // 0 Bezier points (de Casteljau), 1 power basis about 1/2 (Horner)
