@@ -178,6 +178,10 @@ struct Staging {
 
 size_t dtype_size(int dt) { return dt == BEZ_F32 ? 4 : 2; }
 
+// pipelined host calls: at most kPipeChunks chunks of at least kPipeMinCurves curves
+constexpr int kPipeChunks = 8;
+constexpr int64_t kPipeMinCurves = 16384;
+
 bez_status check_common(bez_ctx c, const bez_opts* o)
 {
     if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
@@ -273,6 +277,10 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.chain);
     atlas_free(c->tex.probe);
     atlas_free(c->tex.surf3);
+    if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
+    if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
+    for (auto e : c->pipe_ev)
+        if (e) cudaEventDestroy(e);
     atlas_free(c->tex.surf2);
     cudaFree(c->tex.rescale);
     if (c->tex_done) cudaEventDestroy(c->tex_done);
@@ -359,9 +367,21 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Staging stg{c, s};
     CurveArgs a{};
-    const size_t ctrl_bytes = (size_t)n_curves * (degree + 1) * dim * dtype_size(o->dtype);
-    st = stg.in(ctrl, ctrl_bytes, 0, &a.ctrl);
-    if (st != BEZ_OK) return st;
+    const size_t ctrl_per = (size_t)(degree + 1) * dim * dtype_size(o->dtype);
+    const size_t ctrl_bytes = (size_t)n_curves * ctrl_per;
+    // Host control points and host output on a register evaluator: run the
+    // call as chunks whose copies in and out overlap the evaluation of the
+    // neighbouring chunks (per-curve host parameters disable it).
+    const bool pipe = !tex && classify(ctrl) == MEM_HOST && classify(out) == MEM_HOST &&
+                      n_curves >= 2 * kPipeMinCurves && !(o->t_mode == BEZ_T_PER_CURVE && classify(t) == MEM_HOST);
+    if (pipe) {
+        st = ensure_stage(c, 0, ctrl_bytes, s);
+        if (st != BEZ_OK) return st;
+        a.ctrl = c->stage[0].p;
+    } else {
+        st = stg.in(ctrl, ctrl_bytes, 0, &a.ctrl);
+        if (st != BEZ_OK) return st;
+    }
     if (t_array) {
         const size_t tb = (size_t)n_t * sizeof(float) * (o->t_mode == BEZ_T_PER_CURVE ? (size_t)n_curves : 1);
         const void* td = nullptr;
@@ -370,11 +390,17 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
         a.t = static_cast<const float*>(td);
         a.t_stride = o->t_mode == BEZ_T_PER_CURVE ? n_t : 0;
     }
-    const size_t out_bytes =
-        o->out_mode == BEZ_OUT_POINTS ? (size_t)n_curves * n_t * dim * sizeof(float) : (size_t)n_curves * sizeof(float);
+    const size_t out_per = o->out_mode == BEZ_OUT_POINTS ? (size_t)n_t * dim * sizeof(float) : sizeof(float);
+    const size_t out_bytes = (size_t)n_curves * out_per;
     void* od = nullptr;
-    st = stg.out(out, out_bytes, 2, &od);
-    if (st != BEZ_OK) return st;
+    if (pipe) {
+        st = ensure_stage(c, 2, out_bytes, s);
+        if (st != BEZ_OK) return st;
+        od = c->stage[2].p;
+    } else {
+        st = stg.out(out, out_bytes, 2, &od);
+        if (st != BEZ_OK) return st;
+    }
     a.out = static_cast<float*>(od);
     a.dtype = o->dtype;
     a.degree = degree;
@@ -401,16 +427,58 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
         c->tex_used = true;
         return stg.finish(o->sync);
     }
-    switch (var) {
-    case BEZ_VAR_HORNER: r = launch_curve_horner(a, tm, om, s, h); break;
-    case BEZ_VAR_HORNER_CENTRED: r = launch_curve_horner_centred(a, tm, om, s, h); break;
-    case BEZ_VAR_BERNSTEIN: r = launch_curve_bernstein(a, tm, om, s, h); break;
-    case BEZ_VAR_DECASTELJAU: r = launch_curve_decasteljau(a, tm, om, s, h); break;
-    case BEZ_VAR_HALF2: r = launch_curve_half2(a, tm, om, s, h); break;
-    default: r = launch_curve_seiler(a, tm, om, s, h); break;
+    auto launch = [&](const CurveArgs& ak) {
+        switch (var) {
+        case BEZ_VAR_HORNER: return launch_curve_horner(ak, tm, om, s, h);
+        case BEZ_VAR_HORNER_CENTRED: return launch_curve_horner_centred(ak, tm, om, s, h);
+        case BEZ_VAR_BERNSTEIN: return launch_curve_bernstein(ak, tm, om, s, h);
+        case BEZ_VAR_DECASTELJAU: return launch_curve_decasteljau(ak, tm, om, s, h);
+        case BEZ_VAR_HALF2: return launch_curve_half2(ak, tm, om, s, h);
+        default: return launch_curve_seiler(ak, tm, om, s, h);
+        }
+    };
+    if (!pipe) {
+        r = launch(a);
+        if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
+        return stg.finish(o->sync);
     }
-    if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
-    return stg.finish(o->sync);
+    // chunk k: copy in on pipe_in, evaluate on s, copy out on pipe_out
+    if (!c->pipe_in) {
+        BEZ_CUDA(cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking), "cudaStreamCreate");
+        BEZ_CUDA(cudaStreamCreateWithFlags(&c->pipe_out, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (auto& e : c->pipe_ev) BEZ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    const int K = (int)std::min<int64_t>(kPipeChunks, n_curves / kPipeMinCurves);
+    cudaEvent_t* ev = c->pipe_ev;
+    BEZ_CUDA(cudaEventRecord(ev[0], s), "cudaEventRecord");  // earlier work on s (e.g. the staged t) comes first
+    BEZ_CUDA(cudaStreamWaitEvent(c->pipe_in, ev[0], 0), "cudaStreamWaitEvent");
+    BEZ_CUDA(cudaStreamWaitEvent(c->pipe_out, ev[0], 0), "cudaStreamWaitEvent");
+    const char* hin = static_cast<const char*>(ctrl);
+    char* hout = reinterpret_cast<char*>(out);
+    char* din = static_cast<char*>(c->stage[0].p);
+    char* dout = static_cast<char*>(c->stage[2].p);
+    for (int k = 0; k < K; ++k) {
+        const int64_t c0 = n_curves * k / K, c1 = n_curves * (k + 1) / K, nk = c1 - c0;
+        BEZ_CUDA(cudaMemcpyAsync(din + c0 * ctrl_per, hin + c0 * ctrl_per, nk * ctrl_per, cudaMemcpyHostToDevice,
+                                 c->pipe_in), "copy input chunk to device");
+        BEZ_CUDA(cudaEventRecord(ev[1 + k], c->pipe_in), "cudaEventRecord");
+        BEZ_CUDA(cudaStreamWaitEvent(s, ev[1 + k], 0), "cudaStreamWaitEvent");
+        CurveArgs ak = a;
+        ak.ctrl = din + c0 * ctrl_per;
+        ak.out = reinterpret_cast<float*>(dout + c0 * out_per);
+        ak.n_curves = nk;
+        ak.c_base = c0;
+        r = launch(ak);
+        if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
+        BEZ_CUDA(cudaEventRecord(ev[1 + kPipeChunks + k], s), "cudaEventRecord");
+        BEZ_CUDA(cudaStreamWaitEvent(c->pipe_out, ev[1 + kPipeChunks + k], 0), "cudaStreamWaitEvent");
+        BEZ_CUDA(cudaMemcpyAsync(hout + c0 * out_per, dout + c0 * out_per, nk * out_per, cudaMemcpyDeviceToHost,
+                                 c->pipe_out), "copy output chunk to host");
+    }
+    BEZ_CUDA(cudaEventRecord(ev[1 + 2 * kPipeChunks], c->pipe_out), "cudaEventRecord");
+    BEZ_CUDA(cudaStreamWaitEvent(s, ev[1 + 2 * kPipeChunks], 0), "cudaStreamWaitEvent");
+    BEZ_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    return BEZ_OK;
 }
 
 bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int n_seg, int degree, int dim,

@@ -30,6 +30,9 @@ struct bez_ctx_s {
     StageBuf stage[8];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots / grad_out, 6-7 extra outputs (host staging);
                         // 5 spline spans (scratch)
     bez::TexState tex;
+    // pipelined host calls: chunk copies in and out on their own streams
+    cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+    cudaEvent_t pipe_ev[2 * 8 + 2] = {};
     cudaEvent_t tex_done = nullptr;  // last use of the texture atlases
     bool tex_used = false;
     std::mutex mu;

@@ -465,7 +465,7 @@ template <int TM>
 __device__ __forceinline__ uint32_t curve_key(const CurveArgs& a, int64_t c)
 {
     if (TM != TM_HASH && TM != TM_HASH16) return 0u;
-    const uint32_t kc = lowbias32(a.key ^ (uint32_t)c);
+    const uint32_t kc = lowbias32(a.key ^ (uint32_t)(a.c_base + c));
     return TM == TM_HASH16 ? kc ^ (kc >> 16) : kc;
 }
 

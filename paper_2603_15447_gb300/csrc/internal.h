@@ -22,6 +22,7 @@ struct CurveArgs {
     float* out;         // OM_POINTS [n_curves][n_t][dim]; OM_LENGTH [n_curves]
     uint32_t key;       // TM_HASH stream key
     int32_t n_seg;      // chains: segments per chain (0 for single curves)
+    int64_t c_base;     // global index of curve 0 of this launch (the draw hashes c_base + c)
 };
 
 // Result of a launcher: how many kernels it launched and the CUDA status.

@@ -315,3 +315,27 @@ def test_half2_unsupported():
         with pytest.raises(bez.BezError) as e:
             bez.bez_eval(torch.zeros(shape, device="cuda"), torch.zeros(3, device="cuda"), variant=bez.Variant.HALF2)
         assert e.value.status == bez.Status.UNSUPPORTED
+
+
+@pytest.mark.parametrize("out_mode,t_mode,pinned", [("POLYLINE_LENGTH", "HASH", True), ("POINTS", "HASH", False),
+                                                    ("POLYLINE_LENGTH", "SHARED", False), ("POINTS", "UNIFORM", True)])
+def test_pipelined_host_call_matches_device_call(out_mode, t_mode, pinned):
+    # Host control points and host output: the call runs as chunks whose
+    # copies overlap the evaluation of neighbouring chunks; every chunk hashes
+    # its curves by their global index, so the result equals the device call.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(500)
+    n = 70001
+    n_t = 33 if out_mode == "POINTS" else 256
+    ctrl = _ctrl(rng, n, 3, 3)
+    t = rng.uniform(0, 1, n_t).astype(np.float32) if t_mode == "SHARED" else None
+    kw = dict(n_t=None if t is not None else n_t, variant=bez.Variant.HORNER_CENTRED, out_mode=bez.OutMode[out_mode],
+              t_mode=bez.TMode[t_mode], seed=12, stream_id=3)
+    dev = bez.bez_eval(torch.from_numpy(ctrl).cuda(), None if t is None else torch.from_numpy(t).cuda(), **kw)
+    host_ctrl = torch.from_numpy(ctrl)
+    if pinned:
+        host_ctrl = host_ctrl.pin_memory()
+    host = bez.bez_eval(host_ctrl, None if t is None else torch.from_numpy(t), **kw)
+    assert host.device.type == "cpu"
+    np.testing.assert_array_equal(host.numpy(), dev.cpu().numpy())
