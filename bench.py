@@ -501,6 +501,18 @@ def run_batch(args):
                            w["out_off"])
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
     n_pts = int(w["n_samples"].sum())
+    if args.batch_shape:
+        # one fixed launch shape (chunk, schedule, threads, repr), spans extracted once, no tuning
+        chunk, sched, threads, rep = (int(x) for x in args.batch_shape.split(","))
+        b = bez.Batch(desc, 3, ctrl, wts, out, chunk=chunk, schedule=sched, threads=threads, repr=rep,
+                      setup_each_launch=False, use_graph=True, ctx=ctx)
+        ms_b, st_b = timer.run(b.launch, args.steps, args.warmup)
+        b.close()
+        return _hbm_line(f"batch: {len(desc)} mixed curves, fixed shape chunk {chunk} schedule {sched} threads "
+                         f"{threads} repr {rep}, spans extracted once", n_pts * args.steps / (ms_b * 1e-3), "points/s",
+                         args.steps, args.warmup, ms_b, n_pts * 12 + w["ctrl_pool"].nbytes + w["weight_pool"].nbytes,
+                         ms_b / args.steps, "k_batch_class (graph replay)",
+                         {"gpu_launches": int(st_b["launches"]), "n_points": n_pts})
     full = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=True, use_graph=True, ctx=ctx)
     ms_full, st_full = timer.run(full.launch, args.steps, args.warmup)
     cfg = full.config()
@@ -660,6 +672,7 @@ def main():
     ap.add_argument("--chain-t", type=int, default=65536)
     ap.add_argument("--skip-chains", action="store_true")
     ap.add_argument("--batch-curves", type=int, default=262144)
+    ap.add_argument("--batch-shape", default="", help="chunk,schedule,threads,repr: time one fixed batch shape")
     ap.add_argument("--accuracy-curves", type=int, default=4096)
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-f16", action="store_true", help="skip the half-storage variant table")
