@@ -21,6 +21,8 @@
 // degree 5.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -55,6 +57,37 @@ __device__ __forceinline__ void forward_differences_at0(S (&w)[N], int d)
             if (i >= k && i <= d) w[i] = w[i] - w[i - 1];
     }
 }
+
+// ---------------------------------------------------------------- centred basis matrix
+
+// T_d[m][i]: coefficient of b_i in the power coefficient about t = 1/2,
+// c_m = sum_i T_d[m][i] b_i = binom(d, m) * (Bernstein value at 1/2 of the
+// m-th forward differences) -- the conversion applied to unit vectors.  The
+// entries are small integers over powers of two (exact in FP32 and FP64).
+struct CentredTables {
+    double t[8][8][8];  // [d][m][i], d = 1..7
+};
+constexpr CentredTables make_centred_tables()
+{
+    CentredTables r{};
+    for (int d = 1; d <= 7; ++d)
+        for (int i = 0; i <= d; ++i) {
+            double w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            w[i] = 1.0;
+            double bin = 1.0;
+            for (int m = 0; m <= d; ++m) {
+                double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int k = 0; k <= d - m; ++k) h[k] = w[k];
+                for (int q = 1; q <= d - m; ++q)
+                    for (int k = 0; k <= d - m - q; ++k) h[k] = 0.5 * (h[k] + h[k + 1]);
+                r.t[d][m][i] = bin * h[0];
+                bin = bin * (double)(d - m) / (double)(m + 1);
+                for (int k = 0; k < d - m; ++k) w[k] = w[k + 1] - w[k];
+            }
+        }
+    return r;
+}
+static __constant__ CentredTables kCentredT = make_centred_tables();
 
 // ---------------------------------------------------------------- evaluators
 
@@ -142,6 +175,30 @@ struct Eval<VAR_HORNER_CENTRED, D, DIM> {
         d = Deg<D>::get(deg);
         if (d >= kFp64SetupCentred) setup_t<double>(b);
         else setup_t<float>(b);
+    }
+    // Warp-cooperative setup for 3D curves of fixed degree: the curve's
+    // control points are spread one element per lane (lane 3i + k holds
+    // b_i[k], in v); lane 3m + k forms a[m][k] = sum_i T_d[m][i] b_i[k] (FP64
+    // from degree 5, like setup) and the warp broadcasts the coefficients.
+    // One dot product per lane instead of the whole conversion per lane.
+    __device__ __forceinline__ void setup_warp(float v, int lane)
+    {
+        static_assert(D > 0 && DIM == 3 && 3 * (D + 1) <= 32, "fixed-degree 3D curves only");
+        d = D;
+        using S = typename std::conditional<(D >= kFp64SetupCentred), double, float>::type;
+        const int m = lane < 3 * (D + 1) ? lane / 3 : 0;
+        const int k = lane < 3 * (D + 1) ? lane - 3 * m : 0;
+        S acc = (S)0;
+#pragma unroll
+        for (int i = 0; i <= D; ++i) {
+            const float bik = __shfl_sync(kFull, v, 3 * i + k);
+            acc = fma((S)kCentredT.t[D][m][i], (S)bik, acc);
+        }
+        const float cm = (float)acc;
+#pragma unroll
+        for (int mm = 0; mm <= D; ++mm)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) a[mm][kk] = __shfl_sync(kFull, cm, 3 * mm + kk);
     }
     __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const { eval_u(t - 0.5f, P); }
     // evaluate at u = t - 1/2
@@ -607,11 +664,16 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_curve(const CurveArgs a)
     CtrlRegs<N, DIM> cur;
     cur.load(a, c, per, lane);
     for (; c < a.n_curves; c += n_warps) {
-        float b[N][DIM];
-        cur.unpack(b, deg);
-        cur.load(a, c + n_warps, per, lane);   // prefetch the next curve of this warp
         E e;
-        e.setup(b, deg);
+        if constexpr (VAR == VAR_HORNER_CENTRED && D > 0 && DIM == 3) {
+            e.setup_warp(cur.v[0], lane);
+            cur.load(a, c + n_warps, per, lane);   // prefetch the next curve of this warp
+        } else {
+            float b[N][DIM];
+            cur.unpack(b, deg);
+            cur.load(a, c + n_warps, per, lane);
+            e.setup(b, deg);
+        }
         const uint32_t kc = curve_key<TM>(a, c);
         const int n_t = a.n_t;
 
