@@ -55,10 +55,10 @@ T_OPS, LEN_OPS = 9, 8
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels, per unit of work; null in the JSON line for other kernels.  The
-# curve kernel was captured on 131,072 curves (6,308,352 B: the control
+# curve kernel was captured on 131,072 curves (6,308,864 B: the control
 # points; the 4 B lengths stay in L2) and scales with the curve count; the
 # surface kernel on the full 65,536-patch tensor workload.
-TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6308352 / 131072}
+TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6308864 / 131072}
 TRAFFIC_SURFACE_65536 = 12626688 + 743121664
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
             "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
