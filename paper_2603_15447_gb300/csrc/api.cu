@@ -180,6 +180,8 @@ size_t dtype_size(int dt) { return dt == BEZ_F32 ? 4 : 2; }
 
 // pipelined host calls: at most kPipeChunks chunks of at least kPipeMinCurves curves
 constexpr int kPipeChunks = 8;
+static_assert(sizeof(((bez_ctx_s*)nullptr)->pipe_ev) / sizeof(cudaEvent_t) == 2 * kPipeChunks + 2,
+              "one start event, an in and a done event per chunk, one end event");
 constexpr int64_t kPipeMinCurves = 16384;
 
 bez_status check_common(bez_ctx c, const bez_opts* o)
