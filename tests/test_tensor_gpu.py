@@ -80,6 +80,21 @@ def test_volumes(du, dv, dw, dim, n):
     assert _err_ctrl(got, ref, ctrl).max() <= FP32_BAR
 
 
+@pytest.mark.parametrize("nu,nv,nw", [(16, 16, 16), (1, 3, 4), (5, 7, 12), (32, 20, 256), (33, 4, 8), (8, 8, 6)])
+def test_tricubic_scalar_volume_shapes(nu, nv, nw):
+    # nu <= 32 with nw a multiple of 4 takes the warp-per-volume kernel,
+    # the others the block-per-volume kernel; both against the triple sum
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(nu * 10000 + nv * 100 + nw)
+    ctrl = rng.normal(size=(41, 4, 4, 4, 1)).astype(np.float32)
+    got = bez.bez_eval_volume(torch.from_numpy(ctrl).cuda(), nu, nv, nw).cpu().numpy()
+    ref = oracle.volume(ctrl, nu, nv, nw)
+    assert got.shape == ref.shape
+    assert _err_ctrl(got, ref, ctrl).max() <= FP32_BAR
+    np.testing.assert_array_equal(got[:, 0, 0, 0, 0], ctrl[:, 0, 0, 0, 0])   # corner
+
+
 def test_half_bf16_storage_and_host_arrays():
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
