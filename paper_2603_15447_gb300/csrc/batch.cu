@@ -209,10 +209,7 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
 {
     constexpr bool RAT = C == 4;
     constexpr int DIM = 3;
-    // per-lane stride of the staged tile: even, so two samples (6 floats) go
-    // in as three 8-byte stores, and 13 float2 apart across lanes (odd), so
-    // those stores are free of bank conflicts
-    constexpr int LS = kRun * DIM + 2;
+    constexpr int LS = kRun * DIM + 1;  // padded per-lane stride of the tile
     const int n = it.n_samples;
     const bool spline = it.n_spans > 0;
     const int n_spans = it.n_spans;
@@ -226,13 +223,9 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
     for (int tb = j0; tb < j1; tb += kTile) {
         const int my0 = tb + lane * kRun;
         int s_run = -1;  // span of this lane's previous sample in the run
-        for (int r = 0; r < kRun; r += 2) {
-          float pp[2][DIM];
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int j = my0 + r + hh;
-#pragma unroll
-            for (int q = 0; q < DIM; ++q) pp[hh][q] = 0.f;
+#pragma unroll 2
+        for (int r = 0; r < kRun; ++r) {
+            const int j = my0 + r;
             if (j < j1) {
                 const float t = grid(j);
                 float tau = t;
@@ -266,13 +259,8 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
                     for (int q = 0; q < DIM; ++q) pt[q] *= inv;
                 }
 #pragma unroll
-                for (int q = 0; q < DIM; ++q) pp[hh][q] = pt[q];
+                for (int q = 0; q < DIM; ++q) stage[lane * LS + r * DIM + q] = pt[q];
             }
-          }
-          float2* st2 = reinterpret_cast<float2*>(stage + lane * LS + r * DIM);
-          st2[0] = make_float2(pp[0][0], pp[0][1]);
-          st2[1] = make_float2(pp[0][2], pp[1][0]);
-          st2[2] = make_float2(pp[1][1], pp[1][2]);
         }
         __syncwarp();
         // Coalesced write-out: float f = 32 m + lane of the tile is element
@@ -280,7 +268,7 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
         // With lane = 24 r0 + o0 and a = o0 div 8, run = r0 + m + w and
         // offset = o0 + 8 m - 24 w where w = (a + m) div 3, so its staged
         // position is base + m (LS + 8) + w (LS - 24).
-        static_assert(kRun * DIM == 24 && kRun % 2 == 0, "write-out index formula and sample pairs");
+        static_assert(kRun * DIM == 24 && LS == 25, "write-out index formula");
         const int valid = min(kTile, j1 - tb) * DIM;
         float* o = out + (int64_t)tb * DIM + lane;
         const int a3 = (lane % 24) / 8;
@@ -390,7 +378,7 @@ __global__ void __launch_bounds__(256) k_batch_class(const BatchArgs a, int64_t 
     extern __shared__ float s_stage[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    float* stage = s_stage + wib * (32 * (kRun * a.dim + 2));
+    float* stage = s_stage + wib * (32 * (kRun * a.dim + 1));
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     auto run = [&](const BatchItem& it) {
         if (P == 0) item_generic<REPR>(a, it, stage, lane);
@@ -455,7 +443,7 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
         e = cudaMemsetAsync(a.counter, 0, kBatchClasses * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = (size_t)(threads / 32) * 32 * (kRun * a.dim + 2) * sizeof(float);
+    const size_t smem = (size_t)(threads / 32) * 32 * (kRun * a.dim + 1) * sizeof(float);
     int active = 0;
     for (int cls = 0; cls < kBatchClasses; ++cls) active += a.class_start[cls + 1] > a.class_start[cls];
     if (active == 0) return cudaSuccess;
