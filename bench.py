@@ -591,33 +591,54 @@ def run_fit(args):
     truth, t_true, noise, init = synth.fit()
     target = bez.bez_eval(torch.from_numpy(truth).cuda(), torch.from_numpy(t_true).cuda(),
                           variant=bez.Variant.DECASTELJAU) + torch.from_numpy(noise).cuda()
-    ctrl = torch.tensor(init, device="cuda", requires_grad=True)
-    t = torch.tensor(np.tile((np.arange(512) / 511.0).astype(np.float32), (65536, 1)), device="cuda",
-                     requires_grad=True)
+    n_curves, n_t = target.shape[0], target.shape[1]
+    t0 = np.tile((np.arange(n_t) / (n_t - 1.0)).astype(np.float32), (n_curves, 1))
+    n = n_curves * n_t
+    scale = 1.0 / (n * 3)
+
+    # fused step: one kernel forms C, the residual, the loss and the adjoint
+    ctrl = torch.tensor(init, device="cuda")
+    t = torch.tensor(t0, device="cuda")
     opt = torch.optim.Adam([ctrl, t], lr=1e-2)
 
     def step():
-        opt.zero_grad(set_to_none=False)
-        loss = ((bezier_curve(ctrl, t) - target) ** 2).mean()
-        loss.backward()
+        loss, gc, _, gt = bez.bez_mse_grad(ctrl, t, target, loss_scale=scale, ctx=ctx)
+        ctrl.grad, t.grad = gc, gt
         opt.step()
-        with torch.no_grad():
-            t.clamp_(0, 1)
+        t.clamp_(0, 1)
         return loss
 
+    # the same step through the autograd Function (forward kernel, torch MSE, adjoint kernel)
+    ctrl_a = torch.tensor(init, device="cuda", requires_grad=True)
+    t_a = torch.tensor(t0, device="cuda", requires_grad=True)
+    opt_a = torch.optim.Adam([ctrl_a, t_a], lr=1e-2)
+
+    def step_autograd():
+        opt_a.zero_grad(set_to_none=False)
+        loss = ((bezier_curve(ctrl_a, t_a) - target) ** 2).mean()
+        loss.backward()
+        opt_a.step()
+        with torch.no_grad():
+            t_a.clamp_(0, 1)
+        return loss.detach()
+
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
-    first = float(step())
+    first = float(step().sum())
     ms, st = timer.run(step, args.steps, args.warmup)
     for _ in range(max(0, 200 - args.steps - args.warmup - 2)):
         step()
-    final = float(step())
-    n = 65536 * 512
+    final = float(step().sum())
+    ms_a, _ = timer.run(step_autograd, args.steps, args.warmup)
     kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
-    # forward + adjoint kernels per sample: t 4 B in, point 12 B out; t 4 B + grad_out 12 B in, grad_t 4 B out
-    return _hbm_line("fit: 65,536 cubic 3D curves x 512 samples, forward + MSE + adjoint + Adam per step",
-                     n * args.steps / (ms * 1e-3), "samples/s", args.steps, args.warmup, ms, n * 18, kern_ms,
-                     "k_curve (forward) and k_grad (adjoint), mean launch",
-                     {"loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5})
+    # k_grad with a target, per sample: t 4 B + target 12 B in, grad_t 4 B out;
+    # per curve: 48 B of control points in, 48 B of grad_ctrl and 4 B of loss out
+    bytes_launch = n * 20 + n_curves * 100
+    return _hbm_line(f"fit: {n_curves:,} cubic 3D curves x {n_t} samples, fused forward + squared error + adjoint, "
+                     "then Adam, per step", n * args.steps / (ms * 1e-3), "samples/s", args.steps, args.warmup, ms,
+                     bytes_launch, kern_ms, "k_grad (fused squared error), mean launch",
+                     {"loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5,
+                      "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3), "ms_per_step": ms_a / args.steps,
+                                        "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}})
 
 
 # ------------------------------------------------------------------ reference arm

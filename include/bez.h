@@ -364,6 +364,25 @@ bez_status bez_eval_backward(bez_ctx ctx, const float* ctrl, const float* weight
                              float* grad_weights, float* grad_t, const bez_opts* opts, void* stream);
 
 /*
+ * bez_mse_grad -- squared-error fit loss and its gradients in one pass.
+ *
+ * The paper has no counterpart; this is the curve-fitting step of the
+ * differentiation workload with the loss fused into bez_eval_backward: for
+ * targets y[c][j] and s = loss_scale,
+ *   loss[c]       = s * sum_j ||C(t_j) - y_j||^2
+ *   grad_*        = bez_eval_backward's outputs for grad_out = 2 s (C - y)
+ * computed from the curve values the adjoint forms anyway, so the call reads
+ * t and the targets once and writes no point or gradient arrays.
+ *
+ *   target [n_curves][n_t][dim] FP32; loss [n_curves] FP32 or NULL; other
+ *   arguments, layouts and limits as bez_eval_backward.  Pass s =
+ *   1 / (n_curves n_t dim) for the mean squared error.
+ */
+bez_status bez_mse_grad(bez_ctx ctx, const float* ctrl, const float* weights, int64_t n_curves, int degree, int dim,
+                        const float* t, int64_t n_t, const float* target, float loss_scale, float* loss,
+                        float* grad_ctrl, float* grad_weights, float* grad_t, const bez_opts* opts, void* stream);
+
+/*
  * bez_eval_spline_noalloc -- B-spline / NURBS evaluation that allocates no
  * memory.  The paper has no counterpart; this is a deployment variant of
  * bez_eval_bspline / bez_eval_nurbs.

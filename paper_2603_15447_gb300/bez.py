@@ -408,6 +408,39 @@ def bez_eval_backward(ctrl, t, grad_out, *, weights=None, need_ctrl=True, need_w
     return gc, gw, gt
 
 
+def bez_mse_grad(ctrl, t, target, *, weights=None, loss_scale=None, need_ctrl=True, need_weights=None, need_t=True,
+                 stream=None, sync=False, ctx=None):
+    """Fused squared-error fit step: per-curve loss s * sum_j ||C(t_j) - target_j||^2
+    and its gradients (as bez_eval_backward with grad_out = 2 s (C - target)).
+    loss_scale defaults to 1 / target.numel() (mean squared error).  Returns
+    (loss [n_curves], grad_ctrl, grad_weights, grad_t); entries not requested
+    are None."""
+    n_curves, d1, dim = ctrl.shape
+    n_t = t.shape[-1]
+    t_mode = TMode.SHARED if t.ndim == 1 else TMode.PER_CURVE
+    if need_weights is None:
+        need_weights = weights is not None
+    if loss_scale is None:
+        loss_scale = 1.0 / max(1, n_curves * n_t * dim)
+    loss = _empty_like_location(ctrl, (n_curves,))
+    gc = _empty_like_location(ctrl, (n_curves, d1, dim)) if need_ctrl else None
+    gw = _empty_like_location(ctrl, (n_curves, d1)) if need_weights else None
+    gt = _empty_like_location(ctrl, tuple(t.shape)) if need_t else None
+    dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    L = lib()
+    if not getattr(L, "_mse_ready", False):
+        L.bez_mse_grad.argtypes = [_VP, _VP, _VP, _I64, _INT, _INT, _VP, _I64, _VP, ctypes.c_float, _VP, _VP, _VP,
+                                   _VP, ctypes.POINTER(Opts), _VP]
+        L.bez_mse_grad.restype = ctypes.c_int
+        L._mse_ready = True
+    o = _opts(Variant.AUTO, _dtype_code(ctrl), OutMode.POINTS, t_mode, 0, 0, sync)
+    _check(L.bez_mse_grad(c.handle, _ptr(ctrl), _ptr(weights), n_curves, d1 - 1, dim, _ptr(t), n_t, _ptr(target),
+                          float(loss_scale), _ptr(loss), _ptr(gc), _ptr(gw), _ptr(gt), ctypes.byref(o),
+                          _stream_handle(stream, dev)))
+    return loss, gc, gw, gt
+
+
 # ---------------------------------------------------------------- mixed batches
 
 DESC_DTYPE = np.dtype([("type", "<i4"), ("degree", "<i4"), ("n_ctrl", "<i4"), ("n_samples", "<i4"),

@@ -742,9 +742,12 @@ bez_status bez_eval_volume(bez_ctx c, const void* ctrl, int64_t n, int du, int d
     return eval_tensor(c, ctrl, n, du, dv, dw, dim, nu, nv, nw, out, o, stream);
 }
 
-bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights, int64_t n_curves, int degree, int dim,
-                             const float* t, int64_t n_t, const float* grad_out, float* grad_ctrl,
-                             float* grad_weights, float* grad_t, const bez_opts* o, void* stream)
+// The adjoint, with an upstream gradient (grad_out) or the fused squared
+// error against targets (target, loss_scale, loss).
+static bez_status adjoint(bez_ctx c, const float* ctrl, const float* weights, int64_t n_curves, int degree, int dim,
+                          const float* t, int64_t n_t, const float* grad_out, const float* target, float loss_scale,
+                          float* loss, float* grad_ctrl, float* grad_weights, float* grad_t, const bez_opts* o,
+                          void* stream)
 {
     bez_status st = check_common(c, o);
     if (st != BEZ_OK) return st;
@@ -758,7 +761,8 @@ bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights,
         return fail(BEZ_ERR_UNSUPPORTED, "the adjoint needs the parameters as an array (SHARED / PER_CURVE)");
     if (grad_weights && !weights) return fail(BEZ_ERR_INVALID_ARG, "grad_weights requested without weights");
     if (n_curves == 0) return BEZ_OK;
-    if (!ctrl || (n_t > 0 && (!t || !grad_out))) return fail(BEZ_ERR_INVALID_ARG, "null ctrl, t or grad_out");
+    if (!ctrl || (n_t > 0 && (!t || (!grad_out && !target))))
+        return fail(BEZ_ERR_INVALID_ARG, "null ctrl, t, grad_out or target");
     std::lock_guard<std::mutex> g(c->mu);
     BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -777,10 +781,20 @@ bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights,
     st = stg.in(t, (size_t)n_t * sizeof(float) * (per_curve ? (size_t)n_curves : 1), 1, &p);
     if (st != BEZ_OK) return st;
     a.t = static_cast<const float*>(p);
-    st = stg.in(grad_out, (size_t)n_curves * n_t * dim * sizeof(float), 4, &p);
+    st = stg.in(target ? target : grad_out, (size_t)n_curves * n_t * dim * sizeof(float), 4, &p);
     if (st != BEZ_OK) return st;
-    a.g = static_cast<const float*>(p);
+    if (target) {
+        a.target = static_cast<const float*>(p);
+        a.loss_scale = loss_scale;
+    } else {
+        a.g = static_cast<const float*>(p);
+    }
     void* od = nullptr;
+    if (loss) {
+        st = stg.out(loss, (size_t)n_curves * sizeof(float), 8, &od);
+        if (st != BEZ_OK) return st;
+        a.loss = static_cast<float*>(od);
+    }
     if (grad_ctrl) {
         st = stg.out(grad_ctrl, (size_t)n_curves * (degree + 1) * dim * sizeof(float), 2, &od);
         if (st != BEZ_OK) return st;
@@ -807,6 +821,23 @@ bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights,
     LaunchResult r = launch_grad(a, s, hooks_of(c));
     if (r.err != cudaSuccess) return cuda_fail(r.err, "adjoint launch");
     return stg.finish(o->sync);
+}
+
+bez_status bez_eval_backward(bez_ctx c, const float* ctrl, const float* weights, int64_t n_curves, int degree, int dim,
+                             const float* t, int64_t n_t, const float* grad_out, float* grad_ctrl,
+                             float* grad_weights, float* grad_t, const bez_opts* o, void* stream)
+{
+    return adjoint(c, ctrl, weights, n_curves, degree, dim, t, n_t, grad_out, nullptr, 0.f, nullptr, grad_ctrl,
+                   grad_weights, grad_t, o, stream);
+}
+
+bez_status bez_mse_grad(bez_ctx c, const float* ctrl, const float* weights, int64_t n_curves, int degree, int dim,
+                        const float* t, int64_t n_t, const float* target, float loss_scale, float* loss,
+                        float* grad_ctrl, float* grad_weights, float* grad_t, const bez_opts* o, void* stream)
+{
+    if (n_t > 0 && n_curves > 0 && !target) return fail(BEZ_ERR_INVALID_ARG, "null target");
+    return adjoint(c, ctrl, weights, n_curves, degree, dim, t, n_t, nullptr, target, loss_scale, loss, grad_ctrl,
+                   grad_weights, grad_t, o, stream);
 }
 
 bez_status bez_measure_peak(bez_ctx c, int kind, double* value, void* stream)

@@ -27,8 +27,8 @@ struct bez_ctx_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> spare;
     cudaEvent_t cur_begin = nullptr;
-    StageBuf stage[8];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots / grad_out, 6-7 extra outputs (host staging);
-                        // 5 spline spans (scratch)
+    StageBuf stage[9];  // 0 ctrl, 1 t, 2 out, 3 weights, 4 knots / grad_out / targets, 6-8 extra outputs (host
+                        // staging); 5 spline spans (scratch)
     bez::TexState tex;
     // pipelined host calls: chunk copies in and out on their own streams
     cudaStream_t pipe_in = nullptr, pipe_out = nullptr;

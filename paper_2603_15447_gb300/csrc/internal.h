@@ -156,6 +156,9 @@ struct GradArgs {
     float* grad_w;         // [n][d+1] or NULL
     float* grad_t;         // [n][n_t] (per-curve t) or [n_t] (shared t) or NULL
     int32_t shared_gt;     // shared-t sums staged in shared memory (n_t small enough)
+    const float* target;   // fused squared error: [n][n_t][dim] targets (g is then formed in-kernel), or NULL
+    float loss_scale;      // loss = loss_scale * sum ||C - target||^2, g = 2 loss_scale (C - target)
+    float* loss;           // [n] per-curve loss (fused form) or NULL
 };
 
 LaunchResult launch_grad(const GradArgs& a, cudaStream_t s, const LaunchHooks& h);

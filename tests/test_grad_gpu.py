@@ -142,7 +142,88 @@ def test_adam_fit_reaches_noise_floor():
         with torch.no_grad():
             t.clamp_(0, 1)
         if first is None:
-            first = float(loss)
-    final = float(loss)
+            first = float(loss.detach())
+    final = float(loss.detach())
     assert final < first / 20, (first, final)
     assert np.sqrt(final) < 0.1
+
+
+
+def _dmax_over_wmin(ctrl, w):
+    # bound on |C'(t)|: d max|q_(i+1) - q_i| over the homogeneous points, / min w
+    d = ctrl.shape[1] - 1
+    if w is None:
+        return d * np.abs(np.diff(ctrl.astype(np.float64), axis=1)).max()
+    wp = ctrl * w[:, :, None]
+    return d * (np.abs(np.diff(wp, axis=1)).max() + np.abs(ctrl).max() * np.abs(np.diff(w, axis=1)).max()) / w.min()
+
+
+@pytest.mark.parametrize("d,rational,shared", [(3, False, False), (5, True, False), (2, False, True), (7, True, True)])
+def test_fused_squared_error_step(d, rational, shared):
+    # bez_mse_grad: loss s sum ||C - y||^2 and the adjoint of g = 2 s (C - y),
+    # against the FP64 oracle.  The kernel's C (Bernstein triangle, then A / W)
+    # is within eps_C = (4d + 16) u max|P| of the exact value, which moves
+    # each g_j by at most 2 s eps_C per coordinate; on top of that come the
+    # adjoint's own sum roundings (module doc).  The per-curve weights
+    # w_i B_i / W of dL/dP sum to 1, so over n_t samples the moved g shifts
+    # dL/dP by at most n_t 2 s eps_C.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(700 + d + 10 * rational + 100 * shared)
+    B, n_t, dim = 203, 96, 3
+    ctrl = rng.uniform(-1, 1, (B, d + 1, dim)).astype(np.float32)
+    w = rng.uniform(0.5, 2, (B, d + 1)).astype(np.float32) if rational else None
+    t = rng.uniform(0, 1, n_t if shared else (B, n_t)).astype(np.float32)
+    C = oracle.bezier(ctrl, t, weights=w) if w is not None else oracle.bezier(ctrl, t)
+    y = (C + rng.normal(scale=0.05, size=C.shape)).astype(np.float32)
+    s = 1.0 / (B * n_t * dim)
+    loss, gc, gw, gt = bez.bez_mse_grad(_cuda(torch, ctrl), _cuda(torch, t), _cuda(torch, y),
+                                        weights=_cuda(torch, w), loss_scale=s)
+    torch.cuda.synchronize()
+    r = C - y.astype(np.float64)
+    g = 2 * s * r
+    loss_ref = s * (r ** 2).sum(axis=(1, 2))
+    rc, rw, rt = oracle.bezier_grad(ctrl, t, g, weights=w)
+    ac, _, _ = oracle.bezier_grad(ctrl, t, np.abs(g), weights=w)
+    eps_c = (4 * d + 16) * U * np.abs(ctrl).max(axis=(1, 2)).astype(np.float64)   # [B]
+    dg = 2 * s * eps_c * (1 + 4 * U)                                             # [B], per coordinate
+    k = (n_t / 32 + 2 * d + 12) * U
+    lo = loss.cpu().numpy()
+    assert lo.shape == (B,)
+    assert np.all(np.abs(lo - loss_ref)
+                  <= s * (2 * np.abs(r).sum(axis=(1, 2)) * eps_c + n_t * dim * eps_c ** 2) + k * 2 * loss_ref + 1e-30)
+    assert np.all(np.abs(gc.cpu().numpy() - rc) <= (n_t * dg)[:, None, None] + k * (ac + n_t * dg[:, None, None]) + 1e-30)
+    cp = _dmax_over_wmin(ctrl, w) * np.sqrt(dim)
+    gmag = np.linalg.norm(g, axis=-1) + np.sqrt(dim) * dg[:, None]             # [B][n_t]
+    tol_t = (16 * d + 32) * U * gmag * cp + np.sqrt(dim) * dg[:, None] * cp
+    if shared:
+        assert np.all(np.abs(gt.cpu().numpy() - rt) <= tol_t.sum(axis=0) * (1 + B * U) + 1e-30)
+    else:
+        assert np.all(np.abs(gt.cpu().numpy() - rt) <= tol_t + 1e-30)
+    if w is None:
+        assert gw is None
+    else:
+        span = np.abs(ctrl).max() * 2
+        aw2 = oracle.bezier_grad(ctrl, t, np.abs(g) + dg[:, None, None], weights=w)[0].sum(axis=2) * span / w.min()
+        assert np.all(np.abs(gw.cpu().numpy() - rw) <= k * aw2 * 4 + n_t * dim * dg[:, None] * span / w.min() + 1e-30)
+
+
+def test_fused_step_matches_backward_with_kernel_residual():
+    # the fused path is the unfused adjoint fed its own residual: with g formed
+    # from the forward kernel's points, the two agree to the FP32 evaluation
+    # difference of the two kernels, far inside the oracle tolerances above.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(77)
+    B, n_t, d = 64, 130, 3
+    ctrl = torch.from_numpy(rng.uniform(-1, 1, (B, d + 1, 3)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.uniform(0, 1, (B, n_t)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.uniform(-1, 1, (B, n_t, 3)).astype(np.float32)).cuda()
+    loss, gc, _, gt = bez.bez_mse_grad(ctrl, t, y, loss_scale=0.5)
+    pts = bez.bez_eval(ctrl, t, variant=bez.Variant.BERNSTEIN)
+    g = 2 * 0.5 * (pts - y)
+    gc2, _, gt2 = bez.bez_eval_backward(ctrl, t, g)
+    torch.cuda.synchronize()
+    assert torch.allclose(loss, 0.5 * ((pts - y) ** 2).sum(dim=(1, 2)), rtol=1e-5, atol=1e-6)
+    assert torch.allclose(gc, gc2, rtol=1e-4, atol=1e-5)
+    assert torch.allclose(gt, gt2, rtol=1e-4, atol=1e-5)
