@@ -15,57 +15,59 @@
 // reads t and the targets once and writes dt (no point or gradient arrays).
 //
 // One warp per curve; lanes take samples j = lane + 32 m (coalesced reads of
-// t and g), keep per-lane partial sums of the per-curve gradients in
+// t and g), two at a time (j and j + 32: independent arithmetic to
+// interleave), keep per-lane partial sums of the per-curve gradients in
 // registers, and combine them with a butterfly of shuffles.  Per-sample dt is
 // written directly (per-curve t) or summed over curves (shared t) in shared
-// memory and then with one global atomic per block and parameter.
+// memory and then with one global atomic per block and parameter.  The next
+// pair's loads are issued before the current pair's arithmetic, and the
+// output mode is decided once per launch, outside the sample loop.
 //
 // Per curve the homogeneous points q_i = w_i P_i and the scaled differences
 // d (q_(i+1) - q_i), d (w_(i+1) - w_i) are formed once, so a sample costs the
 // basis triangle plus one FMA per (point, coordinate) for each of A, A' and
 // dL/dP.  Integral curves (RAT false) drop W, W', the division and the weight
-// sums: C = A exactly as the Bernstein sum.  The next sample's loads are
-// issued before the current sample's arithmetic.
+// sums: C = A exactly as the Bernstein sum.
 #include "curve_eval.cuh"
 
 namespace bez {
 
 constexpr int kGradMaxDim = 4;
 
+// samples per loop iteration: two independent samples to interleave while
+// the pair's registers fit, one for high degrees
+__host__ __device__ constexpr int grad_pair(int D, bool RAT) { return (D >= 1 && D <= (RAT ? 3 : 4)) ? 2 : 1; }
+
 // resident blocks per SM the register budget is sized for (64, 80 or 128
 // registers a thread at 256 threads a block)
 __host__ __device__ constexpr int grad_min_blocks(int D, bool RAT)
 {
-    return D == 0 ? 2 : (!RAT && D <= 4) ? 4 : (D <= 3 || (!RAT && D <= 5)) ? 3 : 2;
+    return D == 0 ? 2 : grad_pair(D, RAT) == 1 ? (!RAT && D <= 5 ? 3 : 2) : (!RAT && D <= 3) ? 3 : 2;
 }
 
+// dL/dt output: none, per-curve array, or shared t summed over curves with
+// atomics into gt_sum (this block's shared-memory partial sums, or the global
+// array when n_t is too large for shared memory)
+enum { GT_NONE = 0, GT_PER_CURVE = 1, GT_SHARED = 2 };
+
+// One curve's state in a lane: control data and the lane's partial sums.
 template <int D, int DIM, bool RAT>
-__global__ void __launch_bounds__(kWarps * 32, grad_min_blocks(D, RAT)) k_grad(const GradArgs a)
-{
-    constexpr int N = Deg<D>::N;
-    constexpr int M = DIM ? DIM : kGradMaxDim;
-    constexpr int kUnrollN = D ? N : 1;  // runtime degree: loops, arrays in local memory
-    extern __shared__ float s_gt[];  // shared-t dL/dt partial sums of this block
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int d = Deg<D>::get(a.degree);
-    const int dim = DIM ? DIM : a.dim;
-    const bool shared_t = a.t_stride == 0;
-    const bool fused = a.target != nullptr;
-    const float* gsrc = fused ? a.target : a.g;  // per-sample vector input
-    const float g2 = 2.0f * a.loss_scale;
-    const int n_t = a.n_t;
-    if (shared_t && a.grad_t && a.shared_gt) {
-        for (int j = threadIdx.x; j < n_t; j += blockDim.x) s_gt[j] = 0.f;
-        __syncthreads();
-    }
-    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
-    for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
-        // q_i = w_i P_i; dq_i = d (q_(i+1) - q_i); dw_i = d (w_(i+1) - w_i)
-        float P[N][M], q[N][M], w[N], dq[N][M], dw[N];
-#pragma unroll kUnrollN
-        for (int i = 0; i < N; ++i) {
-            if (i > d) break;
+struct GradCurve {
+    static constexpr int N = Deg<D>::N;
+    static constexpr int M = DIM ? DIM : kGradMaxDim;
+    static constexpr int kU = D ? N : 1;  // runtime degree: loops, arrays in local memory
+    int d, dim;
+    float P[N][M], w[N], dq[N][M], dw[N];
+    float acc_c[N][M], acc_w[N], loss;
+
+    __device__ __forceinline__ void setup(const GradArgs& a, int64_t c)
+    {
+        d = Deg<D>::get(a.degree);
+        dim = DIM ? DIM : a.dim;
+        const int dd = D ? D : d;  // a constant bound unrolls; the runtime degree loops
+        float q[N][M];
+#pragma unroll
+        for (int i = 0; i <= dd; ++i) {
             w[i] = RAT ? __ldg(a.weights + c * (d + 1) + i) : 1.f;
 #pragma unroll
             for (int k = 0; k < M; ++k) {
@@ -75,9 +77,8 @@ __global__ void __launch_bounds__(kWarps * 32, grad_min_blocks(D, RAT)) k_grad(c
             }
         }
         const float fd = (float)d;
-#pragma unroll kUnrollN
-        for (int i = 0; i < N - 1; ++i) {
-            if (i >= d) break;
+#pragma unroll
+        for (int i = 0; i < dd; ++i) {
             if (RAT) dw[i] = fd * (w[i + 1] - w[i]);
 #pragma unroll
             for (int k = 0; k < M; ++k) {
@@ -85,126 +86,99 @@ __global__ void __launch_bounds__(kWarps * 32, grad_min_blocks(D, RAT)) k_grad(c
                 dq[i][k] = fd * (q[i + 1][k] - q[i][k]);
             }
         }
-        float acc_c[N][M], acc_w[N];
-        float loss_acc = 0.f;
-#pragma unroll kUnrollN
-        for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int i = 0; i <= dd; ++i) {
             acc_w[i] = 0.f;
 #pragma unroll
             for (int k = 0; k < M; ++k) acc_c[i][k] = 0.f;
         }
-        const float* tc = a.t + c * a.t_stride;
-        const float* gc = gsrc + c * (int64_t)n_t * dim;
-        // prefetched inputs of sample j
-        float t_next = 0.f, v_next[M];
+        loss = 0.f;
+    }
+
+    // One sample: accumulate its dL/dP, dL/dw (and loss) terms; return dL/dt.
+    // FUSED: v is the target and g = g2 (C - v) mask; else v is g.  A sample
+    // past the end arrives with mask 0 (fused) or v = 0, and adds nothing.
+    template <bool FUSED>
+    __device__ __forceinline__ float sample(float traw, const float (&v)[M], float mask, float g2)
+    {
+        const int dd = D ? D : d;
+        const float t = clamp01(traw);
+        const float s = 1.0f - t;
+        // basis triangle; keep level d-1 for the derivative
+        float B[N], Bd[N];
+        B[0] = 1.f;
 #pragma unroll
-        for (int k = 0; k < M; ++k) v_next[k] = 0.f;
-        if (lane < n_t) {
-            t_next = __ldg(tc + lane);
+        for (int r = 1; r <= dd; ++r) {
+            if (r == dd) {
+#pragma unroll
+                for (int i = 0; i < dd; ++i) Bd[i] = B[i];
+            }
+            B[r] = t * B[r - 1];
+#pragma unroll
+            for (int i = r - 1; i >= 1; --i) B[i] = fmaf(t, B[i - 1], s * B[i]);
+            B[0] = s * B[0];
+        }
+        float A[M], dA[M];
+        float W = RAT ? 0.f : 1.f, dW = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; ++k) A[k] = dA[k] = 0.f;
+#pragma unroll
+        for (int i = 0; i <= dd; ++i) {
+            const float bw = RAT ? B[i] * w[i] : B[i];
+            if (RAT) W += bw;
 #pragma unroll
             for (int k = 0; k < M; ++k)
-                if (k < dim) v_next[k] = __ldg(gc + (int64_t)lane * dim + k);
+                if (k < dim) A[k] = fmaf(bw, P[i][k], A[k]);
         }
-        for (int j = lane; j < n_t; j += 32) {
-            const float traw = t_next;
-            float v[M];
 #pragma unroll
-            for (int k = 0; k < M; ++k) v[k] = v_next[k];
-            if (j + 32 < n_t) {
-                t_next = __ldg(tc + j + 32);
+        for (int i = 0; i < dd; ++i) {
+            if (RAT) dW = fmaf(Bd[i], dw[i], dW);
 #pragma unroll
-                for (int k = 0; k < M; ++k)
-                    if (k < dim) v_next[k] = __ldg(gc + (int64_t)(j + 32) * dim + k);
-            }
-            const float t = clamp01(traw);
-            const float s = 1.0f - t;
-            // basis triangle; keep level d-1 for the derivative
-            float B[N], Bd[N];
-            B[0] = 1.f;
-#pragma unroll kUnrollN
-            for (int r = 1; r < N; ++r) {
-                if (r > d) break;
-                if (r == d) {
-#pragma unroll kUnrollN
-                    for (int i = 0; i < N - 1; ++i)
-                        if (i < d) Bd[i] = B[i];
-                }
-                B[r] = t * B[r - 1];
+            for (int k = 0; k < M; ++k)
+                if (k < dim) dA[k] = fmaf(Bd[i], dq[i][k], dA[k]);
+        }
+        const float invW = RAT ? __frcp_rn(W) : 1.f;
+        float C[M], gj[M];
 #pragma unroll
-                for (int i = r - 1; i >= 1; --i) B[i] = fmaf(t, B[i - 1], s * B[i]);
-                B[0] = s * B[0];
-            }
-            float A[M], dA[M];
-            float W = 1.f, dW = 0.f;
-#pragma unroll
-            for (int k = 0; k < M; ++k) A[k] = dA[k] = 0.f;
-            if (RAT) W = 0.f;
-#pragma unroll kUnrollN
-            for (int i = 0; i < N; ++i) {
-                if (i > d) break;
-                const float bw = RAT ? B[i] * w[i] : B[i];
-                if (RAT) W += bw;
-#pragma unroll
-                for (int k = 0; k < M; ++k)
-                    if (k < dim) A[k] = fmaf(bw, P[i][k], A[k]);
-            }
-#pragma unroll kUnrollN
-            for (int i = 0; i < N - 1; ++i) {
-                if (i >= d) break;
-                if (RAT) dW = fmaf(Bd[i], dw[i], dW);
-#pragma unroll
-                for (int k = 0; k < M; ++k)
-                    if (k < dim) dA[k] = fmaf(Bd[i], dq[i][k], dA[k]);
-            }
-            const float invW = RAT ? __frcp_rn(W) : 1.f;
-            float C[M];
-#pragma unroll
-            for (int k = 0; k < M; ++k) C[k] = RAT ? A[k] * invW : A[k];
-            float gj[M];
-            if (fused) {
+        for (int k = 0; k < M; ++k) {
+            C[k] = RAT ? A[k] * invW : A[k];
+            if (FUSED) {
                 // fused squared error: g = 2 s (C - target), loss += ||C - target||^2
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    if (k >= dim) break;
-                    const float r = C[k] - v[k];
-                    gj[k] = g2 * r;
-                    loss_acc = fmaf(r, r, loss_acc);
-                }
+                const float r = (C[k] - v[k]) * mask;
+                gj[k] = g2 * r;
+                if (k < dim) loss = fmaf(r, r, loss);
             } else {
-#pragma unroll
-                for (int k = 0; k < M; ++k) gj[k] = v[k];
-            }
-#pragma unroll kUnrollN
-            for (int i = 0; i < N; ++i) {
-                if (i > d) break;
-                const float f = RAT ? B[i] * w[i] * invW : B[i];
-#pragma unroll
-                for (int k = 0; k < M; ++k)
-                    if (k < dim) acc_c[i][k] = fmaf(f, gj[k], acc_c[i][k]);
-                if (RAT) {
-                    float dot = 0.f;
-#pragma unroll
-                    for (int k = 0; k < M; ++k)
-                        if (k < dim) dot = fmaf(P[i][k] - C[k], gj[k], dot);
-                    acc_w[i] = fmaf(B[i] * invW, dot, acc_w[i]);
-                }
-            }
-            if (a.grad_t) {
-                float gt = 0.f;
-#pragma unroll
-                for (int k = 0; k < M; ++k)
-                    if (k < dim) gt = fmaf(gj[k], RAT ? fmaf(-C[k], dW, dA[k]) : dA[k], gt);
-                gt = (traw >= 0.f && traw <= 1.f) ? (RAT ? gt * invW : gt) : 0.f;
-                if (!shared_t) a.grad_t[c * n_t + j] = gt;
-                else if (a.shared_gt) atomicAdd(s_gt + j, gt);
-                else atomicAdd(a.grad_t + j, gt);
+                gj[k] = v[k];
             }
         }
-        // butterfly: every lane ends with the curve's sums; lane e writes element e
+#pragma unroll
+        for (int i = 0; i <= dd; ++i) {
+            const float f = RAT ? B[i] * w[i] * invW : B[i];
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+                if (k < dim) acc_c[i][k] = fmaf(f, gj[k], acc_c[i][k]);
+            if (RAT) {
+                float dot = 0.f;
+#pragma unroll
+                for (int k = 0; k < M; ++k)
+                    if (k < dim) dot = fmaf(P[i][k] - C[k], gj[k], dot);
+                acc_w[i] = fmaf(B[i] * invW, dot, acc_w[i]);
+            }
+        }
+        float gt = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (k < dim) gt = fmaf(gj[k], RAT ? fmaf(-C[k], dW, dA[k]) : dA[k], gt);
+        return (traw >= 0.f && traw <= 1.f) ? (RAT ? gt * invW : gt) : 0.f;  // clamped t: no dL/dt
+    }
+
+    // butterfly: every lane ends with the curve's sums; lane e writes element e
+    __device__ __forceinline__ void finish(const GradArgs& a, int64_t c, int lane)
+    {
         const int nc = (d + 1) * dim;
-#pragma unroll kUnrollN
-        for (int i = 0; i < N; ++i) {
-            if (i > d) break;
+        const int dd = D ? D : d;
+#pragma unroll
+        for (int i = 0; i <= dd; ++i) {
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 if (k >= dim) break;
@@ -217,13 +191,111 @@ __global__ void __launch_bounds__(kWarps * 32, grad_min_blocks(D, RAT)) k_grad(c
             }
         }
         if (a.loss) {
-            const float l = warp_sum(loss_acc);
+            const float l = warp_sum(loss);
             if (lane == 0) a.loss[c] = a.loss_scale * l;
         }
     }
-    if (shared_t && a.grad_t && a.shared_gt) {
+};
+
+template <int M>
+__device__ __forceinline__ void load_sample(const float* tc, const float* vc, int dim, int n_t, int j, float& t,
+                                            float (&v)[M])
+{
+    t = 0.f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) v[k] = 0.f;
+    if (j < n_t) {
+        t = __ldg(tc + j);
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (k < dim) v[k] = __ldg(vc + j * dim + k);
+    }
+}
+
+template <int GTM>
+__device__ __forceinline__ void put_gt(float* gtc, float* gt_sum, int j, float gt)
+{
+    if (GTM == GT_PER_CURVE) gtc[j] = gt;
+    else if (GTM == GT_SHARED) atomicAdd(gt_sum + j, gt);
+}
+
+template <int D, int DIM, bool RAT, bool FUSED, int GTM>
+__device__ __forceinline__ void grad_curves(const GradArgs& a, float* gt_sum)
+{
+    using G = GradCurve<D, DIM, RAT>;
+    constexpr int M = G::M;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int n_t = a.n_t;
+    const int dim = DIM ? DIM : a.dim;
+    const float* vsrc = FUSED ? a.target : a.g;
+    const float g2 = 2.0f * a.loss_scale;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
+        G e;
+        e.setup(a, c);
+        const float* tc = a.t + c * a.t_stride;
+        const float* vc = vsrc + c * (int64_t)n_t * dim;
+        float* gtc = GTM == GT_PER_CURVE ? a.grad_t + c * (int64_t)n_t : nullptr;
+        if constexpr (grad_pair(D, RAT) == 2) {
+            float tA, tB, vA[M], vB[M];
+            load_sample<M>(tc, vc, dim, n_t, lane, tA, vA);
+            load_sample<M>(tc, vc, dim, n_t, lane + 32, tB, vB);
+            for (int j = lane; j < n_t; j += 64) {
+                const float t0 = tA, t1 = tB;
+                float v0[M], v1[M];
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    v0[k] = vA[k];
+                    v1[k] = vB[k];
+                }
+                load_sample<M>(tc, vc, dim, n_t, j + 64, tA, vA);
+                load_sample<M>(tc, vc, dim, n_t, j + 96, tB, vB);
+                const bool has1 = j + 32 < n_t;
+                const float gt0 = e.template sample<FUSED>(t0, v0, 1.f, g2);
+                const float gt1 = e.template sample<FUSED>(t1, v1, has1 ? 1.f : 0.f, g2);
+                put_gt<GTM>(gtc, gt_sum, j, gt0);
+                if (has1) put_gt<GTM>(gtc, gt_sum, j + 32, gt1);
+            }
+        } else {
+            float tA, vA[M];
+            load_sample<M>(tc, vc, dim, n_t, lane, tA, vA);
+            for (int j = lane; j < n_t; j += 32) {
+                const float t0 = tA;
+                float v0[M];
+#pragma unroll
+                for (int k = 0; k < M; ++k) v0[k] = vA[k];
+                load_sample<M>(tc, vc, dim, n_t, j + 32, tA, vA);
+                put_gt<GTM>(gtc, gt_sum, j, e.template sample<FUSED>(t0, v0, 1.f, g2));
+            }
+        }
+        e.finish(a, c, lane);
+    }
+}
+
+template <int D, int DIM, bool RAT>
+__global__ void __launch_bounds__(kWarps * 32, grad_min_blocks(D, RAT)) k_grad(const GradArgs a)
+{
+    extern __shared__ float s_gt[];  // shared-t dL/dt partial sums of this block
+    const int gtm = !a.grad_t ? GT_NONE : a.t_stride ? GT_PER_CURVE : GT_SHARED;
+    const bool smem_sum = gtm == GT_SHARED && a.shared_gt;
+    float* gt_sum = smem_sum ? s_gt : a.grad_t;
+    if (smem_sum) {
+        for (int j = threadIdx.x; j < a.n_t; j += blockDim.x) s_gt[j] = 0.f;
         __syncthreads();
-        for (int j = threadIdx.x; j < n_t; j += blockDim.x) atomicAdd(a.grad_t + j, s_gt[j]);
+    }
+    if (a.target) {
+        if (gtm == GT_NONE) grad_curves<D, DIM, RAT, true, GT_NONE>(a, gt_sum);
+        else if (gtm == GT_PER_CURVE) grad_curves<D, DIM, RAT, true, GT_PER_CURVE>(a, gt_sum);
+        else grad_curves<D, DIM, RAT, true, GT_SHARED>(a, gt_sum);
+    } else {
+        if (gtm == GT_NONE) grad_curves<D, DIM, RAT, false, GT_NONE>(a, gt_sum);
+        else if (gtm == GT_PER_CURVE) grad_curves<D, DIM, RAT, false, GT_PER_CURVE>(a, gt_sum);
+        else grad_curves<D, DIM, RAT, false, GT_SHARED>(a, gt_sum);
+    }
+    if (smem_sum) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < a.n_t; j += blockDim.x) atomicAdd(a.grad_t + j, s_gt[j]);
     }
 }
 
