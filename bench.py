@@ -405,7 +405,8 @@ def run_precision(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": workload_name(args.n_curves, args.n_t), "variant": args.variant, "n_curves": args.n_curves, "n_t": args.n_t,
+        "config": {"workload": workload_name(args.n_curves, args.n_t), "variant": args.variant,
+                   "n_curves": args.n_curves, "n_t": args.n_t,
                    "degree": 3, "dim": 3, "l2": "flushed between timed steps (256 MiB device write)",
                    "speedup_vs_horner": head["speedup_vs_horner"],
                    "max_norm_err": head.get("max_norm_err")},
@@ -552,6 +553,15 @@ def run_tensor(args):
                              args.warmup)
     kts = st_ts["timed_ms"] / st_ts["timed_launches"]
     n_s, n_v = 65536 * 1024, 4096 * 4096
+    unorm = {}
+    for vname, var in (("TEX_DECASTELJAU", tex), ("TEX_SEILER", texs)):
+        for fname in ("UNORM16", "UNORM8"):
+            fmt = bez.TexFormat[fname]
+            ms_u, st_u = timer.run(lambda var=var, fmt=fmt: bez.bez_eval_surface(s, 32, 32, variant=var, out=so,
+                                                                                 ctx=ctx, tex_format=fmt),
+                                   args.steps, args.warmup)
+            unorm[f"{vname}/{fname}"] = {"points_per_s": n_s * args.steps / (ms_u * 1e-3),
+                                         "kernel_ms": st_u["timed_ms"] / st_u["timed_launches"]}
     ks = st_s["timed_ms"] / st_s["timed_launches"]
     kv = st_v["timed_ms"] / st_v["timed_launches"]
     kt = st_t["timed_ms"] / st_t["timed_launches"]
@@ -562,9 +572,13 @@ def run_tensor(args):
     ref = oracle.surface(sub.cpu().numpy(), 32, 32).reshape(1024, -1, 3)
     diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
 
-    def surf_err(var):
-        got = bez.bez_eval_surface(sub, 32, 32, variant=var, ctx=ctx).cpu().numpy().reshape(1024, -1, 3)
+    def surf_err(var, fmt=bez.TexFormat.AUTO):
+        got = bez.bez_eval_surface(sub, 32, 32, variant=var, ctx=ctx, tex_format=fmt)
+        got = got.cpu().numpy().reshape(1024, -1, 3)
         return float((np.linalg.norm(got.astype(np.float64) - ref, axis=-1).max(axis=1) / diag).max())
+    for key, rec in unorm.items():
+        vname, fname = key.split("/")
+        rec["max_norm_err"] = surf_err(bez.Variant[vname], bez.TexFormat[fname])
     return _hbm_line("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
                      (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
                      ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3_warp",
@@ -578,7 +592,8 @@ def run_tensor(args):
                       "surface_tex_seiler": {"points_per_s": n_s * args.steps / (ms_ts * 1e-3), "kernel_ms": kts,
                                              "gbs": n_s * 12 / (kts * 1e-3) / 1e9, "max_norm_err": surf_err(texs),
                                              "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
-                                                       "coordinate)"}},
+                                                       "coordinate)"},
+                      "surface_tex_unorm": unorm},
                      traffic=TRAFFIC_SURFACE_65536)
 
 
@@ -637,7 +652,8 @@ def run_fit(args):
                      "then Adam, per step", n * args.steps / (ms * 1e-3), "samples/s", args.steps, args.warmup, ms,
                      bytes_launch, kern_ms, "k_grad (fused squared error), mean launch",
                      {"loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5,
-                      "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3), "ms_per_step": ms_a / args.steps,
+                      "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3),
+                                        "ms_per_step": ms_a / args.steps,
                                         "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}})
 
 
@@ -670,7 +686,8 @@ def run_reference(args, rank):
     return {"metric": METRIC, "value": v, "unit": "points/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_name(args.n_curves, args.n_t), "sample_curves_per_step": args.ref_curves, "n_t": args.n_t},
+            "config": {"workload": workload_name(args.n_curves, args.n_t), "sample_curves_per_step": args.ref_curves,
+                       "n_t": args.n_t},
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": threads, "kind": "oracle",
                              "sample": f"{args.ref_curves} curves x {args.n_t} parameters per step"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

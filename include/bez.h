@@ -110,8 +110,9 @@ typedef struct bez_opts {
     int32_t tex_share; /* BEZ_VAR_COISSUE only: samples out of every 8 read through the  *
                         * texture unit, 1..7; 0 = library default (2)                    */
     int32_t tex_format;/* bez_tex_format of texture tiles of bez_eval (texture variants   *
-                        * and BEZ_VAR_COISSUE); texture chains and surfaces take          *
-                        * BEZ_TEX_AUTO only; entry points without textures ignore it      */
+                        * and BEZ_VAR_COISSUE) and of bez_eval_surface (texture           *
+                        * variants); texture chains take BEZ_TEX_AUTO only; entry points  *
+                        * and variants without textures ignore it                         */
 } bez_opts;
 
 /* Opaque context: owns staging buffers, texture atlases, timing events. */
@@ -264,10 +265,13 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
  *   variant TEX_SEILER (same limits): the four column cubics in the 2x2
  *   cubic Seiler layout (Sec. 4), one per channel of a 2D tile, read
  *   bilinearly at (u, u (1 - u)).
- *   Accuracy is that of 8-bit filter weights (about 3 x 2^-8 of the column
- *   range); the tiles live in a context-owned atlas, so texture calls of one
- *   context are ordered on the device.  Other combinations return
- *   BEZ_ERR_UNSUPPORTED.
+ *   Texels are float4 (FP32 input) or half4 (FP16 input), or with
+ *   opts->tex_format UNORM16 / UNORM8 16- or 8-bit codes with one (lo,
+ *   scale) pair per tile and channel, mapped back after filtering as for
+ *   curves.  Accuracy is that of 8-bit filter weights (about 3 x 2^-8 of the
+ *   column range) plus half a code of the tile's range for unorm texels; the
+ *   tiles live in a context-owned atlas, so texture calls of one context are
+ *   ordered on the device.  Other combinations return BEZ_ERR_UNSUPPORTED.
  */
 bez_status bez_eval_surface(bez_ctx ctx, const void* ctrl, int64_t n, int du, int dv, int dim, int nu, int nv,
                             float* out, const bez_opts* opts, void* stream);

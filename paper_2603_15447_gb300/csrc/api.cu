@@ -684,8 +684,6 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
                     "texture tiles (TEX_DECASTELJAU, TEX_SEILER)", var);
     if (tex && (vol || du != 3 || dv != 3))
         return fail(BEZ_ERR_UNSUPPORTED, "texture tiles hold bicubic surfaces only");
-    if (tex && o->tex_format != BEZ_TEX_AUTO)
-        return fail(BEZ_ERR_UNSUPPORTED, "texture surfaces use float4 / half4 tiles (tex_format AUTO)");
     if (tex && nu > kSurfTexMaxRows)
         return fail(BEZ_ERR_UNSUPPORTED, "texture surfaces take at most %d rows in u", kSurfTexMaxRows);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
@@ -716,7 +714,7 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     if (tex) {
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        LaunchResult r = launch_tex_surface(t, var == BEZ_VAR_TEX_SEILER, c->tex, s, hooks_of(c));
+        LaunchResult r = launch_tex_surface(t, var == BEZ_VAR_TEX_SEILER, o->tex_format, c->tex, s, hooks_of(c));
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "%lld patches do not fit one texture atlas", (long long)n);
         if (r.err != cudaSuccess) return cuda_fail(r.err, "texture surface launch");

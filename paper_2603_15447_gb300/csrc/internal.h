@@ -74,10 +74,15 @@ struct TexState {
     Atlas probe;  // 2x2x2 weight probe
     Atlas surf3;  // bicubic surface tiles: four column cubics per 2x2x2 RGBA tile
     Atlas surf2;  // bicubic surface tiles in the 2x2 Seiler layout, one column cubic per channel
-    float4* rescale = nullptr;  // unorm tiles: per curve (offset, scale)
-    int64_t rescale_cap = 0;    // curves the rescale buffer holds
+    float4* rescale = nullptr;  // unorm tiles: per tile (offset, scale)
+    int64_t rescale_cap = 0;    // tiles the rescale buffer holds
     int max3d = 16384, max2d_w = 131072, max2d_h = 65536;
 };
+
+// Texel storage format of an atlas (TEXEL_* of texel.cuh) for an input
+// dtype and a bez_tex_format; the rescale buffer of unorm atlases, n tiles.
+int texel_format(int dtype, int tex_format);
+cudaError_t rescale_buffer(TexState& ts, int fmt, int64_t n, float4** out);
 
 // Texture evaluators: pack the control points into the atlas of `variant`,
 // then evaluate.  `variant` is a bez_variant texture value.
@@ -136,9 +141,10 @@ struct TensorLaunch {
     float* out;
 };
 LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const LaunchHooks& h);
-// Bicubic surfaces through 2x2x2 RGBA texture tiles (nu <= kSurfTexMaxRows).
+// Bicubic surfaces through 2x2x2 RGBA texture tiles (nu <= kSurfTexMaxRows),
+// texels in the storage format of `tex_format` (a bez_tex_format).
 constexpr int kSurfTexMaxRows = 64;
-LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, TexState& ts, cudaStream_t s,
+LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, TexState& ts, cudaStream_t s,
                                 const LaunchHooks& h);
 size_t tensor_product_smem(const TensorLaunch& t);
 

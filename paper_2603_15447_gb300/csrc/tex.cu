@@ -32,6 +32,7 @@
 // [0.25, 0.75] remap of a 2-texel axis becomes x = x0 + 0.5 + t; for the st
 // axis the offset is added after the product (Sec. 4).  Addressing clamps.
 #include "curve_eval.cuh"
+#include "texel.cuh"
 
 namespace bez {
 
@@ -102,36 +103,6 @@ cudaError_t atlas_ensure(Atlas& at, int w, int h, int depth, int fmt)
 
 // ---------------------------------------------------------------- packers
 
-// unorm code of a value in [0, 1] with `levels` = 2^bits - 1, round to nearest
-__device__ __forceinline__ unsigned unorm_code(float v, float levels)
-{
-    const float x = fminf(fmaxf(v, 0.f), 1.f) * levels;
-    return (unsigned)__float2uint_rn(x);
-}
-
-__device__ __forceinline__ void put(cudaSurfaceObject_t s, int fmt, int x, int y, int z, bool is3d, float4 v)
-{
-    if (fmt == 0) {
-        if (is3d) surf3Dwrite(v, s, x * 16, y, z);
-        else surf2Dwrite(v, s, x * 16, y);
-    } else if (fmt == 1) {
-        const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
-        const uint2 bits = make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
-        if (is3d) surf3Dwrite(bits, s, x * 8, y, z);
-        else surf2Dwrite(bits, s, x * 8, y);
-    } else if (fmt == 2) {
-        const ushort4 u = make_ushort4(unorm_code(v.x, 65535.f), unorm_code(v.y, 65535.f), unorm_code(v.z, 65535.f),
-                                       unorm_code(v.w, 65535.f));
-        if (is3d) surf3Dwrite(u, s, x * 8, y, z);
-        else surf2Dwrite(u, s, x * 8, y);
-    } else {
-        const uchar4 u = make_uchar4(unorm_code(v.x, 255.f), unorm_code(v.y, 255.f), unorm_code(v.z, 255.f),
-                                     unorm_code(v.w, 255.f));
-        if (is3d) surf3Dwrite(u, s, x * 4, y, z);
-        else surf2Dwrite(u, s, x * 4, y);
-    }
-}
-
 __device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 __device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 __device__ __forceinline__ float4 scale4(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
@@ -191,14 +162,6 @@ __device__ void seiler_terms_peeled(const float4* b, int d, float4 (&lo)[4], flo
     }
 }
 
-__device__ __forceinline__ float4 min4(float4 a, float4 b)
-{
-    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
-}
-__device__ __forceinline__ float4 max4(float4 a, float4 b)
-{
-    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
-}
 
 // Texels of curve c's tile: emit(x, y, z, value) for every texel.
 template <int KIND, class Emit>
@@ -466,13 +429,13 @@ static int tiles_per_row(int64_t n, int wt, int max_w)
 
 // texel format of a call: float4 / half4 by the control-point type, or the
 // requested unorm format
-static int texel_format(const CurveArgs& a, int tex_format)
+int texel_format(int dtype, int tex_format)
 {
-    return tex_format == 1 ? 2 : tex_format == 2 ? 3 : (a.dtype == 1 ? 1 : 0);
+    return tex_format == 1 ? TEXEL_UNORM16 : tex_format == 2 ? TEXEL_UNORM8 : (dtype == 1 ? TEXEL_F16 : TEXEL_F32);
 }
 
-// per-curve rescale pairs of unorm tiles (context scratch, grown on demand)
-static cudaError_t rescale_buffer(TexState& ts, int fmt, int64_t n, float4** out)
+// per-tile rescale pairs (lo, scale) of unorm atlases (context scratch, grown on demand)
+cudaError_t rescale_buffer(TexState& ts, int fmt, int64_t n, float4** out)
 {
     *out = nullptr;
     if (fmt < 2) return cudaSuccess;
@@ -496,7 +459,7 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, i
                               cudaStream_t s, const LaunchHooks& h)
 {
     const int d = a.degree;
-    const int fmt = texel_format(a, tex_format);
+    const int fmt = texel_format(a.dtype, tex_format);
     int kind, wt;
     bool is3d;
     if (variant == 6) {  // BEZ_VAR_TEX_DECASTELJAU
@@ -630,7 +593,7 @@ LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, T
     const int tw = tiles_per_row(a.n_curves, wt, ts.max2d_w);
     const int64_t rows = (a.n_curves + tw - 1) / tw;
     if (rows * 2 > ts.max2d_h) return {0, cudaErrorInvalidValue};
-    const int fmt = texel_format(a, tex_format);
+    const int fmt = texel_format(a.dtype, tex_format);
     cudaError_t e = atlas_ensure(ts.seil2, tw * wt, (int)(rows * 2), 0, fmt);
     if (e != cudaSuccess) return {0, e};
     float4* rs = nullptr;

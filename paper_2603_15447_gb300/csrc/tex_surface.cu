@@ -19,6 +19,7 @@
 // with texel centres at i + 0.5, so row u reads at (x0+0.5+u, y0+0.5+u,
 // 0.5+u) and u = 0, 1 land on texel centres (exact corners).
 #include "tensor_common.cuh"
+#include "texel.cuh"
 
 namespace bez {
 
@@ -26,37 +27,18 @@ static_assert(kSurfTexMaxRows == kSurfMaxRows, "row limit of the texture surface
 
 struct SurfTexArgs {
     cudaTextureObject_t tex;
-    int tw;  // tiles per atlas row
+    int tw;                 // tiles per atlas row
+    const float4* rescale;  // unorm tiles: (lo, scale) per tile, value = lo + scale x code / levels; else NULL
 };
-
-__device__ __forceinline__ void put3(cudaSurfaceObject_t s, int fmt, int x, int y, int z, float4 v)
-{
-    if (fmt == 0) {
-        surf3Dwrite(v, s, x * 16, y, z);
-    } else {
-        const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
-        surf3Dwrite(make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi)), s,
-                    x * 8, y, z);
-    }
-}
-
-__device__ __forceinline__ void put2(cudaSurfaceObject_t s, int fmt, int x, int y, float4 v)
-{
-    if (fmt == 0) {
-        surf2Dwrite(v, s, x * 16, y);
-    } else {
-        const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
-        surf2Dwrite(make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi)), s,
-                    x * 8, y);
-    }
-}
 
 // one thread per tile (patch, coordinate).  SEILER: the 2x2 cubic Seiler
 // layout (Sec. 4) of each column curve in its channel, [[b0, b3],
 // [b0 + d1, b3 + d2]] with d1 = 3 (b1 - b0) - (b3 - b0) and
 // d2 = 3 (b2 - b3) - (b0 - b3), read bilinearly at (u, u (1 - u)).
+// unorm formats: each tile's texels are stored as lo + scale u per channel
+// (rescale[2q], rescale[2q + 1]).
 template <bool SEILER>
-__global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t surf, int fmt)
+__global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t surf, int fmt, float4* rescale)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int dim = a.dim;
@@ -71,15 +53,45 @@ __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t s
         b[i] = make_float4(load_elem(a.ctrl, a.dtype, base), load_elem(a.ctrl, a.dtype, base + dim),
                            load_elem(a.ctrl, a.dtype, base + 2 * dim), load_elem(a.ctrl, a.dtype, base + 3 * dim));
     }
+    // the tile's distinct texel values: the four control points (de Casteljau
+    // tile: texel(x,y,z) = b[x+y+z]) or the four Seiler corners
+    float4 v[4];
     if (SEILER) {
         const float4 d1 = make_float4(3.f * (b[1].x - b[0].x) - (b[3].x - b[0].x), 3.f * (b[1].y - b[0].y) - (b[3].y - b[0].y),
                                       3.f * (b[1].z - b[0].z) - (b[3].z - b[0].z), 3.f * (b[1].w - b[0].w) - (b[3].w - b[0].w));
         const float4 d2 = make_float4(3.f * (b[2].x - b[3].x) - (b[0].x - b[3].x), 3.f * (b[2].y - b[3].y) - (b[0].y - b[3].y),
                                       3.f * (b[2].z - b[3].z) - (b[0].z - b[3].z), 3.f * (b[2].w - b[3].w) - (b[0].w - b[3].w));
-        put2(surf, fmt, x0, y0, b[0]);
-        put2(surf, fmt, x0 + 1, y0, b[3]);
-        put2(surf, fmt, x0, y0 + 1, make_float4(b[0].x + d1.x, b[0].y + d1.y, b[0].z + d1.z, b[0].w + d1.w));
-        put2(surf, fmt, x0 + 1, y0 + 1, make_float4(b[3].x + d2.x, b[3].y + d2.y, b[3].z + d2.z, b[3].w + d2.w));
+        v[0] = b[0];
+        v[1] = b[3];
+        v[2] = make_float4(b[0].x + d1.x, b[0].y + d1.y, b[0].z + d1.z, b[0].w + d1.w);
+        v[3] = make_float4(b[3].x + d2.x, b[3].y + d2.y, b[3].z + d2.z, b[3].w + d2.w);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = b[i];
+    }
+    if (fmt >= TEXEL_UNORM16) {
+        // per channel: lo + scale u, u in [0, 1], over the tile's values; a
+        // constant channel maps to code 0 (scale 1 avoids dividing by 0)
+        float4 lo = v[0], hi = v[0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i) {
+            lo = min4(lo, v[i]);
+            hi = max4(hi, v[i]);
+        }
+        float4 sc = make_float4(hi.x - lo.x, hi.y - lo.y, hi.z - lo.z, hi.w - lo.w);
+        sc = make_float4(sc.x > 0.f ? sc.x : 1.f, sc.y > 0.f ? sc.y : 1.f, sc.z > 0.f ? sc.z : 1.f, sc.w > 0.f ? sc.w : 1.f);
+        rescale[2 * q] = lo;
+        rescale[2 * q + 1] = sc;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            v[i] = make_float4(__fdiv_rn(v[i].x - lo.x, sc.x), __fdiv_rn(v[i].y - lo.y, sc.y),
+                               __fdiv_rn(v[i].z - lo.z, sc.z), __fdiv_rn(v[i].w - lo.w, sc.w));
+    }
+    if (SEILER) {
+        put(surf, fmt, x0, y0, 0, false, v[0]);
+        put(surf, fmt, x0 + 1, y0, 0, false, v[1]);
+        put(surf, fmt, x0, y0 + 1, 0, false, v[2]);
+        put(surf, fmt, x0 + 1, y0 + 1, 0, false, v[3]);
         return;
     }
 #pragma unroll
@@ -87,7 +99,7 @@ __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t s
 #pragma unroll
         for (int y = 0; y < 2; ++y)
 #pragma unroll
-            for (int x = 0; x < 2; ++x) put3(surf, fmt, x0 + x, y0 + y, z, b[x + y + z]);
+            for (int x = 0; x < 2; ++x) put(surf, fmt, x0 + x, y0 + y, z, true, v[x + y + z]);
 }
 
 // One warp per patch: lanes read the isoline control points of their rows,
@@ -115,8 +127,15 @@ __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const Tensor
             for (int k = 0; k < DIM; ++k) {
                 const int64_t q = p * DIM + k;
                 const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
-                s_x[w][row * DIM + k] = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
-                                               : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
+                float4 X = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
+                                  : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
+                if (ta.rescale) {
+                    // filtering is affine with weights summing to 1: map the filtered code back
+                    const float4 lo = __ldg(ta.rescale + 2 * q), sc = __ldg(ta.rescale + 2 * q + 1);
+                    X = make_float4(fmaf(sc.x, X.x, lo.x), fmaf(sc.y, X.y, lo.y), fmaf(sc.z, X.z, lo.z),
+                                    fmaf(sc.w, X.w, lo.w));
+                }
+                s_x[w][row * DIM + k] = X;
             }
         }
         __syncwarp();
@@ -153,7 +172,7 @@ static int surface_tiles_per_row(int64_t tiles, int max_w)
     return tw;
 }
 
-LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, TexState& ts, cudaStream_t s,
+LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, TexState& ts, cudaStream_t s,
                                 const LaunchHooks& h)
 {
     TensorArgs a{};
@@ -172,13 +191,15 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, TexState& ts
     const int tw = surface_tiles_per_row(tiles, ts.max3d);
     const int64_t rows = (tiles + tw - 1) / tw;
     if (rows * 2 > ts.max3d) return {0, cudaErrorInvalidValue};
-    const int fmt = a.dtype == 1 ? 1 : 0;
+    const int fmt = texel_format(a.dtype, tex_format);
     Atlas& at = seiler ? ts.surf2 : ts.surf3;
     cudaError_t e = atlas_ensure(at, tw * 2, (int)(rows * 2), seiler ? 0 : 2, fmt);
     if (e != cudaSuccess) return {0, e};
+    float4* rs = nullptr;
+    if ((e = rescale_buffer(ts, fmt, tiles, &rs)) != cudaSuccess) return {0, e};
     h.count(h.self);
-    if (seiler) k_pack_surface<true><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt);
-    else k_pack_surface<false><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt);
+    if (seiler) k_pack_surface<true><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt, rs);
+    else k_pack_surface<false><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt, rs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return {1, e};
     const void* kern;
@@ -193,7 +214,7 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, TexState& ts
                : a.dim == 3 ? (const void*)k_surface_tex<3, false>
                             : (const void*)k_surface_tex<4, false>;
     const int grid = persistent_grid(kern, kSurfWarps * 32, 0, h.sm_count, (a.n + kSurfWarps - 1) / kSurfWarps);
-    SurfTexArgs sa{at.tex, tw};
+    SurfTexArgs sa{at.tex, tw, rs};
     void* args[] = {(void*)&a, (void*)&sa};
     h.count(h.self);
     h.begin(h.self, s);

@@ -293,6 +293,43 @@ def test_texture_bicubic_surface(variant, dim, nu, nv, half):
             np.testing.assert_array_equal(got[:, -1, -1], ctrl[:, -1, -1])
 
 
+@pytest.mark.parametrize("variant", ["TEX_DECASTELJAU", "TEX_SEILER"])
+@pytest.mark.parametrize("fmt,levels", [("UNORM16", 65535.0), ("UNORM8", 255.0)])
+@pytest.mark.parametrize("dim,nu,nv", [(3, 32, 32), (1, 7, 19), (4, 64, 5)])
+def test_texture_surface_unorm(variant, fmt, levels, dim, nu, nv):
+    # unorm tiles: per tile and channel (column cubic j of coordinate k) the
+    # texels are stored as codes of (v - lo) / scale with lo, scale the
+    # channel's minimum and range over the tile, mapped back after filtering.
+    # Rounding to the nearest code moves a texel by at most scale / (2 levels);
+    # filtering and the v cubic are convex combinations, so the error bound of
+    # the float tiles grows by half a code of the largest channel range.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(7100 + 10 * dim + nu + int(levels))
+    ctrl = rng.uniform(-1, 1, (211, 4, 4, dim)).astype(np.float32)
+    ctrl[5] = 0.25                                                        # constant patch: every channel flat
+    ctrl[6, :, 2, :] = -0.5                                               # one flat column cubic
+    got = bez.bez_eval_surface(torch.from_numpy(ctrl).cuda(), nu, nv, variant=bez.Variant[variant],
+                               tex_format=bez.TexFormat[fmt]).cpu().numpy().astype(np.float64)
+    ref = oracle.surface(ctrl, nu, nv)
+    b = ctrl.astype(np.float64)                                           # [n][i][j][k]
+    if variant == "TEX_DECASTELJAU":
+        tile = b
+        axes = 3
+    else:
+        d1 = 3 * (b[:, 1] - b[:, 0]) - (b[:, 3] - b[:, 0])
+        d2 = 3 * (b[:, 2] - b[:, 3]) - (b[:, 0] - b[:, 3])
+        tile = np.stack([b[:, 0], b[:, 3], b[:, 0] + d1, b[:, 3] + d2], 1)
+        axes = 2
+    col_range = (tile.max(axis=1) - tile.min(axis=1)).max(axis=1)         # [n][dim]
+    mag = np.abs(tile).max(axis=(1, 2))
+    tol = (axes * WERR + 0.5 / levels) * col_range + 8 * U * mag
+    err = np.abs(got - ref)
+    assert np.all(err <= tol[:, None, None, :])
+    # a flat channel is stored as code 0 with lo = its value: exact up to the FP32 v stage
+    assert np.abs(got[5] - 0.25).max() <= 8 * U
+
+
 def test_texture_surface_unsupported():
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
