@@ -553,6 +553,14 @@ def run_tensor(args):
                              args.warmup)
     kts = st_ts["timed_ms"] / st_ts["timed_launches"]
     n_s, n_v = 65536 * 1024, 4096 * 4096
+    vol_tex = {}
+    for vname in ("TEX_DECASTELJAU", "TEX_SEILER"):
+        var = bez.Variant[vname]
+        ms_vt, st_vt = timer.run(lambda var=var: bez.bez_eval_volume(v, 16, 16, 16, variant=var, out=vo, ctx=ctx),
+                                 args.steps, args.warmup)
+        kvt = st_vt["timed_ms"] / st_vt["timed_launches"]
+        vol_tex[vname] = {"values_per_s": n_v * args.steps / (ms_vt * 1e-3), "kernel_ms": kvt,
+                          "gbs": (n_v * 4) / (kvt * 1e-3) / 1e9}
     unorm = {}
     for vname, var in (("TEX_DECASTELJAU", tex), ("TEX_SEILER", texs)):
         for fname in ("UNORM16", "UNORM8"):
@@ -579,6 +587,12 @@ def run_tensor(args):
     for key, rec in unorm.items():
         vname, fname = key.split("/")
         rec["max_norm_err"] = surf_err(bez.Variant[vname], bez.TexFormat[fname])
+    vsub = v[:256].contiguous()
+    vref = oracle.volume(vsub.cpu().numpy(), 16, 16, 16).reshape(256, -1)
+    vspan = np.maximum(vref.max(axis=1) - vref.min(axis=1), 2.0 ** -4)
+    for vname, rec in vol_tex.items():
+        got = bez.bez_eval_volume(vsub, 16, 16, 16, variant=bez.Variant[vname], ctx=ctx).cpu().numpy()
+        rec["max_norm_err"] = float((np.abs(got.reshape(256, -1) - vref).max(axis=1) / vspan).max())
     return _hbm_line("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
                      (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
                      ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3_warp",
@@ -593,7 +607,8 @@ def run_tensor(args):
                                              "gbs": n_s * 12 / (kts * 1e-3) / 1e9, "max_norm_err": surf_err(texs),
                                              "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
                                                        "coordinate)"},
-                      "surface_tex_unorm": unorm},
+                      "surface_tex_unorm": unorm,
+                      "volume_tex": vol_tex},
                      traffic=TRAFFIC_SURFACE_65536)
 
 

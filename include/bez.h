@@ -265,6 +265,10 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
  *   variant TEX_SEILER (same limits): the four column cubics in the 2x2
  *   cubic Seiler layout (Sec. 4), one per channel of a 2D tile, read
  *   bilinearly at (u, u (1 - u)).
+ *   bez_eval_volume with TEX_DECASTELJAU / TEX_SEILER: tricubic scalar
+ *   volumes (dim 1, nu <= 32, nw a multiple of 4, out 16-byte aligned);
+ *   tile (p, j) holds the u cubics C[.][j][l] in channel l, one read per
+ *   (row u, j), v and w contract in FP32.
  *   Texels are float4 (FP32 input) or half4 (FP16 input), or with
  *   opts->tex_format UNORM16 / UNORM8 16- or 8-bit codes with one (lo,
  *   scale) pair per tile and channel, mapped back after filtering as for

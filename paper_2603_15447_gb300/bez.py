@@ -375,15 +375,17 @@ def bez_eval_surface(ctrl, nu, nv, *, variant=Variant.AUTO, out=None, stream=Non
     return out
 
 
-def bez_eval_volume(ctrl, nu, nv, nw, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None):
+def bez_eval_volume(ctrl, nu, nv, nw, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None,
+                    tex_format=TexFormat.AUTO):
     """Tensor-product volumes ``ctrl`` [n][du+1][dv+1][dw+1][dim] on an
-    nu x nv x nw uniform grid -> [n][nu][nv][nw][dim]."""
+    nu x nv x nw uniform grid -> [n][nu][nv][nw][dim].  ``tex_format``: texel
+    storage of the texture variants (tricubic scalar volumes)."""
     n, du1, dv1, dw1, dim = ctrl.shape
     if out is None:
         out = _empty_like_location(ctrl, (n, nu, nv, nw, dim))
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync)
+    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync, tex_format=tex_format)
     _check(lib().bez_eval_volume(c.handle, _ptr(ctrl), n, du1 - 1, dv1 - 1, dw1 - 1, dim, nu, nv, nw, _ptr(out),
                                  ctypes.byref(o), _stream_handle(stream, dev)))
     return out

@@ -680,12 +680,15 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER;
     if (var != BEZ_VAR_AUTO && var != BEZ_VAR_BERNSTEIN && !tex)
         return fail(BEZ_ERR_UNSUPPORTED,
-                    "variant %d: grids run on CUDA cores (AUTO / BERNSTEIN) or, for bicubic surfaces, through "
-                    "texture tiles (TEX_DECASTELJAU, TEX_SEILER)", var);
-    if (tex && (vol || du != 3 || dv != 3))
-        return fail(BEZ_ERR_UNSUPPORTED, "texture tiles hold bicubic surfaces only");
-    if (tex && nu > kSurfTexMaxRows)
+                    "variant %d: grids run on CUDA cores (AUTO / BERNSTEIN) or, for bicubic surfaces and tricubic "
+                    "scalar volumes, through texture tiles (TEX_DECASTELJAU, TEX_SEILER)", var);
+    if (tex && (du != 3 || dv != 3 || (vol && (dw != 3 || dim != 1))))
+        return fail(BEZ_ERR_UNSUPPORTED, "texture tiles hold bicubic surfaces and tricubic scalar volumes only");
+    if (tex && !vol && nu > kSurfTexMaxRows)
         return fail(BEZ_ERR_UNSUPPORTED, "texture surfaces take at most %d rows in u", kSurfTexMaxRows);
+    if (tex && vol && (nu > kVolTexMaxRows || nw % 4 != 0))
+        return fail(BEZ_ERR_UNSUPPORTED, "texture volumes take at most %d rows in u and nw a multiple of 4",
+                    kVolTexMaxRows);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     TensorLaunch t{};
     t.dtype = o->dtype;
@@ -711,13 +714,15 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     st = stg.out(out, (size_t)n * nu * nv * (vol ? nw : 1) * dim * sizeof(float), 2, &od);
     if (st != BEZ_OK) return st;
     t.out = static_cast<float*>(od);
+    if (tex && vol && (reinterpret_cast<uintptr_t>(t.out) & 15) != 0)
+        return fail(BEZ_ERR_UNSUPPORTED, "texture volumes write float4s: out must be 16-byte aligned");
     if (tex) {
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
         LaunchResult r = launch_tex_surface(t, var == BEZ_VAR_TEX_SEILER, o->tex_format, c->tex, s, hooks_of(c));
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "%lld patches do not fit one texture atlas", (long long)n);
-        if (r.err != cudaSuccess) return cuda_fail(r.err, "texture surface launch");
+        if (r.err != cudaSuccess) return cuda_fail(r.err, "texture tile launch");
         BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
         c->tex_used = true;
         return stg.finish(o->sync);

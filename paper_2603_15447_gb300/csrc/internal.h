@@ -141,9 +141,12 @@ struct TensorLaunch {
     float* out;
 };
 LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const LaunchHooks& h);
-// Bicubic surfaces through 2x2x2 RGBA texture tiles (nu <= kSurfTexMaxRows),
-// texels in the storage format of `tex_format` (a bez_tex_format).
+// Bicubic surfaces (nu <= kSurfTexMaxRows) and tricubic scalar volumes (nu <=
+// kVolTexMaxRows, nw a multiple of 4, out 16-byte aligned) through RGBA
+// texture tiles, texels in the storage format of `tex_format` (a
+// bez_tex_format).
 constexpr int kSurfTexMaxRows = 64;
+constexpr int kVolTexMaxRows = 32;
 LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, TexState& ts, cudaStream_t s,
                                 const LaunchHooks& h);
 size_t tensor_product_smem(const TensorLaunch& t);

@@ -1,5 +1,6 @@
-// tex_surface.cu -- bicubic surfaces through the texture unit (paper Sec. 2.2:
-// a 2x2x2 RGBA de Casteljau tile holds four cubics, one per channel).
+// tex_surface.cu -- bicubic surfaces and tricubic scalar volumes through the
+// texture unit (paper Sec. 2.2: a 2x2x2 RGBA de Casteljau tile holds four
+// cubics, one per channel).
 //
 // For coordinate k of patch p the tile stores the four column curves
 // C[.][j][k], j = 0..3, one per channel: texel(x,y,z) channel j =
@@ -14,25 +15,28 @@
 // 2D atlas, read bilinearly at (u, u (1 - u)); two filtered axes instead of
 // three, and a 2D fetch rate.
 //
-// Layout: tile q = p * dim + k sits at texel (2 (q mod tw), 2 (q div tw), 0)
-// of a float4 (or half4) 3D atlas of depth 2; coordinates are unnormalised
-// with texel centres at i + 0.5, so row u reads at (x0+0.5+u, y0+0.5+u,
-// 0.5+u) and u = 0, 1 land on texel centres (exact corners).
+// Tricubic scalar volumes (Sec. 6 leaves volumes as future work) take the
+// same tiles one axis up: tile q = 4 p + j holds the u cubics C[.][j][l],
+// l = 0..3, one per channel, so one read per (row u, j) gives Y[u][j][.],
+// and v and w contract on the FP32 pipes (k_volume_tricubic1_warp).
+//
+// Layout: surface tile q = p * dim + k sits at texel (2 (q mod tw),
+// 2 (q div tw), 0) of a float4, half4 or unorm 3D atlas of depth 2 (2D for
+// Seiler tiles); coordinates are unnormalised with texel centres at i + 0.5,
+// so row u reads at (x0+0.5+u, y0+0.5+u, 0.5+u) and u = 0, 1 land on texel
+// centres (exact corners).
 #include "tensor_common.cuh"
 #include "texel.cuh"
 
 namespace bez {
 
 static_assert(kSurfTexMaxRows == kSurfMaxRows, "row limit of the texture surface kernel");
+static_assert(kVolTexMaxRows == kVolMaxRows, "row limit of the texture volume kernel");
 
-struct SurfTexArgs {
-    cudaTextureObject_t tex;
-    int tw;                 // tiles per atlas row
-    const float4* rescale;  // unorm tiles: (lo, scale) per tile, value = lo + scale x code / levels; else NULL
-};
-
-// one thread per tile (patch, coordinate).  SEILER: the 2x2 cubic Seiler
-// layout (Sec. 4) of each column curve in its channel, [[b0, b3],
+// One thread per tile: four u cubics, one per channel.  Surface tile
+// q = p dim + k holds the column cubics C[.][j][k] (channel j); volume tile
+// q = 4 p + j (scalar volumes) holds C[.][j][l] (channel l).  SEILER: the
+// 2x2 cubic Seiler layout (Sec. 4) of each cubic in its channel, [[b0, b3],
 // [b0 + d1, b3 + d2]] with d1 = 3 (b1 - b0) - (b3 - b0) and
 // d2 = 3 (b2 - b3) - (b0 - b3), read bilinearly at (u, u (1 - u)).
 // unorm formats: each tile's texels are stored as lo + scale u per channel
@@ -41,17 +45,21 @@ template <bool SEILER>
 __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t surf, int fmt, float4* rescale)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vol = a.dw >= 0;
     const int dim = a.dim;
-    if (q >= a.n * dim) return;
-    const int64_t p = q / dim;
-    const int k = (int)(q - p * dim);
+    const int per = vol ? 4 : dim;  // tiles per patch / volume
+    if (q >= a.n * per) return;
+    const int64_t p = q / per;
+    const int r = (int)(q - p * per);
     const int x0 = (int)(q % tw) * 2, y0 = (int)(q / tw) * 2;
-    float4 b[4];  // b[i] = (C[i][0][k], C[i][1][k], C[i][2][k], C[i][3][k])
+    // b[i] = the four cubics' control point i: C[i][0..3][r] (surface) or C[i][r][0..3] (volume)
+    const int cs = vol ? 1 : dim;   // channel stride in elements
+    float4 b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int64_t base = ((p * 4 + i) * 4) * dim + k;
-        b[i] = make_float4(load_elem(a.ctrl, a.dtype, base), load_elem(a.ctrl, a.dtype, base + dim),
-                           load_elem(a.ctrl, a.dtype, base + 2 * dim), load_elem(a.ctrl, a.dtype, base + 3 * dim));
+        const int64_t base = vol ? ((p * 4 + i) * 4 + r) * 4 : ((p * 4 + i) * 4) * dim + r;
+        b[i] = make_float4(load_elem(a.ctrl, a.dtype, base), load_elem(a.ctrl, a.dtype, base + cs),
+                           load_elem(a.ctrl, a.dtype, base + 2 * cs), load_elem(a.ctrl, a.dtype, base + 3 * cs));
     }
     // the tile's distinct texel values: the four control points (de Casteljau
     // tile: texel(x,y,z) = b[x+y+z]) or the four Seiler corners
@@ -87,19 +95,19 @@ __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t s
             v[i] = make_float4(__fdiv_rn(v[i].x - lo.x, sc.x), __fdiv_rn(v[i].y - lo.y, sc.y),
                                __fdiv_rn(v[i].z - lo.z, sc.z), __fdiv_rn(v[i].w - lo.w, sc.w));
     }
-    if (SEILER) {
+    if constexpr (SEILER) {
         put(surf, fmt, x0, y0, 0, false, v[0]);
         put(surf, fmt, x0 + 1, y0, 0, false, v[1]);
         put(surf, fmt, x0, y0 + 1, 0, false, v[2]);
         put(surf, fmt, x0 + 1, y0 + 1, 0, false, v[3]);
-        return;
+    } else {
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int y = 0; y < 2; ++y)
+#pragma unroll
+                for (int x = 0; x < 2; ++x) put(surf, fmt, x0 + x, y0 + y, z, true, v[x + y + z]);
     }
-#pragma unroll
-    for (int z = 0; z < 2; ++z)
-#pragma unroll
-        for (int y = 0; y < 2; ++y)
-#pragma unroll
-            for (int x = 0; x < 2; ++x) put(surf, fmt, x0 + x, y0 + y, z, true, v[x + y + z]);
 }
 
 // One warp per patch: lanes read the isoline control points of their rows,
@@ -129,12 +137,7 @@ __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const Tensor
                 const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
                 float4 X = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
                                   : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
-                if (ta.rescale) {
-                    // filtering is affine with weights summing to 1: map the filtered code back
-                    const float4 lo = __ldg(ta.rescale + 2 * q), sc = __ldg(ta.rescale + 2 * q + 1);
-                    X = make_float4(fmaf(sc.x, X.x, lo.x), fmaf(sc.y, X.y, lo.y), fmaf(sc.z, X.z, lo.z),
-                                    fmaf(sc.w, X.w, lo.w));
-                }
+                if (ta.rescale) X = ta_rescale(ta, q, X);
                 s_x[w][row * DIM + k] = X;
             }
         }
@@ -187,7 +190,8 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_form
     a.nv = t.nv;
     a.nw = t.nw;
     a.out = t.out;
-    const int64_t tiles = a.n * a.dim;
+    const bool vol = a.dw >= 0;
+    const int64_t tiles = a.n * (vol ? 4 : a.dim);
     const int tw = surface_tiles_per_row(tiles, ts.max3d);
     const int64_t rows = (tiles + tw - 1) / tw;
     if (rows * 2 > ts.max3d) return {0, cudaErrorInvalidValue};
@@ -203,7 +207,10 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_form
     e = cudaGetLastError();
     if (e != cudaSuccess) return {1, e};
     const void* kern;
-    if (seiler)
+    if (vol)
+        kern = seiler ? (const void*)k_volume_tricubic1_warp<VOL_U_TEX_SEILER>
+                      : (const void*)k_volume_tricubic1_warp<VOL_U_TEX_DC>;
+    else if (seiler)
         kern = a.dim == 1   ? (const void*)k_surface_tex<1, true>
                : a.dim == 2 ? (const void*)k_surface_tex<2, true>
                : a.dim == 3 ? (const void*)k_surface_tex<3, true>

@@ -330,6 +330,46 @@ def test_texture_surface_unorm(variant, fmt, levels, dim, nu, nv):
     assert np.abs(got[5] - 0.25).max() <= 8 * U
 
 
+@pytest.mark.parametrize("variant", ["TEX_DECASTELJAU", "TEX_SEILER"])
+@pytest.mark.parametrize("fmt,levels", [("AUTO", 0.0), ("UNORM16", 65535.0), ("UNORM8", 255.0)])
+@pytest.mark.parametrize("nu,nv,nw", [(16, 16, 16), (32, 5, 8), (1, 1, 4), (7, 33, 12)])
+def test_texture_tricubic_volume(variant, fmt, levels, nu, nv, nw):
+    # Tricubic scalar volumes through the surface tiles one axis up: tile
+    # (p, j) holds the u cubics C[.][j][l] in channel l, one filtered read per
+    # (row u, j) gives Y[u][j][.], and the v and w stages are FP32 convex
+    # combinations.  So the error is that of one filtered read of a tile
+    # (axes x WERR of the largest channel range, plus half a code of it for
+    # unorm texels), the same bound as the surfaces.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(7300 + nu + 3 * nv + 7 * nw + int(levels))
+    ctrl = rng.normal(size=(129, 4, 4, 4, 1)).astype(np.float32)
+    ctrl[3] = -1.5                                                        # constant volume
+    got = bez.bez_eval_volume(torch.from_numpy(ctrl).cuda(), nu, nv, nw, variant=bez.Variant[variant],
+                              tex_format=bez.TexFormat[fmt]).cpu().numpy().astype(np.float64)
+    ref = oracle.volume(ctrl, nu, nv, nw)
+    b = ctrl[..., 0].astype(np.float64)                                  # [n][i][j][l]
+    if variant == "TEX_DECASTELJAU":
+        tile, axes = b, 3
+    else:
+        d1 = 3 * (b[:, 1] - b[:, 0]) - (b[:, 3] - b[:, 0])
+        d2 = 3 * (b[:, 2] - b[:, 3]) - (b[:, 0] - b[:, 3])
+        tile, axes = np.stack([b[:, 0], b[:, 3], b[:, 0] + d1, b[:, 3] + d2], 1), 2
+    rng_jl = (tile.max(axis=1) - tile.min(axis=1)).max(axis=(1, 2))     # [n]
+    mag = np.abs(tile).max(axis=(1, 2, 3))
+    q = 0.5 / levels if levels else 0.0
+    tol = (axes * WERR + q) * rng_jl + 12 * U * mag
+    err = np.abs(got - ref).max(axis=(1, 2, 3, 4))
+    assert np.all(err <= tol), (err / np.maximum(tol, 1e-30)).max()
+    assert np.abs(got[3] + 1.5).max() <= 12 * U * 1.5                     # flat: exact up to the FP32 v, w stages
+    if fmt == "AUTO":
+        # texel centres: u = 0 and u = 1 read the corner texels exactly, and the
+        # v, w stages at their ends select a single control point
+        np.testing.assert_array_equal(got[:, 0, 0, 0, 0], ctrl[:, 0, 0, 0, 0])
+        if nu > 1 and nv > 1 and nw > 1:
+            np.testing.assert_array_equal(got[:, -1, -1, -1, 0], ctrl[:, -1, -1, -1, 0])
+
+
 def test_texture_surface_unsupported():
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
@@ -344,7 +384,16 @@ def test_texture_surface_unsupported():
         bez.bez_eval_surface(torch.zeros((2, 4, 4, 3), device="cuda", dtype=torch.bfloat16), 8, 8, variant=tex)
     assert e.value.status == bez.Status.UNSUPPORTED
     with pytest.raises(bez.BezError) as e:
-        bez.bez_eval_volume(torch.zeros((2, 4, 4, 4, 1), device="cuda"), 4, 4, 4, variant=tex)
+        bez.bez_eval_volume(torch.zeros((2, 4, 4, 4, 3), device="cuda"), 4, 4, 4, variant=tex)   # not scalar
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_volume(torch.zeros((2, 4, 4, 4, 1), device="cuda"), 4, 4, 6, variant=tex)   # nw % 4
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_volume(torch.zeros((2, 4, 4, 4, 1), device="cuda"), 33, 4, 4, variant=tex)  # rows > 32
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_volume(torch.zeros((2, 3, 4, 4, 1), device="cuda"), 4, 4, 4, variant=tex)   # not tricubic
     assert e.value.status == bez.Status.UNSUPPORTED
 
 
