@@ -57,9 +57,11 @@ T_OPS, LEN_OPS = 9, 8
 # kernels, per unit of work; null in the JSON line for other kernels.  The
 # curve kernel was captured on 131,072 curves (6,308,864 B: the control
 # points; the 4 B lengths stay in L2) and scales with the curve count; the
-# surface kernel on the full 65,536-patch tensor workload.
+# surface kernel on the full 65,536-patch tensor workload; the fused adjoint
+# on the full 65,536 x 512 fit step.
 TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6308864 / 131072}
 TRAFFIC_SURFACE_65536 = 12626688 + 743121664
+TRAFFIC_FIT_65536x512 = 540115968 + 121733376
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
             "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
 # filtered fetches per point and the peak they are held to
@@ -669,7 +671,8 @@ def run_fit(args):
                      {"loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5,
                       "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3),
                                         "ms_per_step": ms_a / args.steps,
-                                        "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}})
+                                        "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}},
+                     traffic=TRAFFIC_FIT_65536x512 if (n_curves, n_t) == (65536, 512) else None)
 
 
 # ------------------------------------------------------------------ reference arm
