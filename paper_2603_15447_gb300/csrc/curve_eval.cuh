@@ -181,24 +181,27 @@ struct Eval<VAR_HORNER_CENTRED, D, DIM> {
     // b_i[k], in v); lane 3m + k forms a[m][k] = sum_i T_d[m][i] b_i[k] (FP64
     // from degree 5, like setup) and the warp broadcasts the coefficients.
     // One dot product per lane instead of the whole conversion per lane.
-    __device__ __forceinline__ void setup_warp(float v, int lane)
+    // base: first lane of the group holding the curve (0 for a whole warp;
+    // 0 or 16 when two curves share a warp)
+    __device__ __forceinline__ void setup_warp(float v, int lane, int base = 0)
     {
         static_assert(D > 0 && DIM == 3 && 3 * (D + 1) <= 32, "fixed-degree 3D curves only");
         d = D;
         using S = typename std::conditional<(D >= kFp64SetupCentred), double, float>::type;
-        const int m = lane < 3 * (D + 1) ? lane / 3 : 0;
-        const int k = lane < 3 * (D + 1) ? lane - 3 * m : 0;
+        const int li = lane - base;
+        const int m = li < 3 * (D + 1) ? li / 3 : 0;
+        const int k = li < 3 * (D + 1) ? li - 3 * m : 0;
         S acc = (S)0;
 #pragma unroll
         for (int i = 0; i <= D; ++i) {
-            const float bik = __shfl_sync(kFull, v, 3 * i + k);
+            const float bik = __shfl_sync(kFull, v, base + 3 * i + k);
             acc = fma((S)kCentredT.t[D][m][i], (S)bik, acc);
         }
         const float cm = (float)acc;
 #pragma unroll
         for (int mm = 0; mm <= D; ++mm)
 #pragma unroll
-            for (int kk = 0; kk < 3; ++kk) a[mm][kk] = __shfl_sync(kFull, cm, 3 * mm + kk);
+            for (int kk = 0; kk < 3; ++kk) a[mm][kk] = __shfl_sync(kFull, cm, base + 3 * mm + kk);
     }
     __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const { eval_u(t - 0.5f, P); }
     // evaluate at u = t - 1/2
@@ -507,6 +510,7 @@ struct Pick<VAR, 0, DIM> {
 
 constexpr int kWarps = 8;  // warps per block; one curve per warp per iteration
 constexpr int kCurvesPerWarp = 8;  // curves per warp when the grid is not persistent
+constexpr int kPairsPerWarp = 4;   // the same for the two-curves-per-warp kernel
 
 template <int TM>
 __device__ __forceinline__ float param(const CurveArgs& a, int64_t c, int j, uint32_t kc)
@@ -733,7 +737,76 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_curve(const CurveArgs a)
     }
 }
 
+// Two curves per warp for the fused centred-Horner length of 3D curves of
+// degree <= 4 under the pre-mixed draw: lanes 0-15 take curve 2 p, lanes
+// 16-31 curve 2 p + 1.  Each half loads its 3 (d + 1) control values with
+// one request, converts them cooperatively (setup_warp with a base lane),
+// walks runs of a multiple of 4 samples per lane and reduces its length over
+// 16 lanes, so the per-curve work (load, conversion, shuffles, reduction)
+// is shared by twice the samples of a lane compared with one curve per warp.
+// The sums run over 16 runs of about n_t / 16 samples.
+template <int D>
+__global__ void __launch_bounds__(kWarps * 32, 5) k_curve_pair(const CurveArgs a)
+{
+    using E = Eval<VAR_HORNER_CENTRED, D, 3>;
+    constexpr int PER = 3 * (D + 1);
+    static_assert(PER <= 16, "a half warp holds one curve's control values");
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int half = lane >> 4, li = lane & 15, base = lane & 16;
+    const int64_t n_pairs = (a.n_curves + 1) / 2;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    auto load = [&](int64_t pr) {
+        const int64_t c = 2 * pr + half;
+        return (c < a.n_curves && li < PER) ? load_elem(a.ctrl, a.dtype, c * PER + li) : 0.f;
+    };
+    const int n_t = a.n_t;
+    const int chunk = ((n_t + 15) / 16 + 3) & ~3;
+    int64_t pr = (int64_t)blockIdx.x * kWarps + wib;
+    float v = load(pr);
+    for (; pr < n_pairs; pr += n_warps) {
+        const int64_t c = 2 * pr + half;
+        const bool live = c < a.n_curves;  // the last pair may have one curve
+        E e;
+        e.setup_warp(v, lane, base);
+        v = load(pr + n_warps);  // prefetch this warp's next pair
+        const uint32_t kc = curve_key<TM_HASH16>(a, c);
+        const int jb = li * chunk;
+        const int je = live ? min(jb + chunk, n_t) : jb;
+        float acc = 0.f;
+        float first[3] = {0.f, 0.f, 0.f}, prev[3] = {0.f, 0.f, 0.f};
+        if (jb < je) acc = run_length_h16<E, 3>(e, kc, jb, je, first, prev);
+        float pl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pl[k] = __shfl_up_sync(kFull, prev[k], 1);
+        if (li > 0 && jb < je) acc += seg_len<3>(first, pl);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);  // within the half
+        if (li == 0 && live) a.out[c] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- dispatch
+
+// Grid of the pair kernel: as launch_one, with pairs of curves as the unit.
+template <int D>
+LaunchResult launch_pair(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h)
+{
+    auto kern = k_curve_pair<D>;
+    const int64_t n_pairs = (a.n_curves + 1) / 2;
+    const int64_t work = (n_pairs + kWarps - 1) / kWarps;
+    int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    if (work > grid) {
+        const int64_t g = (n_pairs + (int64_t)kWarps * kPairsPerWarp - 1) / ((int64_t)kWarps * kPairsPerWarp);
+        if (g > grid) grid = (int)(g < 2147483647 ? g : 2147483647);
+    }
+    h.count(h.self);
+    h.begin(h.self, s);
+    kern<<<grid, kWarps * 32, 0, s>>>(a);
+    cudaError_t err = cudaGetLastError();
+    h.end(h.self, s);
+    return {1, err};
+}
 
 template <int VAR, int D, int DIM, int TM, int OM>
 LaunchResult launch_one(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h)
@@ -769,7 +842,10 @@ LaunchResult launch_modes(const CurveArgs& a, int tm, int om, cudaStream_t s, co
     if (tm == TM_ARRAY) return launch_one<VAR, D, DIM, TM_ARRAY, OM_LENGTH>(a, s, h);
     if (tm == TM_UNIFORM) return launch_one<VAR, D, DIM, TM_UNIFORM, OM_LENGTH>(a, s, h);
     // the fused evaluate-and-measure form of 3D curves of fixed degree gets the
-    // pre-mixed draw when every sample index fits 16 bits
+    // pre-mixed draw when every sample index fits 16 bits; centred Horner up
+    // to degree 4 with at least 64 samples runs two curves per warp
+    if constexpr (VAR == VAR_HORNER_CENTRED && D > 0 && D <= 4 && DIM == 3)
+        if (a.n_t >= 64 && a.n_t <= 65536) return launch_pair<D>(a, s, h);
     if (D > 0 && DIM == 3 && a.n_t <= 65536) return launch_one<VAR, D, DIM, (D > 0 && DIM == 3 ? TM_HASH16 : TM_HASH), OM_LENGTH>(a, s, h);
     return launch_one<VAR, D, DIM, TM_HASH, OM_LENGTH>(a, s, h);
 }
