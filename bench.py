@@ -55,11 +55,13 @@ T_OPS, LEN_OPS = 9, 8
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels, per unit of work; null in the JSON line for other kernels.  The
-# curve kernel was captured on 131,072 curves (6,308,864 B: the control
+# curve kernel was captured on 131,072 curves (6,307,584 B: the control
 # points; the 4 B lengths stay in L2) and scales with the curve count; the
 # surface kernel on the full 65,536-patch tensor workload; the fused adjoint
 # on the full 65,536 x 512 fit step.
-TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6308864 / 131072}
+TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6307584 / 131072}
+# the kernel behind each headline variant's fused length (cubic 3D, hashed t)
+KERNEL_NAME = {"HORNER_CENTRED": "k_curve_pair (two curves per warp)", "HALF2": "k_curve_h2"}
 TRAFFIC_SURFACE_65536 = 12626688 + 743121664
 TRAFFIC_FIT_65536x512 = 540115968 + 121733376
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
@@ -414,7 +416,8 @@ def run_precision(args, rank, world, local_rank):
                    "max_norm_err": head.get("max_norm_err")},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_alu / 1e12, "unit": "Tops/s",
                      "frac": achieved / peak_alu, "traffic": traffic, "peak_source": peak_note,
-                     "ops_per_launch": ops_launch, "kernel": "k_curve (fused draw + eval + polyline length)",
+                     "ops_per_launch": ops_launch,
+                     "kernel": KERNEL_NAME.get(args.variant, "k_curve") + " (fused draw + eval + polyline length)",
                      "measured_fma_peak_tops": peaks["fma"] / 1e12},
         "e2e": {"value": pts_step / e2e_s, "unit": "points/s",
                 "h2d_bytes_per_step": int(ctrl_np.nbytes), "d2h_bytes_per_step": int(args.n_curves * 4)},
