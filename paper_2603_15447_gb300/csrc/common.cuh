@@ -101,4 +101,24 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Warp totals of 16 values by recursive halving (a reduce-scatter): at each
+// level a lane keeps one half of its values, sends the other half to its
+// partner and adds what the partner sent for the kept half.  Returns, in
+// lanes 2i and 2i + 1, the warp total of v[i]; 16 shuffles instead of the
+// 80 of sixteen butterflies.  v is overwritten.
+__device__ __forceinline__ float warp_sum16_scatter(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = upper ? v[i] : v[i + h];
+            const float keep = upper ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
 }  // namespace bez

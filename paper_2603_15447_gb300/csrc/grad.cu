@@ -172,9 +172,54 @@ struct GradCurve {
         return (traw >= 0.f && traw <= 1.f) ? (RAT ? gt * invW : gt) : 0.f;  // clamped t: no dL/dt
     }
 
-    // butterfly: every lane ends with the curve's sums; lane e writes element e
+    // Per-curve sums over the warp.  Fixed degree and dim: the values
+    // (dL/dP, dL/dw, loss) go through one 16-value reduce-scatter, lane 2e
+    // writing value e, and any beyond 16 through butterflies; otherwise one
+    // butterfly per value, lane e writing element e.
     __device__ __forceinline__ void finish(const GradArgs& a, int64_t c, int lane)
     {
+        if constexpr (D > 0 && DIM > 0) {
+            constexpr int NC = N * M;                      // dL/dP values
+            constexpr int NV = NC + (RAT ? N : 0) + 1;     // + dL/dw + loss
+            float v[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                float x = 0.f;
+                if (e < NC) x = acc_c[e / M][e % M];
+                else if (RAT && e < NC + N) x = acc_w[e - NC];
+                else if (e == NV - 1) x = loss;
+                v[e] = x;
+            }
+            const float tot = warp_sum16_scatter(v, lane);
+            const int e = (lane >> 1) & 15;
+            if ((lane & 1) == 0) {
+                if (e < NC) {
+                    if (a.grad_ctrl) a.grad_ctrl[c * NC + e] = tot;
+                } else if (RAT && e < NC + N) {
+                    if (a.grad_w) a.grad_w[c * N + (e - NC)] = tot;
+                } else if (e == NV - 1 && a.loss) {
+                    a.loss[c] = a.loss_scale * tot;
+                }
+            }
+            if constexpr (NV > 16) {
+                // values 16.. (at most 16 more here): one butterfly each
+#pragma unroll
+                for (int e2 = 16; e2 < NV; ++e2) {
+                    float x = e2 < NC ? acc_c[e2 / M][e2 % M] : (RAT && e2 < NC + N) ? acc_w[e2 - NC] : loss;
+                    x = warp_sum(x);
+                    if (lane == 0) {
+                        if (e2 < NC) {
+                            if (a.grad_ctrl) a.grad_ctrl[c * NC + e2] = x;
+                        } else if (RAT && e2 < NC + N) {
+                            if (a.grad_w) a.grad_w[c * N + (e2 - NC)] = x;
+                        } else if (a.loss) {
+                            a.loss[c] = a.loss_scale * x;
+                        }
+                    }
+                }
+            }
+            return;
+        }
         const int nc = (d + 1) * dim;
         const int dd = D ? D : d;
 #pragma unroll
