@@ -42,7 +42,7 @@ __host__ __device__ constexpr int grad_pair(int D, bool RAT) { return (D >= 1 &&
 // registers a thread at 256 threads a block)
 __host__ __device__ constexpr int grad_min_blocks(int D, bool RAT)
 {
-    return D == 0 ? 2 : grad_pair(D, RAT) == 1 ? (!RAT && D <= 5 ? 3 : 2) : (!RAT && D <= 3) ? 3 : 2;
+    return D == 0 ? 2 : grad_pair(D, RAT) == 1 ? (!RAT && D <= 5 ? 3 : 2) : (!RAT && D <= 3) ? 4 : 2;
 }
 
 // dL/dt output: none, per-curve array, or shared t summed over curves with
