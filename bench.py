@@ -325,6 +325,8 @@ def run_precision(args, rank, world, local_rank):
             row["fetches_per_s"] = nf * pts_step / (kern_ms * 1e-3)
             row["tex_frac"] = row["fetches_per_s"] / peaks[kind]
             row["tex_peak"] = kind
+            # the step is pack + evaluate; the library's events bracket the evaluation only
+            row["pack_ms"] = r["ms"] / args.steps - kern_ms
         variants[v] = row
     horner = variants["HORNER"]["points_per_s"]
     for v in run_variants:
