@@ -281,6 +281,7 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.surf3);
     if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
     if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
+    if (c->pipe_alt) cudaStreamDestroy(c->pipe_alt);
     for (auto e : c->pipe_ev)
         if (e) cudaEventDestroy(e);
     atlas_free(c->tex.surf2);
@@ -429,25 +430,28 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
         c->tex_used = true;
         return stg.finish(o->sync);
     }
-    auto launch = [&](const CurveArgs& ak) {
+    auto launch = [&](const CurveArgs& ak, cudaStream_t cs) {
         switch (var) {
-        case BEZ_VAR_HORNER: return launch_curve_horner(ak, tm, om, s, h);
-        case BEZ_VAR_HORNER_CENTRED: return launch_curve_horner_centred(ak, tm, om, s, h);
-        case BEZ_VAR_BERNSTEIN: return launch_curve_bernstein(ak, tm, om, s, h);
-        case BEZ_VAR_DECASTELJAU: return launch_curve_decasteljau(ak, tm, om, s, h);
-        case BEZ_VAR_HALF2: return launch_curve_half2(ak, tm, om, s, h);
-        default: return launch_curve_seiler(ak, tm, om, s, h);
+        case BEZ_VAR_HORNER: return launch_curve_horner(ak, tm, om, cs, h);
+        case BEZ_VAR_HORNER_CENTRED: return launch_curve_horner_centred(ak, tm, om, cs, h);
+        case BEZ_VAR_BERNSTEIN: return launch_curve_bernstein(ak, tm, om, cs, h);
+        case BEZ_VAR_DECASTELJAU: return launch_curve_decasteljau(ak, tm, om, cs, h);
+        case BEZ_VAR_HALF2: return launch_curve_half2(ak, tm, om, cs, h);
+        default: return launch_curve_seiler(ak, tm, om, cs, h);
         }
     };
     if (!pipe) {
-        r = launch(a);
+        r = launch(a, s);
         if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
         return stg.finish(o->sync);
     }
-    // chunk k: copy in on pipe_in, evaluate on s, copy out on pipe_out
+    // chunk k: copy in on pipe_in, evaluate on s (even k) or pipe_alt (odd k),
+    // copy out on pipe_out.  Alternating the evaluation streams lets chunk k + 1
+    // take the SMs that chunk k's last wave leaves idle.
     if (!c->pipe_in) {
         BEZ_CUDA(cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking), "cudaStreamCreate");
         BEZ_CUDA(cudaStreamCreateWithFlags(&c->pipe_out, cudaStreamNonBlocking), "cudaStreamCreate");
+        BEZ_CUDA(cudaStreamCreateWithFlags(&c->pipe_alt, cudaStreamNonBlocking), "cudaStreamCreate");
         for (auto& e : c->pipe_ev) BEZ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
     }
     const int K = (int)std::min<int64_t>(kPipeChunks, n_curves / kPipeMinCurves);
@@ -455,6 +459,7 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     BEZ_CUDA(cudaEventRecord(ev[0], s), "cudaEventRecord");  // earlier work on s (e.g. the staged t) comes first
     BEZ_CUDA(cudaStreamWaitEvent(c->pipe_in, ev[0], 0), "cudaStreamWaitEvent");
     BEZ_CUDA(cudaStreamWaitEvent(c->pipe_out, ev[0], 0), "cudaStreamWaitEvent");
+    BEZ_CUDA(cudaStreamWaitEvent(c->pipe_alt, ev[0], 0), "cudaStreamWaitEvent");
     const char* hin = static_cast<const char*>(ctrl);
     char* hout = reinterpret_cast<char*>(out);
     char* din = static_cast<char*>(c->stage[0].p);
@@ -464,15 +469,16 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
         BEZ_CUDA(cudaMemcpyAsync(din + c0 * ctrl_per, hin + c0 * ctrl_per, nk * ctrl_per, cudaMemcpyHostToDevice,
                                  c->pipe_in), "copy input chunk to device");
         BEZ_CUDA(cudaEventRecord(ev[1 + k], c->pipe_in), "cudaEventRecord");
-        BEZ_CUDA(cudaStreamWaitEvent(s, ev[1 + k], 0), "cudaStreamWaitEvent");
+        cudaStream_t cs = (k & 1) ? c->pipe_alt : s;
+        BEZ_CUDA(cudaStreamWaitEvent(cs, ev[1 + k], 0), "cudaStreamWaitEvent");
         CurveArgs ak = a;
         ak.ctrl = din + c0 * ctrl_per;
         ak.out = reinterpret_cast<float*>(dout + c0 * out_per);
         ak.n_curves = nk;
         ak.c_base = c0;
-        r = launch(ak);
+        r = launch(ak, cs);
         if (r.err != cudaSuccess) return cuda_fail(r.err, "curve evaluator launch");
-        BEZ_CUDA(cudaEventRecord(ev[1 + kPipeChunks + k], s), "cudaEventRecord");
+        BEZ_CUDA(cudaEventRecord(ev[1 + kPipeChunks + k], cs), "cudaEventRecord");
         BEZ_CUDA(cudaStreamWaitEvent(c->pipe_out, ev[1 + kPipeChunks + k], 0), "cudaStreamWaitEvent");
         BEZ_CUDA(cudaMemcpyAsync(hout + c0 * out_per, dout + c0 * out_per, nk * out_per, cudaMemcpyDeviceToHost,
                                  c->pipe_out), "copy output chunk to host");

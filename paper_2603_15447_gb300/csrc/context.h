@@ -32,6 +32,7 @@ struct bez_ctx_s {
     bez::TexState tex;
     // pipelined host calls: chunk copies in and out on their own streams
     cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+    cudaStream_t pipe_alt = nullptr;  // odd chunks evaluate here, so a chunk's tail overlaps the next chunk
     cudaEvent_t pipe_ev[2 * 8 + 2] = {};  // start, per chunk in / done (8 chunks at most), end
     cudaEvent_t tex_done = nullptr;  // last use of the texture atlases
     bool tex_used = false;
