@@ -4,7 +4,9 @@
 // and then the isoline cubic in v).
 //
 // Separable contraction, one block per patch (grid-stride; bicubic 3D
-// patches on grids of up to 64 rows take one warp per patch):
+// patches on grids of up to 64 rows take one warp per patch, and tricubic
+// scalar volumes one warp per volume: k_volume_tricubic1_warp in
+// tensor_common.cuh, shared with the texture volumes):
 //   surface  X[a][j] = sum_i Bu[a][i] C[i][j]          (isoline control points)
 //            P[a][b] = sum_j X[a][j] Bv[b][j]
 //   volume   Y[a][j][l] = sum_i Bu[a][i] C[i][j][l]
