@@ -269,7 +269,7 @@ def run_precision(args, rank, world, local_rank):
                         "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
     clock_summary = clocks.summary()
 
-    # chain part of the workload: register de Casteljau vs zig-zag texture
+    # chain part of the workload: register de Casteljau and centred Horner vs zig-zag texture
     chains = None
     if not args.skip_chains:
         cctrl_np, _ = synth.chains(n_chains=args.n_chains, n_t=1)
@@ -277,7 +277,7 @@ def run_precision(args, rank, world, local_rank):
         cout = torch.empty(args.n_chains, dtype=torch.float32, device=dev)
         chains = {}
         csteps = max(args.steps // 4, 3)
-        for v in ("DECASTELJAU", "TEX_DECASTELJAU"):
+        for v in ("DECASTELJAU", "HORNER_CENTRED", "TEX_DECASTELJAU"):
             def cstep(v=v):
                 bez.bez_eval_piecewise(cctrl, 64, 2, None, n_t=args.chain_t, variant=bez.Variant[v],
                                        out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed,

@@ -6,7 +6,11 @@
 // used for ties: an integer t starts the later segment).  One warp owns a
 // chain, stages its control points in shared memory, and evaluates each
 // sample with the per-curve evaluators of curve_eval.cuh (setup per sample,
-// since consecutive samples may fall in different segments).
+// since consecutive samples may fall in different segments).  Centred Horner
+// on quadratic and cubic 3D chains stages the segments' power coefficients
+// about tau = 1/2 instead (one conversion per segment, not per sample), one
+// float4 per coefficient, so a sample reads d + 1 vectors and runs d FMA per
+// coordinate.
 #pragma once
 
 #include "curve_eval.cuh"
@@ -33,23 +37,52 @@ __device__ __forceinline__ int chain_segment(float t, int n_seg)
     return k > n_seg - 1 ? n_seg - 1 : k;
 }
 
+// segments staged as centred power coefficients (float4 each)
+template <int VAR, int D, int DIM>
+__host__ __device__ constexpr bool chain_coef() { return VAR == VAR_HORNER_CENTRED && (D == 2 || D == 3) && DIM == 3; }
+
+// shared floats per warp for the staged chain (control points or coefficients)
+template <int VAR, int D, int DIM>
+__host__ __device__ inline int chain_stage_floats(int n_seg, int degree)
+{
+    return chain_coef<VAR, D, DIM>() ? n_seg * (D + 1) * 4 : (n_seg * degree + 1) * DIM;
+}
+
 template <int VAR, int D, int DIM, int TM, int OM>
 __global__ void __launch_bounds__(kWarps * 32) k_chain(const CurveArgs a)
 {
     using E = typename Pick<VAR, D, DIM>::type;
     constexpr int N = E::N;
+    constexpr bool COEF = chain_coef<VAR, D, DIM>();
     extern __shared__ float s_dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int deg = Deg<D>::get(a.degree);
     const int n_pts = a.n_seg * deg + 1;
     const int per = n_pts * DIM;
-    float* my = s_dyn + wib * per;
-    float* stage = s_dyn + kWarps * per + wib * 32 * DIM;
+    const int held = chain_stage_floats<VAR, D, DIM>(a.n_seg, deg);
+    float* my = s_dyn + wib * held;
+    float* stage = s_dyn + kWarps * held + wib * 32 * DIM;
     const int64_t n_warps = (int64_t)gridDim.x * kWarps;
 
     for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
-        for (int i = lane; i < per; i += 32) my[i] = load_elem(a.ctrl, a.dtype, c * per + i);
+        if constexpr (COEF) {
+            // lane per segment: its centred power coefficients a_m, m = 0..D
+            float4* my4 = reinterpret_cast<float4*>(my);
+            for (int sg = lane; sg < a.n_seg; sg += 32) {
+                float b[N][DIM];
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int q = 0; q < DIM; ++q) b[i][q] = load_elem(a.ctrl, a.dtype, c * per + (sg * D + i) * DIM + q);
+                E e;
+                e.setup(b, D);
+#pragma unroll
+                for (int m = 0; m < N; ++m) my4[sg * N + m] = make_float4(e.a[m][0], e.a[m][1], e.a[m][2], 0.f);
+            }
+        } else {
+            for (int i = lane; i < per; i += 32) my[i] = load_elem(a.ctrl, a.dtype, c * per + i);
+        }
         __syncwarp();
         const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
         const int n_t = a.n_t;
@@ -57,15 +90,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain(const CurveArgs a)
             const float t = chain_param<TM>(a, c, j, kc);
             const int k = chain_segment(t, a.n_seg);
             const float tau = t - (float)k;
-            float b[N][DIM];
-            const float* src = my + k * deg * DIM;
+            if constexpr (COEF) {
+                const float4* sa = reinterpret_cast<const float4*>(my) + k * N;
+                const float u = tau - 0.5f;
+                float4 acc = sa[N - 1];
 #pragma unroll
-            for (int i = 0; i < N; ++i)
+                for (int m = N - 2; m >= 0; --m) {
+                    const float4 am = sa[m];
+                    acc = make_float4(fmaf(acc.x, u, am.x), fmaf(acc.y, u, am.y), fmaf(acc.z, u, am.z), 0.f);
+                }
+                P[0] = acc.x;
+                P[1] = acc.y;
+                P[2] = acc.z;
+            } else {
+                float b[N][DIM];
+                const float* src = my + k * deg * DIM;
 #pragma unroll
-                for (int q = 0; q < DIM; ++q) b[i][q] = (i <= deg) ? src[i * DIM + q] : 0.f;
-            E e;
-            e.setup(b, deg);
-            e.eval(tau, P);
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int q = 0; q < DIM; ++q) b[i][q] = (i <= deg) ? src[i * DIM + q] : 0.f;
+                E e;
+                e.setup(b, deg);
+                e.eval(tau, P);
+            }
         };
         if (OM == OM_POINTS) {
             for (int j0 = 0; j0 < n_t; j0 += 32) {
@@ -121,8 +168,8 @@ template <int VAR, int D, int DIM, int TM, int OM>
 LaunchResult launch_chain_one(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h)
 {
     auto kern = k_chain<VAR, D, DIM, TM, OM>;
-    const int per = (a.n_seg * a.degree + 1) * a.dim;
-    const size_t smem = (size_t)kWarps * (per + 32 * DIM) * sizeof(float);
+    const int held = chain_stage_floats<VAR, D, DIM>(a.n_seg, a.degree);
+    const size_t smem = (size_t)kWarps * (held + 32 * DIM) * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return {0, e};

@@ -151,7 +151,7 @@ def test_zigzag_modes_dims_half():
     assert np.all(err <= zigzag_bound(stored, texel_eps=2.0 ** -11))
 
 
-@pytest.mark.parametrize("variant", ["DECASTELJAU", "TEX_DECASTELJAU"])
+@pytest.mark.parametrize("variant", ["DECASTELJAU", "HORNER_CENTRED", "TEX_DECASTELJAU"])
 def test_chain_polyline_length_hash(variant):
     torch = need_gpu()
     rng = np.random.default_rng(50)
@@ -162,7 +162,7 @@ def test_chain_polyline_length_hash(variant):
     th = (np.float32(n_seg) * oracle.hash_t(20260316, 12, 0, n, n_t).astype(np.float32)).astype(np.float32)
     pts = oracle.chain(ctrl, n_seg, 2, th)
     L = oracle.polyline_length(pts)
-    if variant == "DECASTELJAU":
+    if variant != "TEX_DECASTELJAU":
         diag = np.maximum(np.linalg.norm(pts.max(axis=1) - pts.min(axis=1), axis=-1), 2.0 ** -4)
         e = FP32_BAR * diag
     else:
