@@ -47,22 +47,20 @@ constexpr int kItemsPerWarp = 4;  // static schedule: items per warp of a block
 // then rounded once to FP32, at FP32 instruction rates (GB300 runs FP64 at a
 // small fraction of FP32).
 template <int P>
-__device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s, int q, int comps,
-                                           const bez_curve_desc& dsc)
+__device__ __forceinline__ void setup_comp(const BatchArgs& a, const SpanRec& r, int q, int comps)
 {
-    const bool spline = dsc.type != BEZ_CURVE_BEZIER;
-    const bool rat = dsc.type == BEZ_CURVE_NURBS;
+    const bool spline = r.type != BEZ_CURVE_BEZIER;
+    const bool rat = r.type == BEZ_CURVE_NURBS;
     const int dim = a.dim;
-    const float* ctrl = a.ctrl_pool + dsc.ctrl_off;
-    const float* wts = rat ? a.weight_pool + dsc.weight_off : nullptr;
+    const float* ctrl = a.ctrl_pool + r.ctrl;
+    const float* wts = rat ? a.weight_pool + r.weight : nullptr;
     float xh[P + 1], xl[P + 1];  // X_j = xh_j + xl_j exactly
 #pragma unroll
     for (int i = 0; i <= P; ++i) {
-        const int g = s + i;
         if (rat) {
-            const float w = __ldg(wts + g);
+            const float w = __ldg(wts + i);
             if (q < dim) {
-                const float v = __ldg(ctrl + (int64_t)g * dim + q);
+                const float v = __ldg(ctrl + (int64_t)i * dim + q);
                 xh[i] = __fmul_rn(w, v);
                 xl[i] = fmaf(w, v, -xh[i]);
             } else {
@@ -70,18 +68,18 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s,
                 xl[i] = 0.f;
             }
         } else {
-            xh[i] = __ldg(ctrl + (int64_t)g * dim + q);
+            xh[i] = __ldg(ctrl + (int64_t)i * dim + q);
             xl[i] = 0.f;
         }
     }
-    float* dst = a.span_pool + a.span_off[c] + (int64_t)s * kSpanStride(P, comps);
+    float* dst = a.span_pool + r.dst;
     if (!spline && a.repr == 0) {
 #pragma unroll
         for (int i = 0; i <= P; ++i) dst[i * comps + q] = xh[i];
         return;
     }
     constexpr int S = kOpRowStride(P);
-    const float2* M = a.op_pool + (spline ? a.span_ops[a.op_off[c] + s] : a.tpow_off[P]);
+    const float2* M = a.op_pool + (spline ? r.op : a.tpow_off[P]);
 #pragma unroll
     for (int i = 0; i <= P; ++i) {
         float sh = 0.f, corr = 0.f;
@@ -110,28 +108,45 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, int64_t c, int s,
     }
 }
 
-// Span extraction, one thread per (curve, span, component).
+__device__ __forceinline__ SpanRec load_span_rec(const SpanRec* p)
+{
+    // three 16-byte loads, shared by the span's component threads through L1
+    const int4* src = reinterpret_cast<const int4*>(p);
+    const int4 x = __ldg(src), y = __ldg(src + 1), z = __ldg(src + 2);
+    auto i64 = [](int lo, int hi) { return (int64_t)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo); };
+    SpanRec r;
+    r.ctrl = i64(x.x, x.y);
+    r.weight = i64(x.z, x.w);
+    r.dst = i64(y.x, y.y);
+    r.op = i64(y.z, y.w);
+    r.degree = z.x;
+    r.type = z.y;
+    r.reserved = 0;
+    return r;
+}
+
+// Span extraction, one thread per (span, component).  Each thread reads its
+// span's record and then, independently of each other, the control points
+// (and weights) and the operator rows.
 __global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a)
 {
     const int per = a.dim + 1;  // component slots per span (dim + 1 for homogeneous NURBS)
-    const int64_t total = a.n_span_tab * per;
+    const int64_t total = a.n_span_rec * per;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
         const int64_t sp = idx / per;
         const int q = (int)(idx - sp * per);
-        const int2 cs = a.span_tab[sp];
-        const int64_t c = cs.x;
-        const bez_curve_desc dsc = a.desc[c];
-        const int comps = dsc.type == BEZ_CURVE_NURBS ? a.dim + 1 : a.dim;
+        const SpanRec r = load_span_rec(a.span_rec + sp);
+        const int comps = r.type == BEZ_CURVE_NURBS ? a.dim + 1 : a.dim;
         if (q >= comps) continue;
-        switch (dsc.degree) {
-        case 1: setup_comp<1>(a, c, cs.y, q, comps, dsc); break;
-        case 2: setup_comp<2>(a, c, cs.y, q, comps, dsc); break;
-        case 3: setup_comp<3>(a, c, cs.y, q, comps, dsc); break;
-        case 4: setup_comp<4>(a, c, cs.y, q, comps, dsc); break;
-        case 5: setup_comp<5>(a, c, cs.y, q, comps, dsc); break;
-        case 6: setup_comp<6>(a, c, cs.y, q, comps, dsc); break;
-        default: setup_comp<7>(a, c, cs.y, q, comps, dsc); break;
+        switch (r.degree) {
+        case 1: setup_comp<1>(a, r, q, comps); break;
+        case 2: setup_comp<2>(a, r, q, comps); break;
+        case 3: setup_comp<3>(a, r, q, comps); break;
+        case 4: setup_comp<4>(a, r, q, comps); break;
+        case 5: setup_comp<5>(a, r, q, comps); break;
+        case 6: setup_comp<6>(a, r, q, comps); break;
+        default: setup_comp<7>(a, r, q, comps); break;
         }
     }
 }
@@ -433,7 +448,7 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
     *launches = 0;
     cudaError_t e;
     if (with_setup && a.n_curves > 0) {
-        const int grid = (int)std::min<int64_t>((a.n_span_tab * (a.dim + 1) + 255) / 256, (int64_t)sm_count * 16);
+        const int grid = (int)std::min<int64_t>((a.n_span_rec * (a.dim + 1) + 255) / 256, (int64_t)sm_count * 16);
         h.count(h.self);
         k_batch_setup<<<grid > 0 ? grid : 1, 256, 0, s>>>(a);
         ++*launches;

@@ -98,12 +98,9 @@ struct bez_batch_s {
     BatchArgs a{};
     std::vector<bez_curve_desc> hdesc;
     bez_curve_desc* d_desc = nullptr;
-    int64_t* d_span_off = nullptr;
     float2* d_ops = nullptr;    // span operators M (Bezier-point representation)
     float2* d_ops_c = nullptr;  // T_p M (centred power-basis representation)
-    int64_t* d_span_ops = nullptr;
-    int64_t* d_op_off = nullptr;
-    int2* d_span_tab = nullptr;
+    SpanRec* d_span_rec = nullptr;
     bool spans_ready = false;
     BatchItem* d_items = nullptr;
     size_t items_cap = 0;
@@ -298,12 +295,9 @@ void free_batch(bez_batch b)
         cudaEventDestroy(b->streams.fork);
     }
     cudaFree(b->d_desc);
-    cudaFree(b->d_span_off);
     cudaFree(b->d_ops);
     cudaFree(b->d_ops_c);
-    cudaFree(b->d_span_ops);
-    cudaFree(b->d_op_off);
-    cudaFree(b->d_span_tab);
+    cudaFree(b->d_span_rec);
     cudaFree(b->d_items);
     cudaFree(b->d_spans);
     cudaFree(b->d_counter);
@@ -412,7 +406,6 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
         if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
     };
     alloc((void**)&b->d_desc, (size_t)n_curves * sizeof(bez_curve_desc));
-    alloc((void**)&b->d_span_off, (size_t)n_curves * sizeof(int64_t));
     // Centred representation: the Bezier -> power-basis-about-1/2 map is a
     // fixed matrix T_p per degree, so each span operator M becomes T_p M (FP64
     // here) and a Bezier curve's span uses T_p itself; the device then forms
@@ -454,36 +447,39 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     const std::vector<float2> ops2 = split(ops), ops2c = split(ops_c);
     alloc((void**)&b->d_ops, ops2.size() * sizeof(float2));
     alloc((void**)&b->d_ops_c, ops2c.size() * sizeof(float2));
-    alloc((void**)&b->d_span_ops, span_ops.size() * sizeof(int64_t));
-    alloc((void**)&b->d_op_off, (size_t)n_curves * sizeof(int64_t));
     alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
     alloc(&b->d_counter, kBatchClasses * sizeof(unsigned long long));
-    // (curve, span) of every span, grouped by (degree, type) so that the
-    // warps of the setup kernel run one degree's code at a time
-    std::vector<int2> span_tab;
+    // every span with its offsets resolved, grouped by (degree, type) so that
+    // the warps of the setup kernel run one degree's code at a time
+    std::vector<SpanRec> span_rec;
     for (int deg = 1; deg <= 7; ++deg)
         for (int ty = BEZ_CURVE_BEZIER; ty <= BEZ_CURVE_NURBS; ++ty)
             for (int64_t i = 0; i < n_curves; ++i) {
                 const bez_curve_desc& d = b->hdesc[(size_t)i];
                 if (d.degree != deg || d.type != ty) continue;
-                const int n_spans = d.type == BEZ_CURVE_BEZIER ? 1 : d.n_ctrl - d.degree;
-                for (int s = 0; s < n_spans; ++s) span_tab.push_back(make_int2((int)i, s));
+                const bool spline = d.type != BEZ_CURVE_BEZIER, rat = d.type == BEZ_CURVE_NURBS;
+                const int comps = rat ? dim + 1 : dim;
+                const int n_spans = spline ? d.n_ctrl - d.degree : 1;
+                for (int s = 0; s < n_spans; ++s) {
+                    SpanRec r{};
+                    r.ctrl = d.ctrl_off + (int64_t)s * dim;
+                    r.weight = rat ? d.weight_off + s : -1;
+                    r.dst = span_off[(size_t)i] + (int64_t)s * kSpanStride(d.degree, comps);
+                    r.op = spline ? span_ops[(size_t)(op_off[(size_t)i] + s)] : -1;
+                    r.degree = d.degree;
+                    r.type = d.type;
+                    span_rec.push_back(r);
+                }
             }
-    alloc((void**)&b->d_span_tab, span_tab.size() * sizeof(int2));
-    if (e == cudaSuccess && !span_tab.empty())
-        e = cudaMemcpy(b->d_span_tab, span_tab.data(), span_tab.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    alloc((void**)&b->d_span_rec, span_rec.size() * sizeof(SpanRec));
+    if (e == cudaSuccess && !span_rec.empty())
+        e = cudaMemcpy(b->d_span_rec, span_rec.data(), span_rec.size() * sizeof(SpanRec), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_curves > 0)
         e = cudaMemcpy(b->d_desc, b->hdesc.data(), (size_t)n_curves * sizeof(bez_curve_desc), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && n_curves > 0)
-        e = cudaMemcpy(b->d_span_off, span_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ops.empty())
         e = cudaMemcpy(b->d_ops, ops2.data(), ops2.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ops2c.empty())
         e = cudaMemcpy(b->d_ops_c, ops2c.data(), ops2c.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !span_ops.empty())
-        e = cudaMemcpy(b->d_span_ops, span_ops.data(), span_ops.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && n_curves > 0)
-        e = cudaMemcpy(b->d_op_off, op_off.data(), (size_t)n_curves * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "batch buffers");
@@ -519,12 +515,9 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     a.weight_pool = weight_pool;
     a.out_pool = out_pool;
     a.span_pool = b->d_spans;
-    a.span_off = b->d_span_off;
     a.op_pool = b->d_ops;
-    a.span_ops = b->d_span_ops;
-    a.op_off = b->d_op_off;
-    a.span_tab = b->d_span_tab;
-    a.n_span_tab = (int64_t)span_tab.size();
+    a.span_rec = b->d_span_rec;
+    a.n_span_rec = (int64_t)span_rec.size();
     a.repr = -1;  // set by apply_shape, which then runs the setup
     a.counter = b->d_counter;
     b->setup_each = bo ? bo->setup_each_launch != 0 : true;

@@ -197,6 +197,19 @@ struct BatchStreams {
     cudaEvent_t join[kBatchSideStreams];
 };
 
+// One span of a batch as the setup kernel reads it, with every offset
+// resolved on the host so that its loads depend on this record alone.
+struct alignas(16) SpanRec {
+    int64_t ctrl;    // floats into ctrl_pool: the span's first control point
+    int64_t weight;  // floats into weight_pool: its first weight (NURBS), else -1
+    int64_t dst;     // floats into span_pool: where the span is written
+    int64_t op;      // entry of its extraction operator in op_pool (splines), else -1
+    int32_t degree;
+    int32_t type;    // bez_curve_type
+    int64_t reserved;
+};
+static_assert(sizeof(SpanRec) == 48, "SpanRec is read as three 16-byte loads");
+
 struct BatchArgs {
     const bez_curve_desc* desc;  // device copy
     int64_t n_curves;
@@ -205,14 +218,11 @@ struct BatchArgs {
     const float* weight_pool;
     float* out_pool;
     float* span_pool;            // every curve's spans in the evaluation representation
-    const int64_t* span_off;     // per curve, floats into span_pool
     const float2* op_pool;       // span operators M (repr 0) or T_p M (repr 1), each entry hi + lo (FP64 -> 2 x FP32),
                                  // row-major with rows padded to kOpRowStride(p) entries
-    const int64_t* op_off;       // per curve, index of its first span in span_ops (splines only)
-    const int64_t* span_ops;     // per spline span: offset of its operator matrix in op_pool
     int64_t tpow_off[8];         // offset of T_p (Bezier -> centred power basis) in the centred op_pool
-    const int2* span_tab;        // (curve, span) of every span: one setup thread each
-    int64_t n_span_tab;
+    const SpanRec* span_rec;     // every span, offsets resolved: one setup thread per component
+    int64_t n_span_rec;
     int32_t repr;                // 0 Bezier points (de Casteljau), 1 power basis about 1/2 (Horner)
     const BatchItem* items;      // work items, sorted by item class
     int64_t n_items;
