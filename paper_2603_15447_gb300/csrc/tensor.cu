@@ -317,6 +317,7 @@ static TensorArgs to_args(const TensorLaunch& t)
     a.nv = t.nv;
     a.nw = t.nw;
     a.out = t.out;
+    a.vparts = 1;
     return a;
 }
 
@@ -324,7 +325,7 @@ size_t tensor_product_smem(const TensorLaunch& t) { return tensor_smem_bytes(to_
 
 LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const LaunchHooks& h)
 {
-    const TensorArgs a = to_args(t);
+    TensorArgs a = to_args(t);
     const void* kern;
     size_t smem = 0;
     int threads = kTensorThreads;
@@ -340,7 +341,8 @@ LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const 
     } else if (tricubic1) {
         kern = (const void*)k_volume_tricubic1_warp<VOL_U_CORES>;
         threads = kSurfWarps * 32;
-        work = (a.n + kSurfWarps - 1) / kSurfWarps;
+        a.vparts = volume_parts(a.n, a.nu, h.sm_count);
+        work = (a.n * a.vparts + kSurfWarps - 1) / kSurfWarps;
     } else if (bicubic3) {
         kern = (const void*)k_surface_bicubic3;
     } else {

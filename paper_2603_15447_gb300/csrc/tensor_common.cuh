@@ -20,7 +20,18 @@ struct TensorArgs {  // kernel-side copy of TensorLaunch
     int32_t dim;
     int32_t nu, nv, nw;
     float* out;
+    int32_t vparts;  // tricubic volume kernel: warps per volume, each a range of u rows (0 = 1)
 };
+
+// Warps per volume for the tricubic volume kernel: enough (volume, row
+// range) units to fill the SMs about twice over, at most 4 and at most nu.
+inline int volume_parts(int64_t n, int nu, int sm_count)
+{
+    const int64_t target = (int64_t)sm_count * 2 * 32;  // two rounds of 32 resident warps per SM
+    int parts = 1;
+    while (parts < 4 && parts < nu && n * parts < target) parts *= 2;
+    return parts;
+}
 
 // Bernstein table B[a][i] for n grid values and degree d, via de Casteljau
 // on unit vectors (each entry is a product of lerp weights, exact at ends).
@@ -100,17 +111,22 @@ __global__ void __launch_bounds__(kSurfWarps * 32) k_volume_tricubic1_warp(const
     const int slab4 = nv * q4;            // float4 per u slab
     const int64_t pts = (int64_t)nu * nv * nw;
     const int64_t stride = (int64_t)gridDim.x * kSurfWarps;
+    const int parts = a.vparts > 0 ? a.vparts : 1;
     float* cw = reinterpret_cast<float*>(s_c4[w]);
-    for (int64_t p = (int64_t)blockIdx.x * kSurfWarps + w; p < a.n; p += stride) {
-        __syncwarp();  // the previous volume is done with s_c4 and s_y
+    // unit g: rows [r0, r1) of volume p = g / parts
+    for (int64_t g = (int64_t)blockIdx.x * kSurfWarps + w; g < a.n * parts; g += stride) {
+        const int64_t p = g / parts;
+        const int part = (int)(g - p * parts);
+        const int r0 = nu * part / parts, r1 = nu * (part + 1) / parts;
+        __syncwarp();  // the previous unit is done with s_c4 and s_y
         if (USTAGE == VOL_U_CORES) {
             cw[lane] = load_elem(a.ctrl, a.dtype, p * 64 + lane);
             cw[32 + lane] = load_elem(a.ctrl, a.dtype, p * 64 + 32 + lane);
             __syncwarp();
         }
-        // Y[a][j] (a float4 over l): entry e = 4 a + j
-        for (int e = lane; e < nu * 4; e += 32) {
-            const int ai = e >> 2, j = e & 3;
+        // Y[a][j] (a float4 over l) for rows a of the unit: entry e = 4 (a - r0) + j
+        for (int e = lane; e < (r1 - r0) * 4; e += 32) {
+            const int ai = r0 + (e >> 2), j = e & 3;
             float4 y;
             if (USTAGE == VOL_U_CORES) {
                 const float4 bu = s_bu[ai];
@@ -132,8 +148,9 @@ __global__ void __launch_bounds__(kSurfWarps * 32) k_volume_tricubic1_warp(const
         }
         __syncwarp();
         float4* out = reinterpret_cast<float4*>(a.out + p * pts);
-        for (int ai = 0; ai < nu; ++ai) {
-            const float4 y0 = s_y[w][4 * ai], y1 = s_y[w][4 * ai + 1], y2 = s_y[w][4 * ai + 2], y3 = s_y[w][4 * ai + 3];
+        for (int ai = r0; ai < r1; ++ai) {
+            const float4* ya = s_y[w] + 4 * (ai - r0);
+            const float4 y0 = ya[0], y1 = ya[1], y2 = ya[2], y3 = ya[3];
             float4* o = out + (int64_t)ai * slab4;
             for (int f = lane; f < slab4; f += 32) {
                 const int b = f / q4, c0 = (f - b * q4) * 4;

@@ -220,7 +220,9 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_form
                : a.dim == 2 ? (const void*)k_surface_tex<2, false>
                : a.dim == 3 ? (const void*)k_surface_tex<3, false>
                             : (const void*)k_surface_tex<4, false>;
-    const int grid = persistent_grid(kern, kSurfWarps * 32, 0, h.sm_count, (a.n + kSurfWarps - 1) / kSurfWarps);
+    a.vparts = vol ? volume_parts(a.n, a.nu, h.sm_count) : 1;
+    const int grid = persistent_grid(kern, kSurfWarps * 32, 0, h.sm_count,
+                                     (a.n * a.vparts + kSurfWarps - 1) / kSurfWarps);
     SurfTexArgs sa{at.tex, tw, rs};
     void* args[] = {(void*)&a, (void*)&sa};
     h.count(h.self);
