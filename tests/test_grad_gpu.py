@@ -227,3 +227,23 @@ def test_fused_step_matches_backward_with_kernel_residual():
     assert torch.allclose(loss, 0.5 * ((pts - y) ** 2).sum(dim=(1, 2)), rtol=1e-5, atol=1e-6)
     assert torch.allclose(gc, gc2, rtol=1e-4, atol=1e-5)
     assert torch.allclose(gt, gt2, rtol=1e-4, atol=1e-5)
+
+
+def test_fused_step_host_arrays_match_device():
+    # host (NumPy) arguments are staged through the context's buffers; the
+    # results equal the device-array call bit for bit
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(78)
+    B, n_t, d = 37, 70, 3
+    ctrl = rng.uniform(-1, 1, (B, d + 1, 3)).astype(np.float32)
+    w = rng.uniform(0.5, 2, (B, d + 1)).astype(np.float32)
+    t = rng.uniform(0, 1, (B, n_t)).astype(np.float32)
+    y = rng.uniform(-1, 1, (B, n_t, 3)).astype(np.float32)
+    host = bez.bez_mse_grad(ctrl, t, y, weights=w, loss_scale=0.25, sync=True)
+    dev = bez.bez_mse_grad(_cuda(torch, ctrl), _cuda(torch, t), _cuda(torch, y), weights=_cuda(torch, w),
+                           loss_scale=0.25)
+    torch.cuda.synchronize()
+    for h, g in zip(host, dev):
+        assert isinstance(h, np.ndarray)
+        np.testing.assert_array_equal(h, g.cpu().numpy())
