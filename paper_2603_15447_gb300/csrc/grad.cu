@@ -17,7 +17,8 @@
 // One warp per curve; lanes take samples j = lane + 32 m (coalesced reads of
 // t and g), two at a time (j and j + 32: independent arithmetic to
 // interleave), keep per-lane partial sums of the per-curve gradients in
-// registers, and combine them with a butterfly of shuffles.  Per-sample dt is
+// registers, and combine them at the end of the curve (one 16-value
+// reduce-scatter for fixed degrees, butterflies otherwise).  Per-sample dt is
 // written directly (per-curve t) or summed over curves (shared t) in shared
 // memory and then with one global atomic per block and parameter.  The next
 // pair's loads are issued before the current pair's arithmetic, and the
@@ -55,7 +56,6 @@ template <int D, int DIM, bool RAT>
 struct GradCurve {
     static constexpr int N = Deg<D>::N;
     static constexpr int M = DIM ? DIM : kGradMaxDim;
-    static constexpr int kU = D ? N : 1;  // runtime degree: loops, arrays in local memory
     int d, dim;
     float P[N][M], w[N], dq[N][M], dw[N];
     float acc_c[N][M], acc_w[N], loss;
