@@ -192,7 +192,8 @@ def test_fused_squared_error_step(d, rational, shared):
     assert lo.shape == (B,)
     assert np.all(np.abs(lo - loss_ref)
                   <= s * (2 * np.abs(r).sum(axis=(1, 2)) * eps_c + n_t * dim * eps_c ** 2) + k * 2 * loss_ref + 1e-30)
-    assert np.all(np.abs(gc.cpu().numpy() - rc) <= (n_t * dg)[:, None, None] + k * (ac + n_t * dg[:, None, None]) + 1e-30)
+    dgc = (n_t * dg)[:, None, None]
+    assert np.all(np.abs(gc.cpu().numpy() - rc) <= dgc + k * (ac + dgc) + 1e-30)
     cp = _dmax_over_wmin(ctrl, w) * np.sqrt(dim)
     gmag = np.linalg.norm(g, axis=-1) + np.sqrt(dim) * dg[:, None]             # [B][n_t]
     tol_t = (16 * d + 32) * U * gmag * cp + np.sqrt(dim) * dg[:, None] * cp
@@ -247,3 +248,33 @@ def test_fused_step_host_arrays_match_device():
     for h, g in zip(host, dev):
         assert isinstance(h, np.ndarray)
         np.testing.assert_array_equal(h, g.cpu().numpy())
+
+
+def test_fused_step_edge_sizes_and_errors():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(79)
+    ctrl = _cuda(torch, rng.uniform(-1, 1, (5, 4, 3)).astype(np.float32))
+    # no samples: zero loss and zero gradients
+    empty_t, empty_y = torch.zeros((5, 0), device="cuda"), torch.zeros((5, 0, 3), device="cuda")
+    loss, gc, _, gt = bez.bez_mse_grad(ctrl, empty_t, empty_y, loss_scale=1.0)
+    torch.cuda.synchronize()
+    assert loss.shape == (5,) and float(loss.abs().max()) == 0.0
+    assert float(gc.abs().max()) == 0.0 and gt.numel() == 0
+    # no curves: nothing to do
+    none_t, none_y = torch.zeros((0, 8), device="cuda"), torch.zeros((0, 8, 3), device="cuda")
+    loss, gc, _, _ = bez.bez_mse_grad(ctrl[:0].contiguous(), none_t, none_y)
+    assert loss.numel() == 0 and gc.numel() == 0
+    # a missing target is rejected before any launch
+    import ctypes
+
+    from paper_2603_15447_gb300.bez import Opts, _ptr, context, lib
+    o = Opts(int(bez.Variant.AUTO), 0, int(bez.OutMode.POINTS), int(bez.TMode.PER_CURVE), 0, 0, 1, None, 0, 0)
+    t = torch.zeros((5, 8), device="cuda")
+    gcb = torch.empty((5, 4, 3), device="cuda")
+    L = lib()
+    if not getattr(L, "_mse_ready", False):
+        bez.bez_mse_grad(ctrl, t, torch.zeros((5, 8, 3), device="cuda"))   # sets the argtypes
+    st = L.bez_mse_grad(context(0).handle, _ptr(ctrl), None, 5, 3, 3, _ptr(t), 8, None, ctypes.c_float(1.0), None,
+                        _ptr(gcb), None, None, ctypes.byref(o), None)
+    assert st == int(bez.Status.INVALID_ARG)

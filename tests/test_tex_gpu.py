@@ -370,6 +370,25 @@ def test_texture_tricubic_volume(variant, fmt, levels, nu, nv, nw):
             np.testing.assert_array_equal(got[:, -1, -1, -1, 0], ctrl[:, -1, -1, -1, 0])
 
 
+def test_texture_surface_unorm_from_half_storage():
+    # FP16 control points with unorm16 tiles: the rescale works on the stored
+    # half values, so the bound is the float-tile bound of those values
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(7200)
+    c = torch.from_numpy(rng.uniform(-1, 1, (97, 4, 4, 3)).astype(np.float32)).cuda().half()
+    got = bez.bez_eval_surface(c, 16, 24, variant=bez.Variant.TEX_SEILER,
+                               tex_format=bez.TexFormat.UNORM16).cpu().numpy().astype(np.float64)
+    b = c.float().cpu().numpy().astype(np.float64)
+    ref = oracle.surface(b, 16, 24)
+    d1 = 3 * (b[:, 1] - b[:, 0]) - (b[:, 3] - b[:, 0])
+    d2 = 3 * (b[:, 2] - b[:, 3]) - (b[:, 0] - b[:, 3])
+    tile = np.stack([b[:, 0], b[:, 3], b[:, 0] + d1, b[:, 3] + d2], 1)
+    col_range = (tile.max(axis=1) - tile.min(axis=1)).max(axis=1)
+    tol = (2 * WERR + 0.5 / 65535) * col_range + 8 * U * np.abs(tile).max(axis=(1, 2))
+    assert np.all(np.abs(got - ref) <= tol[:, None, None, :])
+
+
 def test_texture_surface_unsupported():
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
