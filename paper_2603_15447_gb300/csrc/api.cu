@@ -464,8 +464,14 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     char* hout = reinterpret_cast<char*>(out);
     char* din = static_cast<char*>(c->stage[0].p);
     char* dout = static_cast<char*>(c->stage[2].p);
+    // a short first chunk (1/32 of the curves) starts the evaluation early;
+    // the rest is split evenly
+    const int64_t head = n_curves / 32;
+    auto bound = [&](int i) -> int64_t {
+        return i == 0 ? 0 : i == K ? n_curves : head + (n_curves - head) * (i - 1) / (K - 1);
+    };
     for (int k = 0; k < K; ++k) {
-        const int64_t c0 = n_curves * k / K, c1 = n_curves * (k + 1) / K, nk = c1 - c0;
+        const int64_t c0 = bound(k), c1 = bound(k + 1), nk = c1 - c0;
         BEZ_CUDA(cudaMemcpyAsync(din + c0 * ctrl_per, hin + c0 * ctrl_per, nk * ctrl_per, cudaMemcpyHostToDevice,
                                  c->pipe_in), "copy input chunk to device");
         BEZ_CUDA(cudaEventRecord(ev[1 + k], c->pipe_in), "cudaEventRecord");
