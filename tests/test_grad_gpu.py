@@ -69,6 +69,29 @@ def test_adjoint_per_curve_t(d, rational):
     _check(torch, ctrl, t, g, w)
 
 
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("n_t", [4, 132, 260, 512])
+def test_adjoint_low_degrees_and_sample_counts(d, n_t):
+    # integral 3D curves with per-curve t over sample counts that are and are
+    # not multiples of the 64 samples a warp takes per iteration (a partial
+    # last pair); also without dL/dt
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(500 + 10 * d + n_t)
+    B = 77
+    ctrl = rng.uniform(-1, 1, (B, d + 1, 3)).astype(np.float32)
+    t = rng.uniform(0, 1, (B, n_t)).astype(np.float32)
+    t[:, 1] = 1.5                                    # clamped: zero dL/dt
+    g = rng.normal(size=(B, n_t, 3)).astype(np.float32)
+    _check(torch, ctrl, t, g)
+    gc, _, gt = bez.bez_eval_backward(_cuda(torch, ctrl), _cuda(torch, t), _cuda(torch, g), need_t=False)
+    torch.cuda.synchronize()
+    assert gt is None
+    rc, _, _ = oracle.bezier_grad(ctrl, t, g)
+    ac, _, _ = oracle.bezier_grad(ctrl, t, np.abs(g))
+    assert np.all(np.abs(gc.cpu().numpy() - rc) <= (n_t / 32 + 2 * d + 12) * U * ac + 1e-30)
+
+
 @pytest.mark.parametrize("rational", [False, True])
 @pytest.mark.parametrize("dim", [1, 2, 4])
 def test_adjoint_shared_t_and_dims(rational, dim):
