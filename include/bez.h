@@ -53,7 +53,8 @@ typedef enum bez_status {
  * "Polynomial" shader of Sec. 5).  Texture forms: Sec. 2 (de Casteljau
  * tiles), Sec. 4 (Seiler tiles), Fig. 3 (hybrid). */
 typedef enum bez_variant {
-    BEZ_VAR_AUTO = 0,            /* library choice (currently BEZ_VAR_SEILER)           */
+    BEZ_VAR_AUTO = 0,            /* library choice: bez_eval takes HORNER_CENTRED up to  *
+                                  * degree 7, SEILER above; chains, splines: DECASTELJAU */
     BEZ_VAR_HORNER = 1,          /* power basis about t=0, Horner, FP32 (baseline)       */
     BEZ_VAR_HORNER_CENTRED = 2,  /* power basis about t=1/2, Horner                      */
     BEZ_VAR_BERNSTEIN = 3,       /* Bernstein polynomial sum                             */
