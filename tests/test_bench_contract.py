@@ -37,3 +37,23 @@ def test_reference_arm_line_keys_and_types():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_roofline_block_arithmetic():
+    # the roofline object of a bandwidth-bound line: achieved = algorithmic
+    # bytes per launch / launch time, frac = achieved / peak, peak from the
+    # measured copy bandwidth or the stated fallback
+    sys.path.insert(0, ROOT)
+    import bench
+    line = bench._hbm_line("w", 1.0, "points/s", 3, 3, 6.0, 10 ** 9, 0.5, "k", {"extra": 1}, traffic=123.0)
+    r = line["roofline"]
+    assert set(("bound", "achieved", "peak", "unit", "frac", "traffic")) <= set(r)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 123.0
+    assert abs(r["achieved"] - 2000.0) < 1e-9                    # 1e9 B in 0.5 ms
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    peak, note = bench.hbm_peak(bench.load_peaks())
+    assert r["peak"] == peak and ("measured" in note or "fallback" in note)
+    assert bench.hbm_peak(None) == (6800.0, "of fallback (6.8 TB/s)")
+    assert line["extra"] == 1 and line["ms_per_step"] == 2.0 and line["config"] == {"workload": "w"}
+    ops, _ = bench.alu_peak(None)
+    assert ops == 152 * 128 * 2070.0e6
