@@ -59,3 +59,16 @@ def test_create_reports_missing_device_cleanly(libbez):
     st = bez.lib().bez_create(ctypes.byref(h), 0)
     assert st in (bez.Status.CUDA, bez.Status.INVALID_ARG)
     assert not h.value
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no fallback: without libbez.so every call raises instead of computing
+    # anything elsewhere
+    from paper_2603_15447_gb300 import bez
+    monkeypatch.setattr(bez, "_lib", None)
+    monkeypatch.setattr(bez, "LIB_PATH", str(tmp_path / "libbez.so"))
+    with pytest.raises(RuntimeError, match="libbez.so not found"):
+        bez.lib()
+    import numpy as np
+    with pytest.raises(RuntimeError, match="libbez.so not found"):
+        bez.bez_eval(np.zeros((2, 4, 3), np.float32), np.zeros(3, np.float32))
