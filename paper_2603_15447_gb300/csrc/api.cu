@@ -339,8 +339,8 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
         return fail(BEZ_ERR_INVALID_ARG, "hash parameters index curves with 32 bits");
     if (dim < 1 || dim > 4) return fail(BEZ_ERR_INVALID_ARG, "dim %d not in 1..4", dim);
     if (degree < 1) return fail(BEZ_ERR_INVALID_ARG, "degree %d < 1", degree);
-    // AUTO: the fastest register form that meets the FP32 accuracy of the
-    // oracle comparisons up to degree 7 (centred Horner), Seiler above
+    // AUTO: the fastest register form within 1e-6 of the curve's extent up
+    // to degree 7 (centred Horner), Seiler above
     int var = o->variant != BEZ_VAR_AUTO ? o->variant : degree <= 7 ? BEZ_VAR_HORNER_CENTRED : BEZ_VAR_SEILER;
     const bool coissue = var == BEZ_VAR_COISSUE;
     const bool tex = var == BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TEX_SEILER || var == BEZ_VAR_TEX_HYBRID ||
