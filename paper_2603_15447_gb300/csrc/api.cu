@@ -129,6 +129,8 @@ struct Staging {
     };
     std::vector<Out> outs;
 
+    Staging(bez_ctx ctx, cudaStream_t stream) : c(ctx), s(stream) {}
+
     bez_status in(const void* p, size_t bytes, int slot, const void** dev)
     {
         MemKind k = classify(p);
