@@ -127,18 +127,39 @@ __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const Tensor
     const int64_t pts = (int64_t)nu * nv;
     const int64_t stride = (int64_t)gridDim.x * kSurfWarps;
     float* st = s_st[w];
-    for (int64_t p = (int64_t)blockIdx.x * kSurfWarps + w; p < a.n; p += stride) {
-        __syncwarp();  // the previous patch is done with s_x
-        for (int row = lane; row < nu; row += 32) {
-            const float u = nu > 1 ? __fdiv_rn((float)row, (float)(nu - 1)) : 0.f;
+    // the filtered reads of grid row `row` of patch pp, one per coordinate
+    auto fetch = [&](int64_t pp, int row, float4 (&X)[DIM]) {
+        const float u = nu > 1 ? __fdiv_rn((float)row, (float)(nu - 1)) : 0.f;
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) {
-                const int64_t q = p * DIM + k;
-                const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
-                float4 X = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
-                                  : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
-                if (ta.rescale) X = ta_rescale(ta, q, X);
-                s_x[w][row * DIM + k] = X;
+        for (int k = 0; k < DIM; ++k) {
+            const int64_t q = pp * DIM + k;
+            const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
+            X[k] = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
+                          : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
+            if (ta.rescale) X[k] = ta_rescale(ta, q, X[k]);
+        }
+    };
+    // With at most 32 rows a lane owns one row, and the reads of the warp's
+    // next patch are issued before the current patch's sweep, so their
+    // latency overlaps the stores.
+    const bool one_row = nu <= 32;
+    int64_t p = (int64_t)blockIdx.x * kSurfWarps + w;
+    float4 Xn[DIM];
+    if (one_row && p < a.n && lane < nu) fetch(p, lane, Xn);
+    for (; p < a.n; p += stride) {
+        __syncwarp();  // the previous patch is done with s_x
+        if (one_row) {
+            if (lane < nu) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) s_x[w][lane * DIM + k] = Xn[k];
+                if (p + stride < a.n) fetch(p + stride, lane, Xn);
+            }
+        } else {
+            for (int row = lane; row < nu; row += 32) {
+                float4 X[DIM];
+                fetch(p, row, X);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) s_x[w][row * DIM + k] = X[k];
             }
         }
         __syncwarp();
