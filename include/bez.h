@@ -405,8 +405,10 @@ bez_status bez_mse_grad(bez_ctx ctx, const float* ctrl, const float* weights, in
  * every GPU that loads the library holds until the process exits.
  *
  *   weights NULL evaluates B-splines, non-NULL NURBS; other arguments as in
- *   bez_eval_nurbs, with no context.  Every array must be device memory
- *   (host arrays would need staging buffers): BEZ_ERR_INVALID_ARG otherwise.
+ *   bez_eval_nurbs, with no context.  Every array must be device memory of
+ *   the calling thread's current device (or managed memory): host arrays
+ *   would need staging buffers, and the call never switches devices, so
+ *   arrays of another GPU are refused.  BEZ_ERR_INVALID_ARG otherwise.
  *   The batch may need at most 4,194,304 span floats,
  *   n_curves * (n_ctrl - degree) * (degree + 1) * (dim, or dim+1 for NURBS);
  *   larger batches are rejected with BEZ_ERR_INVALID_ARG.
@@ -415,7 +417,8 @@ bez_status bez_mse_grad(bez_ctx ctx, const float* ctrl, const float* weights, in
  * device current; make it before any stream capture.  All calls share the
  * array and each overwrites it, so calls that may overlap on the GPU
  * (different streams without ordering between them) race.  Errors are
- * reported through bez_last_error().
+ * reported through bez_last_error().  Having no context, the call's
+ * launches are not counted or timed by bez_get_stats.
  */
 bez_status bez_eval_spline_noalloc(const float* ctrl, const float* weights, const float* knots, int64_t n_curves,
                                    int n_ctrl, int degree, int dim, const float* t, int64_t n_t, float* out,

@@ -352,11 +352,30 @@ def bez_eval_spline_noalloc(ctrl, degree, t=None, *, weights=None, knots=None, n
     if out is None:
         shape = (n_curves, n_t, dim) if out_mode == OutMode.POINTS else (n_curves,)
         out = _empty_like_location(ctrl, shape)
-    dev = ctrl.device.index if _is_cuda(ctrl) else 0
+    dev = _common_device(ctrl, weights, knots, t, out)
     o = _opts(Variant.AUTO, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync)
-    _check(lib().bez_eval_spline_noalloc(_ptr(ctrl), _ptr(weights), _ptr(knots), n_curves, n_ctrl, degree, dim,
-                                         _ptr(t), n_t, _ptr(out), ctypes.byref(o), _stream_handle(stream, dev)))
+    if dev is None:
+        # host arrays: the library refuses them (it stages nothing)
+        _check(lib().bez_eval_spline_noalloc(_ptr(ctrl), _ptr(weights), _ptr(knots), n_curves, n_ctrl, degree,
+                                             dim, _ptr(t), n_t, _ptr(out), ctypes.byref(o), None))
+        return out
+    torch = _torch()
+    with torch.cuda.device(dev):
+        # the entry point runs on the current device; make it the arrays' one
+        _check(lib().bez_eval_spline_noalloc(_ptr(ctrl), _ptr(weights), _ptr(knots), n_curves, n_ctrl, degree,
+                                             dim, _ptr(t), n_t, _ptr(out), ctypes.byref(o),
+                                             _stream_handle(stream, dev)))
     return out
+
+
+def _common_device(*arrays):
+    """CUDA device index shared by the CUDA tensors among ``arrays`` (None
+    entries skipped), or None when none is on a GPU; raises BezError
+    (INVALID_ARG) when they sit on different GPUs."""
+    devs = {a.device.index for a in arrays if _is_cuda(a)}
+    if len(devs) > 1:
+        raise BezError(Status.INVALID_ARG, f"arrays on different GPUs: {sorted(devs)}")
+    return devs.pop() if devs else None
 
 
 def bez_eval_surface(ctrl, nu, nv, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None,

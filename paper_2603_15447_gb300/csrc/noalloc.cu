@@ -17,6 +17,8 @@
 // array: calls that can overlap on the GPU (different streams without
 // ordering) race on it.  Nothing in it has to start at zero: the setup
 // kernel writes every span slot the evaluator reads, including empty spans.
+// The call has no context, so its launches are not counted or timed by
+// bez_get_stats.
 #include <cstdio>
 #include <mutex>
 
@@ -66,14 +68,19 @@ cudaError_t scratch_for_current_device(float** ptr, int* sm_count)
     return cudaSuccess;
 }
 
-bool is_device_pointer(const void* p)
+// Whether p is device memory that kernels launched on device `dev` may
+// read: memory allocated on `dev` itself, or managed memory.  A pointer to
+// another GPU's memory is refused rather than dereferenced from the wrong
+// device.
+bool is_device_pointer_on(const void* p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -111,14 +118,21 @@ extern "C" bez_status bez_eval_spline_noalloc(const float* ctrl, const float* we
     const bool t_array = o->t_mode == BEZ_T_SHARED || o->t_mode == BEZ_T_PER_CURVE;
     if (!ctrl || !out || (t_array && n_t > 0 && !t))
         return fail_na(BEZ_ERR_INVALID_ARG, "null ctrl, out or t");
-    // this entry point stages nothing: every array must already be on the device
-    if (!is_device_pointer(ctrl) || !is_device_pointer(out) || (weights && !is_device_pointer(weights)) ||
-        (knots && !is_device_pointer(knots)) || (t_array && n_t > 0 && !is_device_pointer(t)))
-        return fail_na(BEZ_ERR_INVALID_ARG, "arrays must be device memory (host arrays would need staging buffers)");
+    // this entry point stages nothing and switches no device: every array
+    // must already be in the current device's memory
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return fail_na(BEZ_ERR_CUDA, cudaGetErrorString(e));
+    if (!is_device_pointer_on(ctrl, cur) || !is_device_pointer_on(out, cur) ||
+        (weights && !is_device_pointer_on(weights, cur)) || (knots && !is_device_pointer_on(knots, cur)) ||
+        (t_array && n_t > 0 && !is_device_pointer_on(t, cur)))
+        return fail_na(BEZ_ERR_INVALID_ARG,
+                       "arrays must be device memory of the current device (host arrays would need staging "
+                       "buffers; make the arrays' device current before the call)");
 
     float* scratch = nullptr;
     int sm_count = 0;
-    cudaError_t e = scratch_for_current_device(&scratch, &sm_count);
+    e = scratch_for_current_device(&scratch, &sm_count);
     if (e != cudaSuccess) return fail_na(BEZ_ERR_CUDA, cudaGetErrorString(e));
     SplineArgs a{};
     a.ctrl = ctrl;

@@ -72,3 +72,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     import numpy as np
     with pytest.raises(RuntimeError, match="libbez.so not found"):
         bez.bez_eval(np.zeros((2, 4, 3), np.float32), np.zeros(3, np.float32))
+
+
+def test_noalloc_binding_refuses_arrays_on_different_gpus():
+    # bez_eval_spline_noalloc runs on the current device and never switches
+    # devices; the binding makes the arrays' device current and refuses a
+    # call whose arrays sit on two GPUs before reaching the library
+    from paper_2603_15447_gb300 import bez
+
+    class FakeDevice:
+        def __init__(self, index):
+            self.index = index
+
+    class FakeCudaTensor:
+        is_cuda = True
+
+        def __init__(self, index):
+            self.device = FakeDevice(index)
+
+    a, b = FakeCudaTensor(0), FakeCudaTensor(1)
+    assert bez._common_device(a, None, FakeCudaTensor(0)) == 0
+    assert bez._common_device(None, None) is None
+    with pytest.raises(bez.BezError) as e:
+        bez._common_device(a, None, b)
+    assert e.value.status == bez.Status.INVALID_ARG and "different GPUs" in str(e.value)
