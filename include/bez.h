@@ -114,6 +114,15 @@ typedef struct bez_opts {
                         * and BEZ_VAR_COISSUE) and of bez_eval_surface (texture           *
                         * variants); texture chains take BEZ_TEX_AUTO only; entry points  *
                         * and variants without textures ignore it                         */
+    int32_t tex_spread;/* 0 or 1: the paper's tile layouts.  2, 4, 8, 16 (s): spread     *
+                        * tiles, each 2D tile's bilinear function sampled on (s+1) x      *
+                        * (s+1) texels and read at s times its coordinates, which cuts   *
+                        * the error of the 8-bit filter weights about s-fold (Sec. 2.3)  *
+                        * for (s+1)^2 / 4 times the texture memory.  Built for           *
+                        * BEZ_VAR_TEX_SEILER curves of degree 2, 3 (bez_eval) and the    *
+                        * zig-zag chain texture (bez_eval_piecewise); elsewhere a value   *
+                        * above 1 returns BEZ_ERR_UNSUPPORTED.  Other values:             *
+                        * BEZ_ERR_INVALID_ARG.                                           */
 } bez_opts;
 
 /* Opaque context: owns staging buffers, texture atlases, timing events. */
@@ -462,6 +471,22 @@ bez_status bez_measure_peak(bez_ctx ctx, int kind, double* value, void* stream);
  *   out  [n][4] FP32 filtered values
  */
 bez_status bez_probe_filter(bez_ctx ctx, const float* xyz, int64_t n, float* out, void* stream);
+
+/*
+ * bez_probe_filter_2d -- the four texel weights of one bilinear read.
+ *
+ * Paper Sec. 2.3 (8-bit fractional filter weights).  Samples a 2x2 float4
+ * texture whose texel (x, y) holds the unit vector of channel x + 2 y, with
+ * linear filtering and clamp addressing, so the read at unnormalised
+ * coordinates (X, Y) returns the weights w00, w10, w01, w11 the hardware
+ * gives the four texels.  On GB300 they follow one rule: a = round8(frac(X -
+ * 0.5)), b = round8(frac(Y - 0.5)) (round to nearest 1/256, ties up), w11 =
+ * round8(a b), w10 = a - w11, w01 = b - w11, w00 = 1 - a - b + w11.
+ *
+ *   xy   [n][2] FP32 coordinates (texel centres at 0.5 and 1.5)
+ *   out  [n][4] FP32 weights (w00, w10, w01, w11); synchronous
+ */
+bez_status bez_probe_filter_2d(bez_ctx ctx, const float* xy, int64_t n, float* out, void* stream);
 
 #ifdef __cplusplus
 }

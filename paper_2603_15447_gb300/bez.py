@@ -71,7 +71,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("dtype", ctypes.c_int32), ("out_mode", ctypes.c_int32),
                 ("t_mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
                 ("sync", ctypes.c_int32), ("err_word", ctypes.c_void_p), ("tex_share", ctypes.c_int32),
-                ("tex_format", ctypes.c_int32)]
+                ("tex_format", ctypes.c_int32), ("tex_spread", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -107,6 +107,7 @@ def lib():
             L.bez_reset_stats.argtypes = [_VP]
             L.bez_eval.argtypes = [_VP, _VP, _I64, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts), _VP]
             L.bez_probe_filter.argtypes = [_VP, _VP, _I64, _VP, _VP]
+            L.bez_probe_filter_2d.argtypes = [_VP, _VP, _I64, _VP, _VP]
             L.bez_eval_bspline.argtypes = [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
                                            ctypes.POINTER(Opts), _VP]
             L.bez_eval_nurbs.argtypes = [_VP, _VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP,
@@ -122,7 +123,8 @@ def lib():
             L.bez_eval_piecewise.argtypes = [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _I64, _VP, ctypes.POINTER(Opts),
                                              _VP]
             for name in ("bez_create", "bez_destroy", "bez_set_timing", "bez_get_stats", "bez_reset_stats",
-                         "bez_eval", "bez_probe_filter", "bez_eval_piecewise", "bez_eval_bspline", "bez_eval_nurbs",
+                         "bez_eval", "bez_probe_filter", "bez_probe_filter_2d", "bez_eval_piecewise",
+                         "bez_eval_bspline", "bez_eval_nurbs",
                          "bez_eval_spline_noalloc", "bez_eval_surface", "bez_eval_volume",
                          "bez_eval_backward"):
                 getattr(L, name).restype = ctypes.c_int
@@ -227,16 +229,17 @@ def context(device: int | None = None) -> Context:
     return _contexts[device]
 
 
-def _opts(variant, dtype, out_mode, t_mode, seed, stream_id, sync, tex_share=0, tex_format=TexFormat.AUTO):
+def _opts(variant, dtype, out_mode, t_mode, seed, stream_id, sync, tex_share=0, tex_format=TexFormat.AUTO,
+          tex_spread=0):
     return Opts(int(variant), int(dtype), int(out_mode), int(t_mode), int(seed) & (2 ** 64 - 1),
-                int(stream_id) & 0xFFFFFFFF, int(sync), None, int(tex_share), int(tex_format))
+                int(stream_id) & 0xFFFFFFFF, int(sync), None, int(tex_share), int(tex_format), int(tex_spread))
 
 
 # ---------------------------------------------------------------- entry points
 
 def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.POINTS, t_mode=None,
              seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None, tex_share=0,
-             tex_format=TexFormat.AUTO):
+             tex_format=TexFormat.AUTO, tex_spread=0):
     """Evaluate Bezier curves ``ctrl`` [n_curves][degree+1][dim].
 
     ``t``: [n_t] (shared) or [n_curves][n_t] (per curve), or None with
@@ -245,7 +248,8 @@ def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.P
     device as ``ctrl``.  ``tex_share``: COISSUE only, samples of every 8
     read through the texture unit (1..7, 0 = library default).
     ``tex_format``: texel format of the texture variants (AUTO, UNORM16,
-    UNORM8)."""
+    UNORM8).  ``tex_spread``: TEX_SEILER degree 2, 3 only, texel intervals
+    per tile axis of the spread Seiler tile (0 / 1: the paper's 2x2 tile)."""
     n_curves, d1, dim = ctrl.shape
     if t_mode is None:
         t_mode = TMode.SHARED if (t is not None and t.ndim == 1) else TMode.PER_CURVE
@@ -257,7 +261,7 @@ def bez_eval(ctrl, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.P
         out = _empty_like_location(ctrl, shape)
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, tex_share, tex_format)
+    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, tex_share, tex_format, tex_spread)
     _check(lib().bez_eval(c.handle, _ptr(ctrl), n_curves, d1 - 1, dim, _ptr(t), n_t, _ptr(out), ctypes.byref(o),
                           _stream_handle(stream, dev)))
     return out
@@ -276,11 +280,25 @@ def bez_probe_filter(xyz, *, out=None, stream=None, ctx=None):
     return out
 
 
+def bez_probe_filter_2d(xy, *, out=None, stream=None, ctx=None):
+    """Bilinear read of a 2x2 texture with one-hot texels at the unnormalised
+    coordinates ``xy`` [n][2]; returns the four texel weights [n][4] (w00,
+    w10, w01, w11)."""
+    n = xy.shape[0]
+    if out is None:
+        out = _empty_like_location(xy, (n, 4))
+    dev = xy.device.index if _is_cuda(xy) else (ctx.device if ctx else 0)
+    c = ctx or context(dev)
+    _check(lib().bez_probe_filter_2d(c.handle, _ptr(xy), n, _ptr(out), _stream_handle(stream, dev)))
+    return out
+
+
 def bez_eval_piecewise(ctrl, n_seg, degree, t=None, *, n_t=None, variant=Variant.AUTO, out_mode=OutMode.POINTS,
                        t_mode=None, seed=0, stream_id=0, out=None, stream=None, sync=False, ctx=None,
-                       tex_format=TexFormat.AUTO):
+                       tex_format=TexFormat.AUTO, tex_spread=0):
     """Evaluate C0 chains ``ctrl`` [n_chains][n_seg*degree+1][dim] at global
-    parameters in [0, n_seg]."""
+    parameters in [0, n_seg].  ``tex_spread``: TEX_DECASTELJAU only, texel
+    intervals per window axis of the zig-zag texture (0 / 1: (N+1) x 2)."""
     n_chains, n_pts, dim = ctrl.shape
     assert n_pts == n_seg * degree + 1, "ctrl must hold n_seg*degree+1 points per chain"
     if t_mode is None:
@@ -293,7 +311,7 @@ def bez_eval_piecewise(ctrl, n_seg, degree, t=None, *, n_t=None, variant=Variant
         out = _empty_like_location(ctrl, shape)
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, 0, tex_format)
+    o = _opts(variant, _dtype_code(ctrl), out_mode, t_mode, seed, stream_id, sync, 0, tex_format, tex_spread)
     _check(lib().bez_eval_piecewise(c.handle, _ptr(ctrl), n_chains, n_seg, degree, dim, _ptr(t), n_t, _ptr(out),
                                     ctypes.byref(o), _stream_handle(stream, dev)))
     return out
@@ -379,7 +397,7 @@ def _common_device(*arrays):
 
 
 def bez_eval_surface(ctrl, nu, nv, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None,
-                     tex_format=TexFormat.AUTO):
+                     tex_format=TexFormat.AUTO, tex_spread=0):
     """Tensor-product surfaces ``ctrl`` [n][du+1][dv+1][dim] on an nu x nv
     uniform grid -> [n][nu][nv][dim].  ``tex_format``: texel storage of the
     texture variants (UNORM16 / UNORM8 with per-tile rescaling)."""
@@ -388,14 +406,15 @@ def bez_eval_surface(ctrl, nu, nv, *, variant=Variant.AUTO, out=None, stream=Non
         out = _empty_like_location(ctrl, (n, nu, nv, dim))
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync, tex_format=tex_format)
+    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync, tex_format=tex_format,
+              tex_spread=tex_spread)
     _check(lib().bez_eval_surface(c.handle, _ptr(ctrl), n, du1 - 1, dv1 - 1, dim, nu, nv, _ptr(out),
                                   ctypes.byref(o), _stream_handle(stream, dev)))
     return out
 
 
 def bez_eval_volume(ctrl, nu, nv, nw, *, variant=Variant.AUTO, out=None, stream=None, sync=False, ctx=None,
-                    tex_format=TexFormat.AUTO):
+                    tex_format=TexFormat.AUTO, tex_spread=0):
     """Tensor-product volumes ``ctrl`` [n][du+1][dv+1][dw+1][dim] on an
     nu x nv x nw uniform grid -> [n][nu][nv][nw][dim].  ``tex_format``: texel
     storage of the texture variants (tricubic scalar volumes)."""
@@ -404,7 +423,8 @@ def bez_eval_volume(ctrl, nu, nv, nw, *, variant=Variant.AUTO, out=None, stream=
         out = _empty_like_location(ctrl, (n, nu, nv, nw, dim))
     dev = ctrl.device.index if _is_cuda(ctrl) else (ctx.device if ctx else 0)
     c = ctx or context(dev)
-    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync, tex_format=tex_format)
+    o = _opts(variant, _dtype_code(ctrl), OutMode.POINTS, TMode.UNIFORM, 0, 0, sync, tex_format=tex_format,
+              tex_spread=tex_spread)
     _check(lib().bez_eval_volume(c.handle, _ptr(ctrl), n, du1 - 1, dv1 - 1, dw1 - 1, dim, nu, nv, nw, _ptr(out),
                                  ctypes.byref(o), _stream_handle(stream, dev)))
     return out

@@ -198,6 +198,8 @@ bez_status check_common(bez_ctx c, const bez_opts* o)
         return fail(BEZ_ERR_INVALID_ARG, "bad variant %d", o->variant);
     if (o->tex_format < BEZ_TEX_AUTO || o->tex_format > BEZ_TEX_UNORM8)
         return fail(BEZ_ERR_INVALID_ARG, "bad tex_format %d", o->tex_format);
+    if (o->tex_spread < 0 || o->tex_spread > 16 || (o->tex_spread & (o->tex_spread - 1)) != 0)
+        return fail(BEZ_ERR_INVALID_ARG, "tex_spread %d is not 0 or a power of two up to 16", o->tex_spread);
     return BEZ_OK;
 }
 
@@ -277,9 +279,11 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.dc3);
     atlas_free(c->tex.strip2);
     atlas_free(c->tex.seil2);
+    atlas_free(c->tex.seil2s);
     atlas_free(c->tex.seil3);
     atlas_free(c->tex.chain);
     atlas_free(c->tex.probe);
+    atlas_free(c->tex.probe2);
     atlas_free(c->tex.surf3);
     if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
     if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
@@ -363,6 +367,9 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
     if (var == BEZ_VAR_TEX_SEILER && (degree < 2 || degree > 7))
         return fail(BEZ_ERR_UNSUPPORTED, "Seiler textures are defined for degrees 2..7 (got %d)", degree);
+    if (o->tex_spread > 1 && !(var == BEZ_VAR_TEX_SEILER && degree <= 3))
+        return fail(BEZ_ERR_UNSUPPORTED, "spread tiles (tex_spread %d) are built for TEX_SEILER of degree 2, 3",
+                    o->tex_spread);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     if (n_curves == 0 || (n_t == 0 && o->out_mode == BEZ_OUT_POINTS)) return BEZ_OK;
     if (!ctrl || !out) return fail(BEZ_ERR_INVALID_ARG, "null ctrl or out");
@@ -425,7 +432,7 @@ bez_status bez_eval(bez_ctx c, const void* ctrl, int64_t n_curves, int degree, i
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
         r = coissue ? launch_tex_coissue(a, o->tex_share ? o->tex_share : kDefaultTexShare, o->tex_format, c->tex, s, h)
-                    : launch_tex_curve(a, var, tm, om, o->tex_format, c->tex, s, h);
+                    : launch_tex_curve(a, var, tm, om, o->tex_format, o->tex_spread, c->tex, s, h);
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "batch of %lld curves does not fit one texture atlas",
                         (long long)n_curves);
@@ -519,6 +526,8 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     if (tex && o->tex_format != BEZ_TEX_AUTO)
         return fail(BEZ_ERR_UNSUPPORTED, "chain textures use float4 / half4 texels (tex_format AUTO)");
+    if (!tex && o->tex_spread > 1)
+        return fail(BEZ_ERR_UNSUPPORTED, "tex_spread applies to the zig-zag chain texture (TEX_DECASTELJAU)");
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
     const int64_t per = ((int64_t)n_seg * degree + 1) * dim;
     if (!tex && per > kChainMaxFloats)
@@ -563,7 +572,7 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     LaunchResult r{0, cudaSuccess};
     if (tex) {
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        r = launch_tex_chain(a, tm, om, c->tex, s, h);
+        r = launch_tex_chain(a, tm, om, o->tex_spread, c->tex, s, h);
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "%lld chains of %d segments do not fit one texture atlas",
                         (long long)n_chains, n_seg);
@@ -706,6 +715,7 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
         return fail(BEZ_ERR_UNSUPPORTED, "texture volumes take at most %d rows in u and nw a multiple of 4",
                     kVolTexMaxRows);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
+    if (o->tex_spread > 1) return fail(BEZ_ERR_UNSUPPORTED, "spread tiles are not built for surfaces and volumes");
     TensorLaunch t{};
     t.dtype = o->dtype;
     t.n = n;
@@ -889,6 +899,30 @@ bez_status bez_probe_filter(bez_ctx c, const float* xyz, int64_t n, float* out, 
     LaunchResult r = launch_tex_probe(static_cast<const float*>(xd), n, static_cast<float*>(od), c->tex, s,
                                       hooks_of(c));
     if (r.err != cudaSuccess) return cuda_fail(r.err, "filter probe");
+    BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
+    c->tex_used = true;
+    return stg.finish(1);
+}
+
+bez_status bez_probe_filter_2d(bez_ctx c, const float* xy, int64_t n, float* out, void* stream)
+{
+    if (!c) return fail(BEZ_ERR_INVALID_ARG, "null context");
+    if (n < 0) return fail(BEZ_ERR_INVALID_ARG, "negative size");
+    if (n > 0 && (!xy || !out)) return fail(BEZ_ERR_INVALID_ARG, "null coordinates or output");
+    std::lock_guard<std::mutex> g(c->mu);
+    BEZ_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging stg{c, s};
+    const void* xd = nullptr;
+    void* od = nullptr;
+    bez_status st = stg.in(xy, (size_t)n * 2 * sizeof(float), 0, &xd);
+    if (st != BEZ_OK) return st;
+    st = stg.out(out, (size_t)n * 4 * sizeof(float), 2, &od);
+    if (st != BEZ_OK) return st;
+    if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
+    LaunchResult r = launch_tex_probe2d(static_cast<const float*>(xd), n, static_cast<float*>(od), c->tex, s,
+                                        hooks_of(c));
+    if (r.err != cudaSuccess) return cuda_fail(r.err, "2D filter probe");
     BEZ_CUDA(cudaEventRecord(c->tex_done, s), "cudaEventRecord");
     c->tex_used = true;
     return stg.finish(1);

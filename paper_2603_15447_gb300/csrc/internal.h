@@ -69,9 +69,11 @@ struct TexState {
     Atlas dc3;    // 3D de Casteljau tiles / strips: texel(x,y,z) = b_(x+y+z)
     Atlas strip2; // 2D strips: texel(x,y) = b_(x+y)
     Atlas seil2;  // 2D 2x2 Seiler tiles (degree 2, 3)
+    Atlas seil2s; // 2D (s+1) x (s+1) spread Seiler tiles (degree 2, 3)
     Atlas seil3;  // 3D 2x2x2 Seiler tiles (degree 4, 5)
     Atlas chain;  // zig-zag C0 chain textures
     Atlas probe;  // 2x2x2 weight probe
+    Atlas probe2; // 2x2 weight probe (one-hot texels)
     Atlas surf3;  // bicubic surface tiles: four column cubics per 2x2x2 RGBA tile
     Atlas surf2;  // bicubic surface tiles in the 2x2 Seiler layout, one column cubic per channel
     float4* rescale = nullptr;  // unorm tiles: per tile (offset, scale)
@@ -86,12 +88,16 @@ cudaError_t rescale_buffer(TexState& ts, int fmt, int64_t n, float4** out);
 
 // Texture evaluators: pack the control points into the atlas of `variant`,
 // then evaluate.  `variant` is a bez_variant texture value.
-LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, int tex_format, TexState& ts,
-                              cudaStream_t s, const LaunchHooks& h);
+// `spread` > 1 selects the spread Seiler tile (TEX_SEILER, degree 2, 3).
+LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, int tex_format, int spread,
+                              TexState& ts, cudaStream_t s, const LaunchHooks& h);
 // Co-issue: `share` of every 8 samples through the tex2D Seiler tile, the
 // rest by centred Horner (cubic, dim 3, hashed t with n_t <= 65536, length).
 constexpr int kDefaultTexShare = 2;
 LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, TexState& ts, cudaStream_t s,
+                                const LaunchHooks& h);
+// 2D probe: out[i] = the four bilinear texel weights at coords xy[i].
+LaunchResult launch_tex_probe2d(const float* xy, int64_t n, float* out, TexState& ts, cudaStream_t s,
                                 const LaunchHooks& h);
 // Filter-weight probe: out[i] = filtered (x, y, z) texel index at coords xyz[i].
 LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState& ts, cudaStream_t s,
@@ -104,7 +110,9 @@ LaunchResult launch_chain_bernstein(const CurveArgs& a, int tm, int om, cudaStre
 LaunchResult launch_chain_decasteljau(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 LaunchResult launch_chain_seiler(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 // Zig-zag texture for C0 quadratic chains (tex.cu).
-LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, cudaStream_t s, const LaunchHooks& h);
+// `spread` s >= 1: each 2x2 window sampled on an (s+1) x (s+1) texel grid.
+LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, TexState& ts, cudaStream_t s,
+                              const LaunchHooks& h);
 constexpr int kChainMaxFloats = 3072;  // (n_seg*degree+1)*dim per chain staged in shared memory
 
 // ---------------------------------------------------------------- splines

@@ -27,6 +27,16 @@
 //         st^3 L3 of any degree <= 7 (L_k = L(d_k, d_(d-k), t)).  The 4 and 16
 //         use the whole weight range of the y and z axes; d_k come from the
 //         exact peeling of the s-power form in FP64.
+//   SEIL2S degrees 2, 3 with a spread s >= 2: the SEIL2 tile's bilinear
+//         function F(x, y) = L(b0, bd, x) + (y/4) L(d1, d_(d-1), x), y = 4 st,
+//         sampled on an (s+1) x (s+1) texel grid (texel (i, j) = F(i/s, j/s))
+//         and read at (s t, 4 s st).  Bilinear filtering of a finer grid of a
+//         bilinear function reproduces the function, so the read computes the
+//         same Seiler form, but the 8-bit filter weights (Sec. 2.3) now
+//         quantise a coordinate s times finer: the hardware forms the weights
+//         of a cell from its fractions rounded to 1/256 (the twist weight
+//         round8(a b)), so every rounding term of a read shrinks by s (the
+//         twist term by s^2) at (s+1)^2 / 4 times the texture memory.
 //
 // Coordinates are unnormalised with texel centres at i + 0.5, so the paper's
 // [0.25, 0.75] remap of a 2-texel axis becomes x = x0 + 0.5 + t; for the st
@@ -36,7 +46,7 @@
 
 namespace bez {
 
-enum { TK_DC3 = 0, TK_DCN = 1, TK_HYB3 = 2, TK_HYBN = 3, TK_SEIL2 = 4, TK_SEIL3 = 5, TK_SEIL3Q = 6 };
+enum { TK_DC3 = 0, TK_DCN = 1, TK_HYB3 = 2, TK_HYBN = 3, TK_SEIL2 = 4, TK_SEIL3 = 5, TK_SEIL3Q = 6, TK_SEIL2S = 7 };
 
 struct TexArgs {
     cudaTextureObject_t tex;
@@ -44,6 +54,8 @@ struct TexArgs {
     int wt;   // tile width in texels
     int deg;
     float4* rescale;  // unorm formats: per curve (offset, scale) of its tile; nullptr for float / half texels
+    int ht;   // tile height in texels
+    int sp;   // SEIL2S: texel intervals per tile axis (spread)
 };
 
 // ---------------------------------------------------------------- atlases (host)
@@ -174,6 +186,20 @@ __device__ __forceinline__ void tile_texels(const float4* b, int d, int wt, Emit
     } else if (KIND == TK_HYB3 || KIND == TK_HYBN) {
         for (int y = 0; y < 2; ++y)
             for (int x = 0; x < wt; ++x) emit(x, y, 0, b[min(x + y, d)]);
+    } else if (KIND == TK_SEIL2S) {
+        // wt = s + 1 texels per axis; row j holds st = j / (4 s)
+        float4 d1, dl, d2, dl2;
+        seiler_terms(b, d, d1, dl, d2, dl2);
+        const int sp = wt - 1;
+        const float inv = 1.f / (float)sp;  // s is a power of two: exact
+        for (int y = 0; y <= sp; ++y) {
+            const float ys = 0.25f * inv * (float)y;
+            const float4 lo = add4(b[0], scale4(ys, d1)), hi = add4(b[d], scale4(ys, dl));
+            for (int x = 0; x <= sp; ++x) {
+                const float xs = inv * (float)x;
+                emit(x, y, 0, add4(scale4(1.f - xs, lo), scale4(xs, hi)));
+            }
+        }
     } else if (KIND == TK_SEIL3Q) {
         float4 lo[4], hi[4];
         seiler_terms_peeled(b, d, lo, hi);
@@ -225,7 +251,7 @@ __global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, 
         for (int k = 0; k < dim; ++k) v[k] = load_elem(a.ctrl, a.dtype, (c * (d + 1) + i) * dim + k);
         b[i] = make_float4(v[0], v[1], v[2], v[3]);
     }
-    const int x0 = (int)(c % ta.tw) * ta.wt, y0 = (int)(c / ta.tw) * 2;
+    const int x0 = (int)(c % ta.tw) * ta.wt, y0 = (int)(c / ta.tw) * ta.ht;
     const bool is3d = KIND == TK_DC3 || KIND == TK_DCN || KIND == TK_SEIL3 || KIND == TK_SEIL3Q;
     if (fmt < 2) {
         tile_texels<KIND>(b, d, ta.wt, [&](int x, int y, int z, float4 v) { put(surf, fmt, x0 + x, y0 + y, z, is3d, v); });
@@ -268,6 +294,11 @@ __device__ __forceinline__ float4 tex_point(const TexArgs& ta, float xb, float y
     if (KIND == TK_SEIL2) {
         const float st = fmaf(-t, t, t);
         return tex2D<float4>(ta.tex, xb + t, yb + st);
+    }
+    if (KIND == TK_SEIL2S) {
+        const float st = fmaf(-t, t, t);
+        const float s = (float)ta.sp;
+        return tex2D<float4>(ta.tex, xb + s * t, yb + (4.f * s) * st);
     }
     if (KIND == TK_SEIL3) {
         const float st = fmaf(-t, t, t);
@@ -342,7 +373,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex(const CurveArgs a, const Te
     const int dim = a.dim;
     for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
         const float xb = (float)((int)(c % ta.tw) * ta.wt) + 0.5f;
-        const float yb = (float)((int)(c / ta.tw) * 2) + 0.5f;
+        const float yb = (float)((int)(c / ta.tw) * ta.ht) + 0.5f;
         const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
         const Rescale rs(ta, c);
         const int n_t = a.n_t;
@@ -390,10 +421,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex(const CurveArgs a, const Te
 // ---------------------------------------------------------------- dispatch
 
 template <int KIND>
-LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, int wt, float4* rescale, cudaStream_t s,
-                         const LaunchHooks& h)
+LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, int wt, int ht, int sp, float4* rescale,
+                         cudaStream_t s, const LaunchHooks& h)
 {
-    TexArgs ta{at.tex, tw, wt, a.degree, rescale};
+    TexArgs ta{at.tex, tw, wt, a.degree, rescale, ht, sp};
     h.count(h.self);
     k_pack<KIND><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, at.surf, at.fmt);
     cudaError_t err = cudaGetLastError();
@@ -418,12 +449,13 @@ LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, 
     return {2, err};
 }
 
-// Tiles per atlas row: a power of two near sqrt(n * 2 / wt) so that the
-// atlas is roughly square (small coordinates keep more fractional bits).
-static int tiles_per_row(int64_t n, int wt, int max_w)
+// Tiles per atlas row: a power of two near sqrt(n * ht / wt) so that the
+// atlas of wt x ht tiles is roughly square (small coordinates keep more
+// fractional bits).
+static int tiles_per_row(int64_t n, int wt, int max_w, int ht = 2)
 {
     int tw = 1;
-    while ((int64_t)tw * tw * wt < n * 2 && tw * 2 * wt <= max_w) tw *= 2;
+    while ((int64_t)tw * tw * wt < n * ht && tw * 2 * wt <= max_w) tw *= 2;
     return tw;
 }
 
@@ -455,12 +487,12 @@ cudaError_t rescale_buffer(TexState& ts, int fmt, int64_t n, float4** out)
     return cudaSuccess;
 }
 
-LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, int tex_format, TexState& ts,
-                              cudaStream_t s, const LaunchHooks& h)
+LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, int tex_format, int spread,
+                              TexState& ts, cudaStream_t s, const LaunchHooks& h)
 {
     const int d = a.degree;
     const int fmt = texel_format(a.dtype, tex_format);
-    int kind, wt;
+    int kind, wt, ht = 2;
     bool is3d;
     if (variant == 6) {  // BEZ_VAR_TEX_DECASTELJAU
         kind = d == 3 ? TK_DC3 : TK_DCN;
@@ -470,31 +502,38 @@ LaunchResult launch_tex_curve(const CurveArgs& a, int variant, int tm, int om, i
         kind = d == 3 ? TK_HYB3 : TK_HYBN;
         wt = d >= 2 ? d : 2;
         is3d = false;
+    } else if (spread > 1) {  // BEZ_VAR_TEX_SEILER, degree 2 or 3, spread tile
+        kind = TK_SEIL2S;
+        wt = ht = spread + 1;
+        is3d = false;
     } else {  // BEZ_VAR_TEX_SEILER
         kind = d <= 3 ? TK_SEIL2 : d <= 5 ? TK_SEIL3 : TK_SEIL3Q;
         wt = 2;
         is3d = d > 3;
     }
     const int max_w = is3d ? ts.max3d : ts.max2d_w;
-    const int tw = tiles_per_row(a.n_curves, wt, max_w);
+    const int tw = tiles_per_row(a.n_curves, wt, max_w, ht);
     const int64_t rows = (a.n_curves + tw - 1) / tw;
-    const int64_t h_needed = rows * 2;
+    const int64_t h_needed = rows * ht;
     if (h_needed > (is3d ? ts.max3d : ts.max2d_h)) return {0, cudaErrorInvalidValue};
     Atlas& at = kind == TK_DC3 || kind == TK_DCN ? ts.dc3
                 : kind == TK_HYB3 || kind == TK_HYBN ? ts.strip2
-                : kind == TK_SEIL2 ? ts.seil2 : ts.seil3;   // SEIL3 and SEIL3Q share the 2x2x2 atlas
+                : kind == TK_SEIL2 ? ts.seil2
+                : kind == TK_SEIL2S ? ts.seil2s : ts.seil3;   // SEIL3 and SEIL3Q share the 2x2x2 atlas
     cudaError_t e = atlas_ensure(at, tw * wt, (int)h_needed, is3d ? 2 : 0, fmt);
     if (e != cudaSuccess) return {0, e};
     float4* rs = nullptr;
     if ((e = rescale_buffer(ts, fmt, a.n_curves, &rs)) != cudaSuccess) return {0, e};
+    const int sp = spread > 1 ? spread : 1;
     switch (kind) {
-    case TK_DC3: return launch_kind<TK_DC3>(a, tm, om, at, tw, wt, rs, s, h);
-    case TK_DCN: return launch_kind<TK_DCN>(a, tm, om, at, tw, wt, rs, s, h);
-    case TK_HYB3: return launch_kind<TK_HYB3>(a, tm, om, at, tw, wt, rs, s, h);
-    case TK_HYBN: return launch_kind<TK_HYBN>(a, tm, om, at, tw, wt, rs, s, h);
-    case TK_SEIL2: return launch_kind<TK_SEIL2>(a, tm, om, at, tw, wt, rs, s, h);
-    case TK_SEIL3: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, rs, s, h);
-    default: return launch_kind<TK_SEIL3Q>(a, tm, om, at, tw, wt, rs, s, h);
+    case TK_DC3: return launch_kind<TK_DC3>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    case TK_DCN: return launch_kind<TK_DCN>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    case TK_HYB3: return launch_kind<TK_HYB3>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    case TK_HYBN: return launch_kind<TK_HYBN>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    case TK_SEIL2: return launch_kind<TK_SEIL2>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    case TK_SEIL2S: return launch_kind<TK_SEIL2S>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    case TK_SEIL3: return launch_kind<TK_SEIL3>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
+    default: return launch_kind<TK_SEIL3Q>(a, tm, om, at, tw, wt, ht, sp, rs, s, h);
     }
 }
 
@@ -598,7 +637,7 @@ LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, T
     if (e != cudaSuccess) return {0, e};
     float4* rs = nullptr;
     if ((e = rescale_buffer(ts, fmt, a.n_curves, &rs)) != cudaSuccess) return {0, e};
-    TexArgs ta{ts.seil2.tex, tw, wt, 3, rs};
+    TexArgs ta{ts.seil2.tex, tw, wt, 3, rs, 2, 1};
     h.count(h.self);
     k_pack<TK_SEIL2><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, ts.seil2.surf, fmt);
     e = cudaGetLastError();
@@ -640,6 +679,25 @@ LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, T
 // (per component) minimises max_k |F_k|: with F_k = (-1)^k F_0 + G_k,
 // F_0 = -(max_k H_k + min_k H_k) / 2 for H_k = (-1)^k G_k.  Each F_(k+1) is
 // formed from the stored F_k, so every constraint holds to one rounding.
+//
+// Reads.  Along segment k both axes take the same fraction (tau on even k,
+// 1 - tau on odd k), so the hardware's per-axis weight rounding moves the
+// read along the curve: (tau~ - tau) Q'(tau) plus the twist weight's
+// rounding times the window's twist P_2k - 2 P_(2k+1) + P_(2k+2).  That holds
+// only if both coordinates carry the same fraction bits; the FP32 sums of the
+// atlas offsets would round them differently, and a read whose two 8-bit
+// weights round in opposite directions is off by 2^-8 of the free texels,
+// which can be tens of times the segment size.  The evaluator therefore
+// snaps the fraction to the hardware's 1/256 grid itself (round half up, as
+// the filter does) and adds it to exact integer coordinates (atlas width and
+// height below 2^15, so the sums are exact).
+//
+// Spread s >= 2: every window's bilinear function is sampled on an
+// (s+1) x (s+1) texel grid (neighbouring windows share their boundary
+// column, where both functions interpolate the same two texels), the
+// texture is (N s + 1) x (s + 1), and segment k is read at
+// (s (k + tau), s tau) or (s (k + tau), s (1 - tau)); the rounding terms
+// shrink by s (the twist term by s^2).
 __global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf, int fmt)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -679,9 +737,75 @@ __global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf
     }
 }
 
+// Spread chain texture: one warp per chain.  Lane 0 solves the free texels
+// F_k as k_chain_pack does and stages the column texels (P_2k, F_k) in shared
+// memory; then the lanes write the (N s + 1) x (s + 1) grid column by column.
+constexpr int kChainPackWarps = 4;
+constexpr size_t kChainPackMaxSmem = 192 * 1024;  // spread chains up to 1535 segments
+__global__ void __launch_bounds__(kChainPackWarps * 32) k_chain_pack_spread(const CurveArgs a, int cw, int sp,
+                                                                            cudaSurfaceObject_t surf, int fmt)
+{
+    extern __shared__ float4 s_cols[];  // per warp: [N+1] P_2k, then [N+1] F_k
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kChainPackWarps + wib;
+    if (c >= a.n_curves) return;
+    const int N = a.n_seg, dim = a.dim;
+    float4* Pc = s_cols + (size_t)wib * 2 * (N + 1);
+    float4* Fc = Pc + (N + 1);
+    const int64_t base = c * (int64_t)(2 * N + 1) * dim;
+    auto P = [&](int i, int k) { return load_elem(a.ctrl, a.dtype, base + (int64_t)i * dim + k); };
+    if (lane == 0) {
+        float f0[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < dim; ++k) {
+            float g = 0.f, hmax = 0.f, hmin = 0.f;
+            for (int s = 0; s < N; ++s) {
+                g = 2.f * P(2 * s + 1, k) - g;
+                const float h = (s & 1) ? g : -g;
+                hmax = fmaxf(hmax, h);
+                hmin = fminf(hmin, h);
+            }
+            f0[k] = -0.5f * (hmax + hmin);
+        }
+        float4 F = make_float4(f0[0], f0[1], f0[2], f0[3]);
+        for (int s = 0; s <= N; ++s) {
+            float p[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < dim; ++k) p[k] = P(2 * s, k);
+            if (fmt == 1)
+                F = make_float4(__half2float(__float2half_rn(F.x)), __half2float(__float2half_rn(F.y)),
+                                __half2float(__float2half_rn(F.z)), __half2float(__float2half_rn(F.w)));
+            Pc[s] = make_float4(p[0], p[1], p[2], p[3]);
+            Fc[s] = F;
+            if (s < N) {
+                float m[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int k = 0; k < dim; ++k) m[k] = P(2 * s + 1, k);
+                F = make_float4(2.f * m[0] - F.x, 2.f * m[1] - F.y, 2.f * m[2] - F.z, 2.f * m[3] - F.w);
+            }
+        }
+    }
+    __syncwarp();
+    const int W = N * sp + 1;
+    const int x0 = (int)(c % cw) * W, y0 = (int)(c / cw) * (sp + 1);
+    const float inv = 1.f / (float)sp;  // sp a power of two: exact
+    for (int i = lane; i < W; i += 32) {
+        const int k = min(i / sp, N - 1);
+        const float xs = inv * (float)(i - k * sp);
+        // window k: row r of column k holds P_2k if r == k mod 2, else F_k
+        const int rk = k & 1, rk1 = (k + 1) & 1;
+        const float4 t00 = rk == 0 ? Pc[k] : Fc[k], t01 = rk == 0 ? Fc[k] : Pc[k];
+        const float4 t10 = rk1 == 0 ? Pc[k + 1] : Fc[k + 1], t11 = rk1 == 0 ? Fc[k + 1] : Pc[k + 1];
+        const float4 r0 = add4(scale4(1.f - xs, t00), scale4(xs, t10));
+        const float4 r1 = add4(scale4(1.f - xs, t01), scale4(xs, t11));
+        for (int j = 0; j <= sp; ++j) {
+            const float ys = inv * (float)j;
+            put(surf, fmt, x0 + i, y0 + j, 0, false, add4(scale4(1.f - ys, r0), scale4(ys, r1)));
+        }
+    }
+}
+
 template <int TM>
 __device__ __forceinline__ float4 zigzag_eval(const CurveArgs& a, cudaTextureObject_t tex, int64_t c, int j,
-                                              uint32_t kc, float xb, float yb)
+                                              uint32_t kc, float xb, float yb, int sp)
 {
     const float ns = (float)a.n_seg;
     float t;
@@ -696,14 +820,25 @@ __device__ __forceinline__ float4 zigzag_eval(const CurveArgs& a, cudaTextureObj
     int k = (int)floorf(t);
     k = k < 0 ? 0 : (k > a.n_seg - 1 ? a.n_seg - 1 : k);
     const float tau = t - (float)k;
-    const float y = (k & 1) ? 1.f - tau : tau;
-    float4 P = tex2D<float4>(tex, (xb + (float)k) + tau, yb + y);
+    // u = s tau = iu + fq with fq on the filter's 1/256 grid (round half up)
+    const float u = (float)sp * tau;
+    float iu = floorf(u);
+    float fq = floorf(fmaf(u - iu, 256.f, 0.5f)) * (1.f / 256.f);
+    if (fq >= 1.f) {
+        iu += 1.f;
+        fq = 0.f;
+    }
+    // odd segments run from row s down to row 0: s (1 - tau) = (s - iu - 1) + (1 - fq)
+    const bool odd = k & 1;
+    const float iy = odd ? (float)sp - iu - (fq > 0.f ? 1.f : 0.f) : iu;
+    const float fy = odd ? (fq > 0.f ? 1.f - fq : 0.f) : fq;
+    float4 P = tex2D<float4>(tex, (xb + ((float)(k * sp) + iu)) + fq, (yb + iy) + fy);
     if (TM == TM_ARRAY && t != t) P = make_float4(t, t, t, t);
     return P;
 }
 
 template <int TM, int OM>
-__global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cudaTextureObject_t tex, int cw)
+__global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cudaTextureObject_t tex, int cw, int sp)
 {
     __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * 4 : 1];
     const int lane = threadIdx.x & 31;
@@ -711,8 +846,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
     const int64_t n_warps = (int64_t)gridDim.x * kWarps;
     const int dim = a.dim;
     for (int64_t c = (int64_t)blockIdx.x * kWarps + wib; c < a.n_curves; c += n_warps) {
-        const float xb = (float)((int)(c % cw) * (a.n_seg + 1)) + 0.5f;
-        const float yb = (float)((int)(c / cw) * 2) + 0.5f;
+        const float xb = (float)((int)(c % cw) * (a.n_seg * sp + 1)) + 0.5f;
+        const float yb = (float)((int)(c / cw) * (sp + 1)) + 0.5f;
         const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
         const int n_t = a.n_t;
         if (OM == OM_POINTS) {
@@ -720,7 +855,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
             for (int j0 = 0; j0 < n_t; j0 += 32) {
                 const int j = j0 + lane;
                 float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < n_t) P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb);
+                if (j < n_t) P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp);
                 const float pv[4] = {P.x, P.y, P.z, P.w};
                 for (int k = 0; k < dim; ++k) stage[lane * dim + k] = pv[k];
                 __syncwarp();
@@ -736,10 +871,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
             float acc = 0.f;
             float4 first = make_float4(0.f, 0.f, 0.f, 0.f), prev = first;
             if (jb < je) {
-                first = prev = zigzag_eval<TM>(a, tex, c, jb, kc, xb, yb);
+                first = prev = zigzag_eval<TM>(a, tex, c, jb, kc, xb, yb, sp);
 #pragma unroll 4
                 for (int j = jb + 1; j < je; ++j) {
-                    const float4 P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb);
+                    const float4 P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp);
                     acc += seg_len4(P, prev);
                     prev = P;
                 }
@@ -756,17 +891,38 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
     }
 }
 
-LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, cudaStream_t s, const LaunchHooks& h)
+// Chain atlases stay below 2^15 texels per axis so that the snapped read
+// coordinates (integer + 8-bit fraction) are exact in FP32.
+constexpr int kChainMaxCoord = 32768;
+
+LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, TexState& ts, cudaStream_t s,
+                              const LaunchHooks& h)
 {
-    const int wt = a.n_seg + 1;
+    const int sp = spread > 1 ? spread : 1;
+    const int64_t wt64 = (int64_t)a.n_seg * sp + 1;
+    const int max_w = ts.max2d_w < kChainMaxCoord ? ts.max2d_w : kChainMaxCoord;
+    const int max_h = ts.max2d_h < kChainMaxCoord ? ts.max2d_h : kChainMaxCoord;
+    if (wt64 > max_w) return {0, cudaErrorInvalidValue};
+    const int wt = (int)wt64;
     const int fmt = a.dtype == 1 ? 1 : 0;
-    const int cw = tiles_per_row(a.n_curves, wt, ts.max2d_w);
-    const int64_t h_needed = (a.n_curves + cw - 1) / cw * 2;
-    if (h_needed > ts.max2d_h || (int64_t)cw * wt > ts.max2d_w) return {0, cudaErrorInvalidValue};
+    const int cw = tiles_per_row(a.n_curves, wt, max_w, sp + 1);
+    const int64_t h_needed = (a.n_curves + cw - 1) / cw * (sp + 1);
+    if (h_needed > max_h || (int64_t)cw * wt > max_w) return {0, cudaErrorInvalidValue};
     cudaError_t e = atlas_ensure(ts.chain, cw * wt, (int)h_needed, 0, fmt);
     if (e != cudaSuccess) return {0, e};
     h.count(h.self);
-    k_chain_pack<<<(unsigned)((a.n_curves + 127) / 128), 128, 0, s>>>(a, cw, ts.chain.surf, fmt);
+    if (sp == 1) {
+        k_chain_pack<<<(unsigned)((a.n_curves + 127) / 128), 128, 0, s>>>(a, cw, ts.chain.surf, fmt);
+    } else {
+        const size_t smem = (size_t)kChainPackWarps * 2 * (a.n_seg + 1) * sizeof(float4);
+        if (smem > kChainPackMaxSmem) return {0, cudaErrorInvalidValue};
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_chain_pack_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return {0, e};
+        }
+        k_chain_pack_spread<<<(unsigned)((a.n_curves + kChainPackWarps - 1) / kChainPackWarps), kChainPackWarps * 32,
+                              smem, s>>>(a, cw, sp, ts.chain.surf, fmt);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return {1, e};
     const void* kern;
@@ -780,8 +936,8 @@ LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, TexState& ts, 
                                   : (const void*)k_chain_tex<TM_HASH, OM_LENGTH>;
     const int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, (a.n_curves + kWarps - 1) / kWarps);
     cudaTextureObject_t tex = ts.chain.tex;
-    int cw_arg = cw;
-    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg};
+    int cw_arg = cw, sp_arg = sp;
+    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg, (void*)&sp_arg};
     h.count(h.self);
     h.begin(h.self, s);
     e = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);
@@ -820,6 +976,37 @@ LaunchResult launch_tex_probe(const float* xyz, int64_t n, float* out, TexState&
     e = cudaGetLastError();
     h.end(h.self, s);
     return {2, e};
+}
+
+// 2D probe: texel (x, y) of a 2x2 float4 texture holds the unit vector of
+// channel x + 2 y, so a bilinear read returns the four texel weights.
+__global__ void k_probe2_pack(cudaSurfaceObject_t surf)
+{
+    const int x = threadIdx.x & 1, y = threadIdx.x >> 1;
+    const int k = x + 2 * y;
+    surf2Dwrite(make_float4(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f, k == 3 ? 1.f : 0.f), surf,
+                x * 16, y);
+}
+
+__global__ void k_probe2(cudaTextureObject_t tex, const float* xy, int64_t n, float* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    reinterpret_cast<float4*>(out)[i] = tex2D<float4>(tex, xy[2 * i], xy[2 * i + 1]);
+}
+
+LaunchResult launch_tex_probe2d(const float* xy, int64_t n, float* out, TexState& ts, cudaStream_t s,
+                                const LaunchHooks& h)
+{
+    cudaError_t e = atlas_ensure(ts.probe2, 2, 2, 0, 0);
+    if (e != cudaSuccess) return {0, e};
+    h.count(h.self);
+    k_probe2_pack<<<1, 4, 0, s>>>(ts.probe2.surf);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || n == 0) return {1, e};
+    h.count(h.self);
+    k_probe2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ts.probe2.tex, xy, n, out);
+    return {2, cudaGetLastError()};
 }
 
 }  // namespace bez

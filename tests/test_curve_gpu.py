@@ -339,3 +339,52 @@ def test_pipelined_host_call_matches_device_call(out_mode, t_mode, pinned):
     host = bez.bez_eval(host_ctrl, None if t is None else torch.from_numpy(t), **kw)
     assert host.device.type == "cpu"
     np.testing.assert_array_equal(host.numpy(), dev.cpu().numpy())
+
+
+def _ctrl_diag(ctrl):
+    c = ctrl.astype(np.float64)
+    return np.linalg.norm(c.max(axis=1) - c.min(axis=1), axis=-1)
+
+
+def test_headline_length_kernel_at_full_size():
+    # The fused draw + centred Horner + length kernel in the launch shape the
+    # benchmark times: 1,048,575 cubic 3D curves (the last pair of the
+    # two-curves-per-warp kernel half empty) x 1024 hashed parameters, so the
+    # grid is not persistent and every warp walks several pairs with the next
+    # pair's control points prefetched.  Every curve's length is compared with
+    # the oracle's; the tolerance takes the 1e-6 point bar over the control
+    # polygon's diagonal (>= the curve's), and a sample spread over the batch
+    # is held to the curve-diagonal tolerance of the smaller tests.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import synth
+    seed = synth.BASE_SEED + 1
+    n, n_t = (1 << 20) - 1, 1024
+    ctrl = synth.precision(seed=seed, n_curves=n)
+    got = _run(torch, ctrl, n_t=n_t, variant="HORNER_CENTRED", out_mode="POLYLINE_LENGTH", t_mode="HASH",
+               seed=seed, stream_id=synth.PRECISION_T_STREAM)
+    chunk = 1 << 15
+    L = np.concatenate([oracle.hashed_bezier_polyline_length(ctrl[s:s + chunk], n_t, seed,
+                                                             synth.PRECISION_T_STREAM, c0=s)
+                        for s in range(0, n, chunk)])
+    u = 2.0 ** -24
+    tol = 2 * (n_t - 1) * FP32_BAR * _ctrl_diag(ctrl) + (6 + n_t / 32 + 6) * u * L + 1e-7
+    assert np.all(np.abs(got - L) <= tol), (np.abs(got - L) / tol).max()
+    idx = np.unique(np.concatenate([np.arange(0, n, 97), [n - 2, n - 1]]))
+    th = np.concatenate([oracle.hash_t(seed, synth.PRECISION_T_STREAM, int(c), 1, n_t) for c in idx])
+    pts = oracle.bezier(ctrl[idx], th)
+    assert np.all(np.abs(got[idx] - L[idx]) <= _length_tol(pts, L[idx], n_t))
+    print(f"\nfull-size headline: max relative length error {np.max(np.abs(got - L) / L):.3g}")
+
+
+@pytest.mark.parametrize("variant", ["HORNER_CENTRED", "DECASTELJAU"])
+def test_points_kernel_at_block_scheduled_size(variant):
+    # k_curve (points) with more curves than resident warps: 50,001 curves
+    # (ragged against the 8-curve warp blocks) x 256 hashed parameters
+    torch = need_gpu()
+    rng = np.random.default_rng(1234)
+    n, n_t = 50001, 256
+    ctrl = _ctrl(rng, n, 3, 3)
+    got = _run(torch, ctrl, n_t=n_t, variant=variant, t_mode="HASH", seed=77, stream_id=5)
+    th = oracle.hash_t(77, 5, 0, n, n_t)
+    ref = oracle.bezier(ctrl, th)
+    assert normalised_error(got, ref).max() <= FP32_BAR

@@ -1,0 +1,282 @@
+"""GPU parity of the spread texture tiles and the snapped zig-zag reads.
+
+The filter rule.  A bilinear read on GB300 weighs the four texels of a cell
+by w00 = 1 - a - b + w11, w10 = a - w11, w01 = b - w11, w11 = round8(a b),
+where a, b are the coordinate fractions rounded to the nearest 1/256 (ties
+up) and round8 rounds to the nearest 1/256 (paper Sec. 2.3: 8 fractional
+bits).  test_bilinear_weight_rule pins that on every on-grid fraction pair
+and on random coordinates through bez_probe_filter_2d.  A read of a cell
+with corner values T00, T10, T01, T11 therefore returns the cell's bilinear
+function F at the rounded fractions, with the twist weight rounded:
+    F~ - F(a, b) = (a~ - a) dF/dx + (b~ - b) dF/dy + (round8(a~ b~) - a~ b~) D
+(dF/dx, dF/dy at (a~, b) and (a~, b~), D = T00 - T10 - T01 + T11), so
+    |F~ - F| <= e_x |dF/dx| + e_y |dF/dy| + 2^-9 |D|
+with e = 2^-9 plus the FP32 rounding of the unnormalised coordinate.
+
+Spread Seiler tiles (TEX_SEILER, degree 2, 3, tex_spread s).  The tile holds
+F(X, Y) = L(b0, bd, X) + (Y / 4) L(d1, d_(d-1), X) on an (s+1) x (s+1) grid
+and is read at (s t, 4 s st), so a cell's slopes are those of F over 1/s:
+    |dF/dx| <= max(|bd - b0|, |bd - b0 + (d_(d-1) - d1) / 4|) / s
+    |dF/dy| <= max(|d1|, |d_(d-1)|) / (4 s),   |D| = |d_(d-1) - d1| / (4 s^2).
+
+Zig-zag chains.  The evaluator snaps the shared fraction u = frac(s tau) to
+the 1/256 grid itself and forms exact coordinates, so the hardware keeps
+both fractions and the read is the segment's quadratic Q at the snapped
+parameter plus the twist term: with |tau_q - tau| <= 2^-9 / s,
+    |P - Q(tau)| <= 2^-9 / s max|Q'| + 2^-9 |P_2k - 2 P_(2k+1) + P_(2k+2)| / s^2.
+
+Beyond those a-priori bounds, the layouts the benchmark uses (spread 8 for
+cubic curves, spread 4 for chains) are held to the 2e-3 bar of the curve's
+bounding-box diagonal against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import need_gpu, normalised_error
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+E8 = 2.0 ** -9
+TEX_BAR = 2e-3
+
+
+def _dev(torch, x):
+    return None if x is None else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _eval(torch, ctrl, t=None, n_t=None, spread=8, t_mode=None, out_mode="POINTS", seed=0, stream_id=0,
+          half=False, tex_format="AUTO"):
+    from paper_2603_15447_gb300 import bez
+    c = _dev(torch, ctrl)
+    if half:
+        c = c.half()
+    out = bez.bez_eval(c, _dev(torch, None if t is None else np.asarray(t, np.float32)), n_t=n_t,
+                       variant=bez.Variant.TEX_SEILER, out_mode=bez.OutMode[out_mode],
+                       t_mode=None if t_mode is None else bez.TMode[t_mode], seed=seed, stream_id=stream_id,
+                       tex_format=bez.TexFormat[tex_format], tex_spread=spread)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _seiler_d(b):
+    d = b.shape[1] - 1
+    d1 = d * (b[:, 1] - b[:, 0]) - (b[:, d] - b[:, 0])
+    dl = d * (b[:, d - 1] - b[:, d]) - (b[:, 0] - b[:, d])
+    return d1, dl
+
+
+def spread_seiler_bound(ctrl, s, coord_eps=2.0 ** -11, texel_eps=U, texel_q=0.0):
+    """Per-curve bound on |P_tex - C| for the spread Seiler tile (module doc).
+    coord_eps: FP32 rounding of an unnormalised coordinate (half an ulp of
+    atlas coordinates below 2^13 is 2^-11 texel); texel_q: unorm rounding as
+    a fraction of the tile's range per component."""
+    b = ctrl.astype(np.float64)
+    d = b.shape[1] - 1
+    d1, dl = _seiler_d(b)
+    chord = b[:, d] - b[:, 0]
+    nrm = lambda v: np.linalg.norm(v, axis=-1)
+    fx = np.maximum(nrm(chord), nrm(chord + (dl - d1) / 4)) / s
+    fy = np.maximum(nrm(d1), nrm(dl)) / (4 * s)
+    tw = nrm(dl - d1) / (4 * s * s)
+    tiles = np.stack([b[:, 0], b[:, d], b[:, 0] + d1 / 4, b[:, d] + dl / 4], 1)
+    mag = np.abs(tiles).max(axis=(1, 2))
+    rng = np.linalg.norm(tiles.max(axis=1) - tiles.min(axis=1), axis=-1)
+    e = E8 + coord_eps
+    return e * (fx + fy) + E8 * tw + texel_q * rng + (4 * texel_eps + 16 * U) * mag * np.sqrt(3)
+
+
+def test_bilinear_weight_rule():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    k = np.arange(257) / 256.0
+    A, B = np.meshgrid(k, k, indexing="ij")
+    rng = np.random.default_rng(5)
+    ra, rb = rng.uniform(0, 1, 20000), rng.uniform(0, 1, 20000)
+    a = np.concatenate([A.ravel(), ra])
+    b = np.concatenate([B.ravel(), rb])
+    xy = np.stack([0.5 + a, 0.5 + b], 1).astype(np.float32)
+    w = bez.bez_probe_filter_2d(torch.from_numpy(xy).cuda()).cpu().numpy().astype(np.float64)
+    fa = xy[:, 0].astype(np.float64) - 0.5
+    fb = xy[:, 1].astype(np.float64) - 0.5
+    r8 = lambda v: np.floor(v * 256.0 + 0.5) / 256.0
+    aq, bq = r8(fa), r8(fb)
+    w11 = r8(aq * bq)
+    want = np.stack([1 - aq - bq + w11, aq - w11, bq - w11, w11], 1)
+    np.testing.assert_array_equal(w, want)
+    # on the 1/256 grid the per-axis weights are exact; only the twist weight rounds
+    n_on = 257 * 257
+    np.testing.assert_array_equal(w[:n_on, 1] + w[:n_on, 3], a[:n_on])
+    assert np.abs(w[:n_on, 3] - a[:n_on] * b[:n_on]).max() == 2.0 ** -9
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("s", [2, 4, 8, 16])
+def test_spread_seiler_within_bound(d, s):
+    torch = need_gpu()
+    rng = np.random.default_rng(300 + 10 * d + s)
+    ctrl = rng.uniform(-1, 1, size=(1501, d + 1, 3)).astype(np.float32)
+    t = rng.uniform(0, 1, 129).astype(np.float32)
+    t[:3] = [0.0, 1.0, 0.5]
+    got = _eval(torch, ctrl, t, spread=s)
+    ref = oracle.bezier(ctrl, t)
+    err = np.linalg.norm(got - ref, axis=-1).max(axis=1)
+    bound = spread_seiler_bound(ctrl, s)
+    assert np.all(err <= bound), (err / bound).max()
+    # the end points land on texel centres: exact
+    np.testing.assert_array_equal(got[:, 0], ctrl[:, 0])
+    np.testing.assert_array_equal(got[:, 1], ctrl[:, d])
+    print(f"\nspread Seiler d={d} s={s}: max normalised error {normalised_error(got, ref).max():.3g}, "
+          f"max error / bound {(err / bound).max():.3f}")
+
+
+@pytest.mark.parametrize("tex_format,half", [("UNORM16", False), ("AUTO", True)])
+def test_spread_seiler_texel_formats(tex_format, half):
+    torch = need_gpu()
+    rng = np.random.default_rng(310 + half)
+    ctrl = rng.uniform(-1, 1, size=(997, 4, 3)).astype(np.float32)
+    t = rng.uniform(0, 1, 97).astype(np.float32)
+    got = _eval(torch, ctrl, t, spread=8, tex_format=tex_format, half=half)
+    if half:
+        c16 = ctrl.astype(np.float16).astype(np.float32)
+        ref = oracle.bezier(c16, t)
+        bound = spread_seiler_bound(c16, 8, texel_eps=2.0 ** -11)
+    else:
+        ref = oracle.bezier(ctrl, t)
+        bound = spread_seiler_bound(ctrl, 8, texel_q=2.0 ** -17 * np.sqrt(3))
+    err = np.linalg.norm(got - ref, axis=-1).max(axis=1)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_spread_seiler_meets_bar_on_the_precision_workload():
+    # the benchmark's texture configuration: cubic 3D curves U[-1,1]^3,
+    # hashed parameters, spread 8, float4 texels; 16,385 curves x 1024 points
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import synth
+    seed = synth.BASE_SEED + 1
+    n, n_t = 16385, 1024
+    ctrl = synth.precision(seed=seed, n_curves=n)
+    got = _eval(torch, ctrl, n_t=n_t, t_mode="HASH", seed=seed, stream_id=synth.PRECISION_T_STREAM)
+    th = oracle.hash_t(seed, synth.PRECISION_T_STREAM, 0, n, n_t)
+    ref = oracle.bezier(ctrl, th)
+    e = normalised_error(got, ref)
+    assert e.max() <= TEX_BAR, e.max()
+    print(f"\nspread-8 Seiler, {n} curves x {n_t}: max normalised error {e.max():.3g}")
+
+
+def test_spread_seiler_full_size_atlas_sample():
+    # 1,048,576 curves take the full-size atlas (coordinates near 9,000
+    # texels); 64 hashed points each, every 16th curve checked at the bar
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import synth
+    seed = synth.BASE_SEED + 1
+    n, n_t = 1 << 20, 64
+    ctrl = synth.precision(seed=seed, n_curves=n)
+    got = _eval(torch, ctrl, n_t=n_t, t_mode="HASH", seed=seed, stream_id=synth.PRECISION_T_STREAM)
+    idx = np.arange(0, n, 16)
+    th = oracle.hash_t(seed, synth.PRECISION_T_STREAM, 0, n, n_t)[idx]
+    ref = oracle.bezier(ctrl[idx], th)
+    e = normalised_error(got[idx], ref)
+    assert e.max() <= TEX_BAR, e.max()
+
+
+def test_spread_arguments():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    c = torch.zeros((4, 4, 3), device="cuda")
+    t = torch.zeros(5, device="cuda")
+    for bad in (3, 32, -2):
+        with pytest.raises(bez.BezError) as e:
+            bez.bez_eval(c, t, variant=bez.Variant.TEX_SEILER, tex_spread=bad)
+        assert e.value.status == bez.Status.INVALID_ARG
+    for v in (bez.Variant.TEX_DECASTELJAU, bez.Variant.TEX_HYBRID, bez.Variant.HORNER):
+        with pytest.raises(bez.BezError) as e:
+            bez.bez_eval(c, t, variant=v, tex_spread=4)
+        assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:   # degree 5 Seiler tiles are 3D
+        bez.bez_eval(torch.zeros((4, 6, 3), device="cuda"), t, variant=bez.Variant.TEX_SEILER, tex_spread=4)
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_piecewise(torch.zeros((2, 9, 3), device="cuda"), 4, 2, torch.zeros(3, device="cuda"),
+                               variant=bez.Variant.DECASTELJAU, tex_spread=4)
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:
+        bez.bez_eval_surface(torch.zeros((2, 4, 4, 3), device="cuda"), 8, 8, variant=bez.Variant.TEX_SEILER,
+                             tex_spread=4)
+    assert e.value.status == bez.Status.UNSUPPORTED
+
+
+# ---------------------------------------------------------------- chains
+
+def _chain(torch, ctrl, n_seg, t=None, n_t=None, spread=1, t_mode=None, out_mode="POINTS", seed=0, stream_id=0):
+    from paper_2603_15447_gb300 import bez
+    out = bez.bez_eval_piecewise(_dev(torch, ctrl), n_seg, 2, _dev(torch, None if t is None else np.asarray(t, np.float32)),
+                                 n_t=n_t, variant=bez.Variant.TEX_DECASTELJAU, out_mode=bez.OutMode[out_mode],
+                                 t_mode=None if t_mode is None else bez.TMode[t_mode], seed=seed,
+                                 stream_id=stream_id, tex_spread=spread)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _free_texels_max(P):
+    """max |F_k| of the chain's zig-zag texels with F_0 minimising it."""
+    P = P.astype(np.float64)
+    N = (P.shape[0] - 1) // 2
+    G = np.zeros((N + 1, P.shape[1]))
+    for s in range(N):
+        G[s + 1] = 2 * P[2 * s + 1] - G[s]
+    H = G * np.array([(-1) ** k for k in range(N + 1)])[:, None]
+    F0 = -(H.max(axis=0) + H.min(axis=0)) / 2
+    F = np.array([(-1) ** k for k in range(N + 1)])[:, None] * (F0 + H)
+    return np.abs(F).max()
+
+
+def chain_bound(ctrl, t, s):
+    """Per-point bound of the snapped read (module doc), plus FP32 rounding
+    of the texels (free texels up to M in magnitude)."""
+    C, npts, dim = ctrl.shape
+    N = (npts - 1) // 2
+    P = ctrl.astype(np.float64)
+    k = np.clip(np.floor(t), 0, N - 1).astype(int)              # [C][n]
+    ci = np.arange(C)[:, None]
+    P0, P1, P2 = P[ci, 2 * k], P[ci, 2 * k + 1], P[ci, 2 * k + 2]
+    nrm = lambda v: np.linalg.norm(v, axis=-1)
+    dq = 2 * np.maximum(nrm(P1 - P0), nrm(P2 - P1))
+    tw = nrm(P0 - 2 * P1 + P2)
+    M = np.array([_free_texels_max(P[c]) for c in range(C)])[:, None]
+    return E8 / s * dq + E8 * tw / (s * s) + 24 * U * np.maximum(M, 1.0) * np.sqrt(dim)
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 8])
+def test_chain_snapped_reads_within_bound(s):
+    torch = need_gpu()
+    rng = np.random.default_rng(600 + s)
+    n_seg = 16
+    ctrl = rng.uniform(-1, 1, size=(257, 2 * n_seg + 1, 3)).astype(np.float32)
+    t = (rng.uniform(0, 1, (257, 301)) * n_seg).astype(np.float32)
+    t[:, :4] = [0.0, n_seg, 3.0, 4.0]                  # ends and two joints (even and odd segments)
+    got = _chain(torch, ctrl, n_seg, t, spread=s, t_mode="PER_CURVE")
+    ref = oracle.chain(ctrl, n_seg, 2, t)
+    err = np.linalg.norm(got - ref, axis=-1)
+    bound = chain_bound(ctrl, t, s)
+    assert np.all(err <= bound), (err / bound).max()
+    np.testing.assert_array_equal(got[:, 0], ctrl[:, 0])
+    np.testing.assert_array_equal(got[:, 1], ctrl[:, -1])
+    print(f"\nzig-zag s={s}: max normalised error {normalised_error(got, ref).max():.3g}")
+
+
+def test_chain_spread4_meets_bar_on_the_chain_workload():
+    # the benchmark's chain configuration (64 quadratic segments, control
+    # points U[-1,1]^3, parameters drawn U[0,64) in the kernel), spread 4
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import synth
+    seed = synth.BASE_SEED + 1
+    n, n_t = 2049, 4096
+    ctrl, _ = synth.chains(n_chains=n, n_t=1)
+    got = _chain(torch, ctrl, 64, n_t=n_t, spread=4, t_mode="HASH", seed=seed, stream_id=12)
+    u = oracle.hash_t(seed, 12, 0, n, n_t)
+    t = (np.float32(64) * u).astype(np.float32)
+    ref = oracle.chain(ctrl, 64, 2, t)
+    e = normalised_error(got, ref)
+    assert e.max() <= TEX_BAR, e.max()
+    print(f"\nzig-zag spread 4, {n} chains x {n_t}: max normalised error {e.max():.3g}")
