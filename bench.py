@@ -12,13 +12,16 @@ workload (16,384 chains x 64 quadratic segments, 65,536 parameters each,
 register de Casteljau vs the zig-zag texture).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload precision|plain|chains|batch|tensor|fit]
+                    [--workload all|precision|plain|chains|batch|tensor|fit]
 
-Prints one JSON line.  Under torchrun (N > 1) every rank evaluates its own
-batch of the same size (weak scaling, different seeds); the only cross-rank
-traffic is the timing barrier and a max over ranks of the timed duration.
-Workloads other than the default print their own line (measurement of the
-other configurations; the default line is the headline).
+Prints one JSON line.  The default (all) line is the precision workload's
+headline, and on one GPU its "configs" object adds the other four
+workloads (plain, batch, tensor, fit), each with its own throughput,
+roofline, accuracy against the oracle and clock sample.  Under torchrun
+(N > 1) every rank evaluates its own precision batch of the same size (weak
+scaling, different seeds); the only cross-rank traffic is the timing barrier
+and a max over ranks of the timed duration.  --workload X prints the line
+of one workload alone.
 """
 from __future__ import annotations
 
@@ -65,14 +68,19 @@ KERNEL_NAME = {"HORNER_CENTRED": "k_curve_pair (two curves per warp)", "HALF2": 
 TRAFFIC_SURFACE_65536 = 12652544 + 742988544
 TRAFFIC_FIT_65536x512 = 540098304 + 121953024
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
-            "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10}
+            "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10, "TEX_SEILER_S8": 3}
 # filtered fetches per point and the peak they are held to
-TEX_FETCHES = {"TEX_DECASTELJAU": (1, "tex3d_f32"), "TEX_SEILER": (1, "tex2d_f32"), "TEX_HYBRID": (2, "tex2d_f32")}
+TEX_FETCHES = {"TEX_DECASTELJAU": (1, "tex3d_f32"), "TEX_SEILER": (1, "tex2d_f32"), "TEX_HYBRID": (2, "tex2d_f32"),
+               "TEX_SEILER_S8": (1, "tex2d_f32")}
 REG_VARIANTS = ["HORNER", "HORNER_CENTRED", "BERNSTEIN", "SEILER", "DECASTELJAU", "HALF2"]
-TEX_VARIANTS = ["TEX_DECASTELJAU", "TEX_SEILER", "TEX_HYBRID"]
+TEX_VARIANTS = ["TEX_DECASTELJAU", "TEX_SEILER", "TEX_HYBRID", "TEX_SEILER_S8"]
 VARIANTS = REG_VARIANTS + TEX_VARIANTS
+# bench name -> (bez_variant name, tex_spread): TEX_SEILER_S8 is the cubic
+# Seiler tile spread over 9 x 9 texels
+VARIANT_SPEC = {v: (v, 0) for v in VARIANTS}
+VARIANT_SPEC["TEX_SEILER_S8"] = ("TEX_SEILER", 8)
 FP32_BAR, TEX_BAR = 1e-6, 2e-3
-SMS, LANES = 152, 128
+FALLBACK_SMS, LANES = 152, 128
 
 
 def load_peaks():
@@ -83,10 +91,24 @@ def load_peaks():
     return None
 
 
-def alu_peak(peaks):
-    """FP32/INT32 lane-operation issue peak: 152 SMs x 128 lanes x max clock."""
+def sm_count(dev=0):
+    """Streaming multiprocessors of the device (None without a GPU)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    except Exception:  # pragma: no cover - no torch / no device
+        pass
+    return None
+
+
+def alu_peak(peaks, sms=None):
+    """FP32/INT32 lane-operation issue peak: SMs x 128 lanes x max clock,
+    with the SM count read from the device (152 when none is given)."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
-    return SMS * LANES * mhz * 1e6, f"derived: {SMS} SMs x {LANES} lanes x {mhz:.0f} MHz"
+    src = "device" if sms else "fallback"
+    sms = sms or FALLBACK_SMS
+    return sms * LANES * mhz * 1e6, f"derived: {sms} SMs ({src}) x {LANES} lanes x {mhz:.0f} MHz"
 
 
 def hbm_peak(peaks):
@@ -114,6 +136,11 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to start: let its first sample arrive
+            # before the measured work begins, so short workloads are covered
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.01)
         except (FileNotFoundError, OSError):
             self.proc = None
         return self
@@ -222,9 +249,12 @@ def run_precision(args, rank, world, local_rank):
     ts = synth.PRECISION_T_STREAM
 
     def step_for(v, c=ctrl, fmt=bez.TexFormat.AUTO):
+        var, spread = VARIANT_SPEC[v]
+
         def step():
-            bez.bez_eval(c, None, n_t=args.n_t, variant=bez.Variant[v], out_mode=bez.OutMode.POLYLINE_LENGTH,
-                         t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, out=out, ctx=ctx, tex_format=fmt)
+            bez.bez_eval(c, None, n_t=args.n_t, variant=bez.Variant[var], out_mode=bez.OutMode.POLYLINE_LENGTH,
+                         t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, out=out, ctx=ctx, tex_format=fmt,
+                         tex_spread=spread)
         return step
 
     run_variants = [v for v in VARIANTS if v in args.variants.split(",")] if args.variants else list(VARIANTS)
@@ -277,17 +307,56 @@ def run_precision(args, rank, world, local_rank):
         cout = torch.empty(args.n_chains, dtype=torch.float32, device=dev)
         chains = {}
         csteps = max(args.steps // 4, 3)
-        for v in ("DECASTELJAU", "HORNER_CENTRED", "TEX_DECASTELJAU"):
-            def cstep(v=v):
-                bez.bez_eval_piecewise(cctrl, 64, 2, None, n_t=args.chain_t, variant=bez.Variant[v],
+        chain_variants = {"DECASTELJAU": ("DECASTELJAU", 0), "HORNER_CENTRED": ("HORNER_CENTRED", 0),
+                          "TEX_DECASTELJAU": ("TEX_DECASTELJAU", 0), "TEX_DECASTELJAU_S4": ("TEX_DECASTELJAU", 4)}
+        for name, (v, spread) in chain_variants.items():
+            def cstep(v=v, spread=spread, o=cout, n_t=args.chain_t, c=cctrl):
+                bez.bez_eval_piecewise(c, 64, 2, None, n_t=n_t, variant=bez.Variant[v],
                                        out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed,
-                                       stream_id=12, out=cout, ctx=ctx)
+                                       stream_id=12, out=o, ctx=ctx, tex_spread=spread)
             ms, st = timer.run(cstep, csteps, 2)
             n_pts = args.n_chains * args.chain_t * csteps
-            chains[v] = {"points_per_s": n_pts / (ms * 1e-3),
-                         "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
+            chains[name] = {"points_per_s": n_pts / (ms * 1e-3),
+                            "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
+            if spread:
+                chains[name]["tex_spread"] = spread
+        if not args.skip_accuracy:
+            # points of the first chains at 4096 of their hashed parameters against the oracle
+            import oracle
+            nc, nt = 256, 4096
+            u = oracle.hash_t(seed, 12, 0, nc, nt)
+            tch = (np.float32(64) * u.astype(np.float32)).astype(np.float32)
+            cref = oracle.chain(cctrl_np[:nc], 64, 2, tch)
+            cdiag = np.maximum(np.linalg.norm(cref.max(axis=1) - cref.min(axis=1), axis=-1), 2.0 ** -4)
+            for name, (v, spread) in chain_variants.items():
+                pts = bez.bez_eval_piecewise(cctrl[:nc].contiguous(), 64, 2, None, n_t=nt, variant=bez.Variant[v],
+                                             t_mode=bez.TMode.HASH, seed=seed, stream_id=12, ctx=ctx,
+                                             tex_spread=spread)
+                err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - cref, axis=-1).max(axis=1) / cdiag
+                bar = TEX_BAR if v.startswith("TEX") else FP32_BAR
+                chains[name].update({"max_norm_err": float(err.max()), "bar": bar,
+                                     "meets_bar": bool(err.max() <= bar)})
 
     ms_head = max_over_ranks(torch, dev, world, results[args.variant]["ms"])
+
+    # error of the timed kernel's own output: the headline step once more over
+    # the whole batch, then the lengths of 8 blocks of 512 curves spread over
+    # it (the last block ends at the last curve) against the oracle's
+    length_err = None
+    if not args.skip_accuracy:
+        import oracle
+        step_for(args.variant)()
+        torch.cuda.synchronize()
+        got_len = out.cpu().numpy().astype(np.float64)
+        bs = min(512, args.n_curves)
+        starts = np.unique(np.linspace(0, args.n_curves - bs, 8).astype(np.int64))
+        rel = []
+        for s0 in starts:
+            Lr = oracle.hashed_bezier_polyline_length(ctrl_np[s0:s0 + bs], args.n_t, seed, ts, c0=int(s0))
+            rel.append(np.abs(got_len[s0:s0 + bs] - Lr) / Lr)
+        length_err = {"max_rel_length_err": float(np.max(rel)),
+                      "sample": f"{len(starts)} blocks of {bs} curves spread over the batch (last block ends at "
+                                f"curve {args.n_curves - 1}), lengths of the timed launch shape"}
 
     # end to end through the public API with pinned host buffers
     ctrl_host = torch.from_numpy(ctrl_np).pin_memory()
@@ -308,7 +377,7 @@ def run_precision(args, rank, world, local_rank):
 
     if rank != 0:
         return None
-    peak_alu, peak_note = alu_peak(load_peaks())
+    peak_alu, peak_note = alu_peak(load_peaks(), sm_count(local_rank))
     peaks = measure_peaks(bez, ctx)
     pts_step = args.n_curves * args.n_t
     variants = {}
@@ -359,8 +428,9 @@ def run_precision(args, rank, world, local_rank):
         ref = oracle.bezier(ctrl_np[:ns], th)
         diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
         for v in run_variants:
-            pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
-                               seed=seed, stream_id=ts, ctx=ctx)
+            var, spread = VARIANT_SPEC[v]
+            pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[var], t_mode=bez.TMode.HASH,
+                               seed=seed, stream_id=ts, ctx=ctx, tex_spread=spread)
             err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
             bar = TEX_BAR if (v in TEX_FETCHES or v == "HALF2") else FP32_BAR
             variants[v]["max_norm_err"] = float(err.max())
@@ -368,14 +438,15 @@ def run_precision(args, rank, world, local_rank):
             variants[v]["meets_bar"] = bool(err.max() <= bar)
             for fname, tab in variants_unorm.items():
                 if v in tab:
-                    pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
-                                       seed=seed, stream_id=ts, ctx=ctx, tex_format=bez.TexFormat[fname])
+                    pts = bez.bez_eval(sample, None, n_t=args.n_t, variant=bez.Variant[var], t_mode=bez.TMode.HASH,
+                                       seed=seed, stream_id=ts, ctx=ctx, tex_format=bez.TexFormat[fname],
+                                       tex_spread=spread)
                     err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
                     tab[v]["max_norm_err"] = float(err.max())
             if v in variants16:
                 # against the oracle of the FP32 control points: includes the 2^-11 storage rounding
-                pts = bez.bez_eval(sample.half(), None, n_t=args.n_t, variant=bez.Variant[v], t_mode=bez.TMode.HASH,
-                                   seed=seed, stream_id=ts, ctx=ctx)
+                pts = bez.bez_eval(sample.half(), None, n_t=args.n_t, variant=bez.Variant[var],
+                                   t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, ctx=ctx, tex_spread=spread)
                 err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
                 variants16[v]["max_norm_err"] = float(err.max())
 
@@ -415,7 +486,9 @@ def run_precision(args, rank, world, local_rank):
                    "n_curves": args.n_curves, "n_t": args.n_t,
                    "degree": 3, "dim": 3, "l2": "flushed between timed steps (256 MiB device write)",
                    "speedup_vs_horner": head["speedup_vs_horner"],
-                   "max_norm_err": head.get("max_norm_err")},
+                   "max_norm_err": head.get("max_norm_err"),
+                   "max_norm_err_sample": f"first {args.accuracy_curves} curves x {args.n_t} points",
+                   **(length_err or {})},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_alu / 1e12, "unit": "Tops/s",
                      "frac": achieved / peak_alu, "traffic": traffic, "peak_source": peak_note,
                      "ops_per_launch": ops_launch,
@@ -435,6 +508,7 @@ def run_precision(args, rank, world, local_rank):
     if chains is not None:
         line["chains"] = {"workload": f"{args.n_chains} C0 chains x 64 quadratic segments, {args.chain_t} "
                                       "parameters per chain drawn U[0,64) in-kernel, fused polyline length",
+                          "accuracy_sample": "first 256 chains x 4096 points",
                           **chains}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ctrl_np, seed, args.n_t, args.cpu_seconds)
@@ -475,26 +549,85 @@ def _hbm_line(name, value, unit, steps, warmup, ms, bytes_step, kern_ms, kernel,
     return line
 
 
+def _record(name, value, unit, steps, warmup, ms, bytes_launch, kern_ms, kernel, clocks, extra, traffic=None):
+    """One workload's entry of the default line's "configs" object: the
+    metric over the whole step, the dominant kernel's HBM roofline and the
+    clocks sampled while it ran."""
+    line = _hbm_line(name, value, unit, steps, warmup, ms, bytes_launch, kern_ms, kernel, extra, traffic)
+    rec = {"workload": name, "value": value, "unit": unit, "ms_per_step": line["ms_per_step"], "steps": steps,
+           "warmup": warmup, "roofline": line["roofline"], "clocks": clocks}
+    rec.update(extra)
+    return rec
+
+
+def _standalone(rec):
+    """A workload's record as a JSON line of its own (--workload X)."""
+    line = {"metric": METRIC, "value": rec["value"], "unit": rec["unit"], "n_gpus": 1, "steps": rec["steps"],
+            "warmup": rec["warmup"], "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": rec["workload"]}}
+    line.update({k: v for k, v in rec.items() if k not in line and k not in ("workload",)})
+    return line
+
+
 def run_plain(args):
     import torch
 
     from paper_2603_15447_gb300 import bez, synth
+    import oracle
     ctx = bez.context(0)
     ctrl_np, t_np = synth.plain()
     ctrl, t = torch.from_numpy(ctrl_np).cuda(), torch.from_numpy(t_np).cuda()
     out = torch.empty((4096, 256, 3), device="cuda")
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
     res = {}
-    for v in ("HORNER", "DECASTELJAU", "SEILER", "HORNER_CENTRED"):
-        ms, st = timer.run(lambda v=v: bez.bez_eval(ctrl, t, variant=bez.Variant[v], out=out, ctx=ctx),
-                           args.steps, args.warmup)
-        res[v] = {"points_per_s": 4096 * 256 * args.steps / (ms * 1e-3),
-                  "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
+    # a launch takes microseconds: time more steps so that the clock sampler
+    # (100 ms period) sees the work
+    steps = max(args.steps, 400)
+    with ClockSampler(0) as clocks:
+        for v in ("HORNER", "DECASTELJAU", "SEILER", "HORNER_CENTRED"):
+            ms, st = timer.run(lambda v=v: bez.bez_eval(ctrl, t, variant=bez.Variant[v], out=out, ctx=ctx),
+                               steps, args.warmup)
+            res[v] = {"points_per_s": 4096 * 256 * steps / (ms * 1e-3),
+                      "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1), "ms": ms}
+    ref = oracle.bezier(ctrl_np, t_np)
+    diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
+    for v in res:
+        got = bez.bez_eval(ctrl, t, variant=bez.Variant[v], ctx=ctx).cpu().numpy().astype(np.float64)
+        res[v]["max_norm_err"] = float((np.linalg.norm(got - ref, axis=-1).max(axis=1) / diag).max())
+        res[v]["speedup_vs_horner"] = res[v]["points_per_s"] / res["HORNER"]["points_per_s"]
     head = res["DECASTELJAU"]
-    return _hbm_line("plain: 4,096 cubic 3D curves x 256 shared uniform t, points stored", head["points_per_s"],
-                     "points/s", args.steps, args.warmup, 4096 * 256 * args.steps / head["points_per_s"] * 1e3,
-                     4096 * 256 * 12 + 4096 * 48 + 1024, head["kernel_ms"], "k_curve (points)",
-                     {"variants": res, "note": "12.6 MB of output fits in L2; the launch is latency-bound"})
+    return _record("plain: 4,096 cubic 3D curves x 256 shared uniform t, points stored", head["points_per_s"],
+                   "points/s", steps, args.warmup, head["ms"], 4096 * 256 * 12 + 4096 * 48 + 1024,
+                   head["kernel_ms"], "k_curve (points, de Casteljau)", clocks.summary(),
+                   {"max_norm_err": head["max_norm_err"], "bar": FP32_BAR,
+                    "variants": {v: {k: x for k, x in r.items() if k != "ms"} for v, r in res.items()},
+                    "note": "12.6 MB of output fits in L2; the launch is latency-bound, so its HBM fraction is "
+                            "not a roofline statement"})
+
+
+def _batch_reference_sample(w, ids):
+    """Oracle points of the curves `ids` of a synth.batch workload: {c: [n][dim]}."""
+    import oracle
+    dim = w["dim"]
+    groups = {}
+    for c in ids:
+        groups.setdefault((int(w["type"][c]), int(w["degree"][c]), int(w["n_ctrl"][c]), int(w["n_samples"][c])),
+                          []).append(int(c))
+    out = {}
+    for (ty, p, n, ns), cs in groups.items():
+        ctrl = np.stack([w["ctrl_pool"][w["ctrl_off"][c]: w["ctrl_off"][c] + n * dim].reshape(n, dim) for c in cs])
+        t = oracle.grid(ns)
+        if ty == 0:
+            pts = oracle.bezier(ctrl, t)
+        elif ty == 1:
+            pts = oracle.bspline(ctrl, p, t)
+        else:
+            wts = np.stack([w["weight_pool"][w["weight_off"][c]: w["weight_off"][c] + n] for c in cs])
+            pts = oracle.bspline(ctrl, p, t, weights=wts)
+        for k, c in enumerate(cs):
+            out[c] = pts[k]
+    return out
 
 
 def run_batch(args):
@@ -509,114 +642,155 @@ def run_batch(args):
                            w["out_off"])
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
     n_pts = int(w["n_samples"].sum())
+    bytes_step = n_pts * 12 + w["ctrl_pool"].nbytes + w["weight_pool"].nbytes
     if args.batch_shape:
         # one fixed launch shape (chunk, schedule, threads, repr), spans extracted once, no tuning
         chunk, sched, threads, rep = (int(x) for x in args.batch_shape.split(","))
-        b = bez.Batch(desc, 3, ctrl, wts, out, chunk=chunk, schedule=sched, threads=threads, repr=rep,
-                      setup_each_launch=False, use_graph=True, ctx=ctx)
-        ms_b, st_b = timer.run(b.launch, args.steps, args.warmup)
-        b.close()
-        return _hbm_line(f"batch: {len(desc)} mixed curves, fixed shape chunk {chunk} schedule {sched} threads "
-                         f"{threads} repr {rep}, spans extracted once", n_pts * args.steps / (ms_b * 1e-3), "points/s",
-                         args.steps, args.warmup, ms_b, n_pts * 12 + w["ctrl_pool"].nbytes + w["weight_pool"].nbytes,
-                         ms_b / args.steps, "k_batch_class (graph replay)",
-                         {"gpu_launches": int(st_b["launches"]), "n_points": n_pts})
-    full = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=True, use_graph=True, ctx=ctx)
-    ms_full, st_full = timer.run(full.launch, args.steps, args.warmup)
-    cfg = full.config()
-    full.close()
-    ev = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=False, use_graph=True, ctx=ctx)
-    ms_ev, st_ev = timer.run(ev.launch, args.steps, args.warmup)
-    cfg_ev = ev.config()
+        with ClockSampler(0) as clocks:
+            b = bez.Batch(desc, 3, ctrl, wts, out, chunk=chunk, schedule=sched, threads=threads, repr=rep,
+                          setup_each_launch=False, use_graph=True, ctx=ctx)
+            ms_b, st_b = timer.run(b.launch, args.steps, args.warmup)
+            b.close()
+        return _record(f"batch: {len(desc)} mixed curves, fixed shape chunk {chunk} schedule {sched} threads "
+                       f"{threads} repr {rep}, spans extracted once", n_pts * args.steps / (ms_b * 1e-3),
+                       "points/s", args.steps, args.warmup, ms_b, bytes_step, ms_b / args.steps,
+                       "k_batch_class (graph replay)", clocks.summary(),
+                       {"gpu_launches": int(st_b["launches"]), "n_points": n_pts})
+    with ClockSampler(0) as clocks:
+        full = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=True, use_graph=True, ctx=ctx)
+        ms_full, st_full = timer.run(full.launch, args.steps, args.warmup)
+        cfg = full.config()
+        full.close()
+        ev = bez.Batch(desc, 3, ctrl, wts, out, autotune=True, setup_each_launch=False, use_graph=True, ctx=ctx)
+        ms_ev, st_ev = timer.run(ev.launch, args.steps, args.warmup)
+        cfg_ev = ev.config()
+    # accuracy of the timed launch's output: every 64th curve against the oracle
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
     ev.close()
-    bytes_step = n_pts * 12 + w["ctrl_pool"].nbytes + w["weight_pool"].nbytes
-    return _hbm_line(f"batch: {len(desc)} mixed curves (50% Bezier deg 1-7, 25% cubic B-spline, 25% NURBS), "
-                     f"{n_pts} points, one graph-captured persistent launch, autotuned",
-                     n_pts * args.steps / (ms_full * 1e-3), "points/s", args.steps, args.warmup, ms_full, bytes_step,
-                     ms_ev / args.steps, "k_batch_eval (graph replay, spans extracted once)",
-                     {"setup_each_launch_points_per_s": n_pts * args.steps / (ms_full * 1e-3),
-                      "eval_only_points_per_s": n_pts * args.steps / (ms_ev * 1e-3),
-                      "gpu_launches": int(st_full["launches"]), "autotuned": cfg, "autotuned_eval_only": cfg_ev,
-                      "n_points": n_pts})
+    ids = np.arange(0, len(desc), 64)
+    ref = _batch_reference_sample(w, ids)
+    worst, worst_kind = 0.0, {}
+    for c in ids:
+        ns = int(w["n_samples"][c])
+        g = got[w["out_off"][c]: w["out_off"][c] + ns * 3].reshape(ns, 3)
+        r = ref[int(c)]
+        diag = max(float(np.linalg.norm(r.max(axis=0) - r.min(axis=0))), 2.0 ** -4)
+        e = float(np.linalg.norm(g - r, axis=-1).max() / diag)
+        kind = ("bezier", "bspline", "nurbs")[int(w["type"][c])]
+        worst_kind[kind] = max(worst_kind.get(kind, 0.0), e)
+        worst = max(worst, e)
+    return _record(f"batch: {len(desc)} mixed curves (50% Bezier deg 1-7, 25% cubic B-spline, 25% NURBS), "
+                   f"{n_pts} points, one graph-captured launch of the class kernels, autotuned",
+                   n_pts * args.steps / (ms_full * 1e-3), "points/s", args.steps, args.warmup, ms_full, bytes_step,
+                   ms_ev / args.steps, "k_batch_class (graph replay, spans extracted once)", clocks.summary(),
+                   {"setup_each_launch_points_per_s": n_pts * args.steps / (ms_full * 1e-3),
+                    "eval_only_points_per_s": n_pts * args.steps / (ms_ev * 1e-3),
+                    "gpu_launches": int(st_full["launches"]), "autotuned": cfg, "autotuned_eval_only": cfg_ev,
+                    "n_points": n_pts, "max_norm_err": worst, "max_norm_err_by_type": worst_kind, "bar": FP32_BAR,
+                    "max_norm_err_sample": f"every 64th curve ({len(ids)} curves), all their points"})
 
 
 def run_tensor(args):
     import torch
 
     from paper_2603_15447_gb300 import bez, synth
+    import oracle
     ctx = bez.context(0)
     s = torch.from_numpy(synth.surfaces()).cuda()
     v = torch.from_numpy(synth.volumes()).cuda()
     so = torch.empty((65536, 32, 32, 3), device="cuda")
     vo = torch.empty((4096, 16, 16, 16, 1), device="cuda")
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
-    ms_s, st_s = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, out=so, ctx=ctx), args.steps, args.warmup)
-    ms_v, st_v = timer.run(lambda: bez.bez_eval_volume(v, 16, 16, 16, out=vo, ctx=ctx), args.steps, args.warmup)
-    tex = bez.Variant.TEX_DECASTELJAU
-    ms_t, st_t = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=tex, out=so, ctx=ctx), args.steps,
-                           args.warmup)
-    texs = bez.Variant.TEX_SEILER
-    ms_ts, st_ts = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx), args.steps,
-                             args.warmup)
-    kts = st_ts["timed_ms"] / st_ts["timed_launches"]
     n_s, n_v = 65536 * 1024, 4096 * 4096
-    vol_tex = {}
-    for vname in ("TEX_DECASTELJAU", "TEX_SEILER"):
-        var = bez.Variant[vname]
-        ms_vt, st_vt = timer.run(lambda var=var: bez.bez_eval_volume(v, 16, 16, 16, variant=var, out=vo, ctx=ctx),
+    tex, texs = bez.Variant.TEX_DECASTELJAU, bez.Variant.TEX_SEILER
+    # launches of ~0.1 ms: more steps so that the clock sampler sees the work
+    args = argparse.Namespace(**{**vars(args), "steps": max(args.steps, 100)})
+    with ClockSampler(0) as clocks:
+        ms_s, st_s = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, out=so, ctx=ctx), args.steps, args.warmup)
+        ms_v, st_v = timer.run(lambda: bez.bez_eval_volume(v, 16, 16, 16, out=vo, ctx=ctx), args.steps,
+                               args.warmup)
+        ms_t, st_t = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=tex, out=so, ctx=ctx), args.steps,
+                               args.warmup)
+        ms_ts, st_ts = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx),
                                  args.steps, args.warmup)
-        kvt = st_vt["timed_ms"] / st_vt["timed_launches"]
-        vol_tex[vname] = {"values_per_s": n_v * args.steps / (ms_vt * 1e-3), "kernel_ms": kvt,
-                          "gbs": (n_v * 4) / (kvt * 1e-3) / 1e9}
-    unorm = {}
-    for vname, var in (("TEX_DECASTELJAU", tex), ("TEX_SEILER", texs)):
-        for fname in ("UNORM16", "UNORM8"):
-            fmt = bez.TexFormat[fname]
-            ms_u, st_u = timer.run(lambda var=var, fmt=fmt: bez.bez_eval_surface(s, 32, 32, variant=var, out=so,
-                                                                                 ctx=ctx, tex_format=fmt),
-                                   args.steps, args.warmup)
-            unorm[f"{vname}/{fname}"] = {"points_per_s": n_s * args.steps / (ms_u * 1e-3),
-                                         "kernel_ms": st_u["timed_ms"] / st_u["timed_launches"]}
+        # half / bfloat16 control-point storage, FP32 contraction
+        low = {}
+        for lname, lt in (("f16", s.half()), ("bf16", s.bfloat16())):
+            ms_l, st_l = timer.run(lambda lt=lt: bez.bez_eval_surface(lt, 32, 32, out=so, ctx=ctx), args.steps,
+                                   args.warmup)
+            low[lname] = {"points_per_s": n_s * args.steps / (ms_l * 1e-3),
+                          "kernel_ms": st_l["timed_ms"] / max(st_l["timed_launches"], 1)}
+        vol_tex = {}
+        for vname in ("TEX_DECASTELJAU", "TEX_SEILER"):
+            var = bez.Variant[vname]
+            ms_vt, st_vt = timer.run(lambda var=var: bez.bez_eval_volume(v, 16, 16, 16, variant=var, out=vo, ctx=ctx),
+                                     args.steps, args.warmup)
+            kvt = st_vt["timed_ms"] / st_vt["timed_launches"]
+            vol_tex[vname] = {"values_per_s": n_v * args.steps / (ms_vt * 1e-3), "kernel_ms": kvt,
+                              "l2_gbs": (n_v * 4) / (kvt * 1e-3) / 1e9}
+        unorm = {}
+        for vname, var in (("TEX_DECASTELJAU", tex), ("TEX_SEILER", texs)):
+            for fname in ("UNORM16", "UNORM8"):
+                fmt = bez.TexFormat[fname]
+                ms_u, st_u = timer.run(lambda var=var, fmt=fmt: bez.bez_eval_surface(s, 32, 32, variant=var, out=so,
+                                                                                     ctx=ctx, tex_format=fmt),
+                                       args.steps, args.warmup)
+                unorm[f"{vname}/{fname}"] = {"points_per_s": n_s * args.steps / (ms_u * 1e-3),
+                                             "kernel_ms": st_u["timed_ms"] / st_u["timed_launches"]}
     ks = st_s["timed_ms"] / st_s["timed_launches"]
     kv = st_v["timed_ms"] / st_v["timed_launches"]
     kt = st_t["timed_ms"] / st_t["timed_launches"]
+    kts = st_ts["timed_ms"] / st_ts["timed_launches"]
     # accuracy on the first 1024 patches: max point error over the AABB
-    # diagonal of the patch's FP64 grid points
-    import oracle
+    # diagonal of the patch's FP64 grid points (FP32 control points)
     sub = s[:1024].contiguous()
     ref = oracle.surface(sub.cpu().numpy(), 32, 32).reshape(1024, -1, 3)
     diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
 
-    def surf_err(var, fmt=bez.TexFormat.AUTO):
-        got = bez.bez_eval_surface(sub, 32, 32, variant=var, ctx=ctx, tex_format=fmt)
+    def surf_err(var, fmt=bez.TexFormat.AUTO, c=sub):
+        got = bez.bez_eval_surface(c, 32, 32, variant=var, ctx=ctx, tex_format=fmt)
         got = got.cpu().numpy().reshape(1024, -1, 3)
         return float((np.linalg.norm(got.astype(np.float64) - ref, axis=-1).max(axis=1) / diag).max())
     for key, rec in unorm.items():
         vname, fname = key.split("/")
         rec["max_norm_err"] = surf_err(bez.Variant[vname], bez.TexFormat[fname])
+    low["f16"]["max_norm_err"] = surf_err(bez.Variant.AUTO, c=sub.half())
+    low["bf16"]["max_norm_err"] = surf_err(bez.Variant.AUTO, c=sub.bfloat16())
+    for lname in low:
+        low[lname]["bar"] = TEX_BAR
+        low[lname]["meets_bar"] = low[lname]["max_norm_err"] <= TEX_BAR
     vsub = v[:256].contiguous()
     vref = oracle.volume(vsub.cpu().numpy(), 16, 16, 16).reshape(256, -1)
     vspan = np.maximum(vref.max(axis=1) - vref.min(axis=1), 2.0 ** -4)
+
+    def vol_err(var):
+        got = bez.bez_eval_volume(vsub, 16, 16, 16, variant=var, ctx=ctx).cpu().numpy()
+        return float((np.abs(got.reshape(256, -1) - vref).max(axis=1) / vspan).max())
     for vname, rec in vol_tex.items():
-        got = bez.bez_eval_volume(vsub, 16, 16, 16, variant=bez.Variant[vname], ctx=ctx).cpu().numpy()
-        rec["max_norm_err"] = float((np.abs(got.reshape(256, -1) - vref).max(axis=1) / vspan).max())
-    return _hbm_line("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
-                     (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
-                     ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3_warp",
-                     {"surface_points_per_s": n_s * args.steps / (ms_s * 1e-3),
-                      "volume_values_per_s": n_v * args.steps / (ms_v * 1e-3), "volume_kernel_ms": kv,
-                      "volume_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9,
-                      "surface_max_norm_err": surf_err(bez.Variant.AUTO),
-                      "surface_tex": {"points_per_s": n_s * args.steps / (ms_t * 1e-3), "kernel_ms": kt,
-                                      "gbs": n_s * 12 / (kt * 1e-3) / 1e9, "max_norm_err": surf_err(tex),
-                                      "kernel": "k_surface_tex<3> (one trilinear read per row and coordinate)"},
-                      "surface_tex_seiler": {"points_per_s": n_s * args.steps / (ms_ts * 1e-3), "kernel_ms": kts,
-                                             "gbs": n_s * 12 / (kts * 1e-3) / 1e9, "max_norm_err": surf_err(texs),
-                                             "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
-                                                       "coordinate)"},
-                      "surface_tex_unorm": unorm,
-                      "volume_tex": vol_tex},
-                     traffic=TRAFFIC_SURFACE_65536)
+        rec["max_norm_err"] = vol_err(bez.Variant[vname])
+    surf_err_fp32 = surf_err(bez.Variant.AUTO)
+    return _record("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
+                   (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
+                   ms_s + ms_v, n_s * 12 + 65536 * 192, ks, "k_surface_bicubic3_warp", clocks.summary(),
+                   {"max_norm_err": max(surf_err_fp32, vol_err(bez.Variant.AUTO)), "bar": FP32_BAR,
+                    "max_norm_err_sample": "first 1024 patches and 256 volumes, all grid points",
+                    "surface_points_per_s": n_s * args.steps / (ms_s * 1e-3), "surface_max_norm_err": surf_err_fp32,
+                    "volume_values_per_s": n_v * args.steps / (ms_v * 1e-3), "volume_kernel_ms": kv,
+                    "volume_l2_gbs": (n_v * 4 + 4096 * 256) / (kv * 1e-3) / 1e9,
+                    "volume_note": "the 67 MB volume output stays in the 126 MB L2 between steps, so volume "
+                                   "GB/s are L2 figures, not an HBM roofline",
+                    "surface_low_precision_storage": low,
+                    "surface_tex": {"points_per_s": n_s * args.steps / (ms_t * 1e-3), "kernel_ms": kt,
+                                    "gbs": n_s * 12 / (kt * 1e-3) / 1e9, "max_norm_err": surf_err(tex),
+                                    "kernel": "k_surface_tex<3> (one trilinear read per row and coordinate)"},
+                    "surface_tex_seiler": {"points_per_s": n_s * args.steps / (ms_ts * 1e-3), "kernel_ms": kts,
+                                           "gbs": n_s * 12 / (kts * 1e-3) / 1e9, "max_norm_err": surf_err(texs),
+                                           "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
+                                                     "coordinate)"},
+                    "surface_tex_unorm": unorm,
+                    "volume_tex": vol_tex},
+                   traffic=TRAFFIC_SURFACE_65536)
 
 
 def run_fit(args):
@@ -624,6 +798,7 @@ def run_fit(args):
 
     from paper_2603_15447_gb300 import bez, synth
     from paper_2603_15447_gb300.autograd import bezier_curve
+    import oracle
     ctx = bez.context(0)
     truth, t_true, noise, init = synth.fit()
     target = bez.bez_eval(torch.from_numpy(truth).cuda(), torch.from_numpy(t_true).cuda(),
@@ -637,6 +812,17 @@ def run_fit(args):
     ctrl = torch.tensor(init, device="cuda")
     t = torch.tensor(t0, device="cuda")
     opt = torch.optim.Adam([ctrl, t], lr=1e-2)
+
+    # gradients of the first step against the oracle's analytic gradient
+    # (first 1024 curves; upstream gradient 2 s (C - y) from the oracle's C)
+    nsub = 1024
+    _, gc, _, gt = bez.bez_mse_grad(ctrl[:nsub].contiguous(), t[:nsub].contiguous(), target[:nsub].contiguous(),
+                                    loss_scale=scale, ctx=ctx)
+    y = target[:nsub].cpu().numpy().astype(np.float64)
+    C = oracle.bezier(init[:nsub], t0[:nsub])
+    gref_c, _, gref_t = oracle.bezier_grad(init[:nsub], t0[:nsub], 2 * scale * (C - y))
+    gc_err = float((np.abs(gc.cpu().numpy() - gref_c).max(axis=(1, 2)) / np.abs(gref_c).max(axis=(1, 2))).max())
+    gt_err = float((np.abs(gt.cpu().numpy() - gref_t).max(axis=1) / np.abs(gref_t).max(axis=1)).max())
 
     def step():
         loss, gc, _, gt = bez.bez_mse_grad(ctrl, t, target, loss_scale=scale, ctx=ctx)
@@ -660,24 +846,30 @@ def run_fit(args):
         return loss.detach()
 
     timer = Timer(torch, ctx, torch.device("cuda", 0), 1)
-    first = float(step().sum())
-    ms, st = timer.run(step, args.steps, args.warmup)
-    for _ in range(max(0, 200 - args.steps - args.warmup - 2)):
-        step()
-    final = float(step().sum())
-    ms_a, _ = timer.run(step_autograd, args.steps, args.warmup)
+    with ClockSampler(0) as clocks:
+        first = float(step().sum())
+        ms, st = timer.run(step, args.steps, args.warmup)
+        for _ in range(max(0, 200 - args.steps - args.warmup - 2)):
+            step()
+        final = float(step().sum())
+        ms_a, _ = timer.run(step_autograd, args.steps, args.warmup)
     kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
     # k_grad with a target, per sample: t 4 B + target 12 B in, grad_t 4 B out;
     # per curve: 48 B of control points in, 48 B of grad_ctrl and 4 B of loss out
     bytes_launch = n * 20 + n_curves * 100
-    return _hbm_line(f"fit: {n_curves:,} cubic 3D curves x {n_t} samples, fused forward + squared error + adjoint, "
-                     "then Adam, per step", n * args.steps / (ms * 1e-3), "samples/s", args.steps, args.warmup, ms,
-                     bytes_launch, kern_ms, "k_grad (fused squared error), mean launch",
-                     {"loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5,
-                      "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3),
-                                        "ms_per_step": ms_a / args.steps,
-                                        "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}},
-                     traffic=TRAFFIC_FIT_65536x512 if (n_curves, n_t) == (65536, 512) else None)
+    sigma = 0.01
+    return _record(f"fit: {n_curves:,} cubic 3D curves x {n_t} samples, fused forward + squared error + adjoint, "
+                   "then Adam, per step", n * args.steps / (ms * 1e-3), "samples/s", args.steps, args.warmup, ms,
+                   bytes_launch, kern_ms, "k_grad (fused squared error), mean launch", clocks.summary(),
+                   {"grad_ctrl_max_rel_err": gc_err, "grad_t_max_rel_err": gt_err,
+                    "grad_err_sample": f"first step, first {nsub} curves, per-curve max error over the curve's "
+                                       "largest oracle gradient",
+                    "loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5,
+                    "noise_sigma": sigma, "rms_over_sigma": final ** 0.5 / sigma,
+                    "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3),
+                                      "ms_per_step": ms_a / args.steps,
+                                      "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}},
+                   traffic=TRAFFIC_FIT_65536x512 if (n_curves, n_t) == (65536, 512) else None)
 
 
 # ------------------------------------------------------------------ reference arm
@@ -722,8 +914,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["precision", "plain", "chains", "batch", "tensor", "fit"],
-                    default="precision")
+    ap.add_argument("--workload", choices=["all", "precision", "plain", "chains", "batch", "tensor", "fit"],
+                    default="all")
     ap.add_argument("--variant", default="HORNER_CENTRED", choices=VARIANTS,
                     help="headline evaluator (the fastest one meeting the FP32 bar)")
     ap.add_argument("--variants", default="", help="comma-separated subset of evaluators to time")
@@ -764,14 +956,18 @@ def main():
         else:
             _build.build()
             torch.cuda.set_device(0)
-        if args.workload == "precision":
+        others = {"plain": run_plain, "batch": run_batch, "tensor": run_tensor, "fit": run_fit}
+        if args.workload in ("all", "precision"):
             line = run_precision(args, rank, world, local_rank)
+            if args.workload == "all" and world == 1 and line is not None:
+                # the other four workloads, each measured on this GPU right after the headline
+                line["configs"] = {name: fn(args) for name, fn in others.items()}
         elif args.workload == "chains":
             args.variants = "HORNER"
             args.skip_accuracy = True
             line = run_precision(args, rank, world, local_rank)
         else:
-            line = {"plain": run_plain, "batch": run_batch, "tensor": run_tensor, "fit": run_fit}[args.workload](args)
+            line = _standalone(others[args.workload](args))
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -274,6 +274,56 @@ __global__ void k_pack(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, 
     });
 }
 
+// Spread Seiler tiles: one thread per texel (curve c, row j, column i; i
+// fastest), so a warp writes neighbouring texels of one or two tiles.  Each
+// texel is F(i/s, j/s) of its curve's tile function (see SEIL2S above); the
+// unorm range of a tile is that of its four corners (a bilinear function
+// takes its extremes there), recorded by the thread of texel (0, 0).
+__global__ void k_pack_spread(const CurveArgs a, TexArgs ta, cudaSurfaceObject_t surf, int fmt)
+{
+    const int sp = ta.sp, n1 = sp + 1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c = idx / (n1 * n1);
+    if (c >= a.n_curves) return;
+    const int r = (int)(idx - c * n1 * n1);
+    const int j = r / n1, i = r - j * n1;
+    const int d = a.degree, dim = a.dim;
+    float4 b[4];
+    for (int q = 0; q < 4; ++q) {
+        const int pi = q == 0 ? 0 : q == 1 ? 1 : q == 2 ? d - 1 : d;  // b0, b1, b_(d-1), bd
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < dim; ++k) v[k] = load_elem(a.ctrl, a.dtype, (c * (d + 1) + pi) * dim + k);
+        b[q] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    // d1 = d (b1 - b0) - (bd - b0), d_(d-1) = d (b_(d-1) - bd) - (b0 - bd)  (Sec. 3.1)
+    const float fd = (float)d;
+    const float4 d1 = sub4(scale4(fd, sub4(b[1], b[0])), sub4(b[3], b[0]));
+    const float4 dl = sub4(scale4(fd, sub4(b[2], b[3])), sub4(b[0], b[3]));
+    const float inv = 1.f / (float)sp;  // sp a power of two: exact
+    auto texel = [&](int x, int y) {
+        const float ys = 0.25f * inv * (float)y, xs = inv * (float)x;
+        const float4 lo = add4(b[0], scale4(ys, d1)), hi = add4(b[3], scale4(ys, dl));
+        return add4(scale4(1.f - xs, lo), scale4(xs, hi));
+    };
+    const float4 v = texel(i, j);
+    const int x0 = (int)(c % ta.tw) * ta.wt, y0 = (int)(c / ta.tw) * ta.ht;
+    if (fmt < 2) {
+        put(surf, fmt, x0 + i, y0 + j, 0, false, v);
+        return;
+    }
+    const float4 c00 = texel(0, 0), c10 = texel(sp, 0), c01 = texel(0, sp), c11 = texel(sp, sp);
+    const float4 lo = min4(min4(c00, c10), min4(c01, c11)), hi = max4(max4(c00, c10), max4(c01, c11));
+    float4 sc = sub4(hi, lo);
+    sc = make_float4(sc.x > 0.f ? sc.x : 1.f, sc.y > 0.f ? sc.y : 1.f, sc.z > 0.f ? sc.z : 1.f, sc.w > 0.f ? sc.w : 1.f);
+    if (i == 0 && j == 0) {
+        ta.rescale[2 * c] = lo;
+        ta.rescale[2 * c + 1] = sc;
+    }
+    const float4 u = make_float4(__fdiv_rn(v.x - lo.x, sc.x), __fdiv_rn(v.y - lo.y, sc.y), __fdiv_rn(v.z - lo.z, sc.z),
+                                 __fdiv_rn(v.w - lo.w, sc.w));
+    put(surf, fmt, x0 + i, y0 + j, 0, false, u);
+}
+
 // ---------------------------------------------------------------- evaluators
 
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t)
@@ -426,7 +476,12 @@ LaunchResult launch_kind(const CurveArgs& a, int tm, int om, Atlas& at, int tw, 
 {
     TexArgs ta{at.tex, tw, wt, a.degree, rescale, ht, sp};
     h.count(h.self);
-    k_pack<KIND><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, at.surf, at.fmt);
+    if constexpr (KIND == TK_SEIL2S) {
+        const int64_t n_texels = a.n_curves * (int64_t)(sp + 1) * (sp + 1);
+        k_pack_spread<<<(unsigned)((n_texels + 255) / 256), 256, 0, s>>>(a, ta, at.surf, at.fmt);
+    } else {
+        k_pack<KIND><<<(unsigned)((a.n_curves + 255) / 256), 256, 0, s>>>(a, ta, at.surf, at.fmt);
+    }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return {1, err};
     const void* kern;

@@ -55,5 +55,7 @@ def test_roofline_block_arithmetic():
     assert r["peak"] == peak and ("measured" in note or "fallback" in note)
     assert bench.hbm_peak(None) == (6800.0, "of fallback (6.8 TB/s)")
     assert line["extra"] == 1 and line["ms_per_step"] == 2.0 and line["config"] == {"workload": "w"}
-    ops, _ = bench.alu_peak(None)
-    assert ops == 152 * 128 * 2070.0e6
+    ops, note = bench.alu_peak(None)
+    assert ops == 152 * 128 * 2070.0e6 and "fallback" in note
+    ops, note = bench.alu_peak({"sm_max_mhz": 2000.0}, sms=100)
+    assert ops == 100 * 128 * 2000.0e6 and "device" in note

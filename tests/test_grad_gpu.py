@@ -142,10 +142,13 @@ def test_autograd_function_matches_adjoint_and_finite_differences():
         assert abs(fd - float(t.grad[i, j])) <= 5e-3 * max(1.0, abs(fd))
 
 
-def test_adam_fit_reaches_noise_floor():
+def test_adam_fit_reduces_loss():
     # the fitting workload at reduced size: curves fitted to noisy samples of
     # random cubics (sigma 0.01) with Adam (lr 1e-2, 200 steps) through the
-    # autograd Function, t clamped to [0,1] after each step
+    # autograd Function, t clamped to [0,1] after each step.  200 steps at
+    # this rate cut the loss about 30-fold but stop well above the noise
+    # floor (RMS ~0.1 against sigma 0.01); the benchmark reports the final
+    # RMS, and test_adam_trajectory_matches_oracle_steps checks the steps
     torch = need_gpu()
     from paper_2603_15447_gb300 import synth
     from paper_2603_15447_gb300.autograd import bezier_curve
@@ -170,6 +173,51 @@ def test_adam_fit_reaches_noise_floor():
     assert final < first / 20, (first, final)
     assert np.sqrt(final) < 0.1
 
+
+def _adam_fp64(theta, g, m, v, k, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015, Algorithm 1) in FP64; k counts from 1."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** k)
+    vh = v / (1 - b2 ** k)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def test_adam_trajectory_matches_oracle_steps():
+    # ten steps of the fused fit step (bez_mse_grad + torch Adam on the GPU)
+    # against the same steps driven on the CPU by the oracle's curve and
+    # analytic gradient with an FP64 Adam: parameters stay within 1e-4 while
+    # each step moves them by up to lr = 1e-2 (a wrong term in a gradient
+    # shows up at the step size)
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez, synth
+    truth, t_true, noise, init = synth.fit(n_curves=64, n_t=512)
+    y = (oracle.bezier(truth, t_true) + noise).astype(np.float32)
+    n_c, n_t = y.shape[0], y.shape[1]
+    t0 = np.tile((np.arange(n_t) / (n_t - 1.0)).astype(np.float32), (n_c, 1))
+    scale = 1.0 / (n_c * n_t * 3)
+    ctrl = torch.tensor(init, device="cuda")
+    t = torch.tensor(t0, device="cuda")
+    target = torch.tensor(y, device="cuda")
+    opt = torch.optim.Adam([ctrl, t], lr=1e-2)
+    P, T = init.astype(np.float64), t0.astype(np.float64)
+    mP, vP, mT, vT = (np.zeros_like(P), np.zeros_like(P), np.zeros_like(T), np.zeros_like(T))
+    for k in range(1, 11):
+        _, gc, _, gt = bez.bez_mse_grad(ctrl, t, target, loss_scale=scale)
+        ctrl.grad, t.grad = gc, gt
+        opt.step()
+        t.clamp_(0, 1)
+        C = oracle.bezier(P, T)
+        rc, _, rt = oracle.bezier_grad(P, T, 2 * scale * (C - y))
+        P, mP, vP = _adam_fp64(P, rc, mP, vP, k)
+        T, mT, vT = _adam_fp64(T, rt, mT, vT, k)
+        T = np.clip(T, 0.0, 1.0)
+    torch.cuda.synchronize()
+    dP = np.abs(ctrl.cpu().numpy() - P).max()
+    dT = np.abs(t.cpu().numpy() - T).max()
+    assert dP <= 1e-4 and dT <= 1e-4, (dP, dT)
+    moved = np.abs(P - init).max()
+    assert moved > 0.05, moved                                # the parameters did move
 
 
 def _dmax_over_wmin(ctrl, w):
