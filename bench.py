@@ -714,6 +714,16 @@ def run_tensor(args):
                                args.warmup)
         ms_ts, st_ts = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx),
                                  args.steps, args.warmup)
+        # Seiler tiles spread over 9 x 9 texels (float4 and unorm16 texels)
+        spread_s = {}
+        for fname in ("AUTO", "UNORM16"):
+            fmt = bez.TexFormat[fname]
+            ms_x, st_x = timer.run(lambda fmt=fmt: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx,
+                                                                        tex_format=fmt, tex_spread=8),
+                                   args.steps, args.warmup)
+            kx = st_x["timed_ms"] / st_x["timed_launches"]
+            spread_s[fname] = {"points_per_s": n_s * args.steps / (ms_x * 1e-3), "kernel_ms": kx,
+                               "pack_ms": ms_x / args.steps - kx, "gbs": n_s * 12 / (kx * 1e-3) / 1e9}
         # half / bfloat16 control-point storage, FP32 contraction
         low = {}
         for lname, lt in (("f16", s.half()), ("bf16", s.bfloat16())):
@@ -722,9 +732,11 @@ def run_tensor(args):
             low[lname] = {"points_per_s": n_s * args.steps / (ms_l * 1e-3),
                           "kernel_ms": st_l["timed_ms"] / max(st_l["timed_launches"], 1)}
         vol_tex = {}
-        for vname in ("TEX_DECASTELJAU", "TEX_SEILER"):
-            var = bez.Variant[vname]
-            ms_vt, st_vt = timer.run(lambda var=var: bez.bez_eval_volume(v, 16, 16, 16, variant=var, out=vo, ctx=ctx),
+        for vname in ("TEX_DECASTELJAU", "TEX_SEILER", "TEX_SEILER_S8"):
+            var = bez.Variant[vname.replace("_S8", "")]
+            sp = 8 if vname.endswith("_S8") else 0
+            ms_vt, st_vt = timer.run(lambda var=var, sp=sp: bez.bez_eval_volume(v, 16, 16, 16, variant=var, out=vo,
+                                                                                ctx=ctx, tex_spread=sp),
                                      args.steps, args.warmup)
             kvt = st_vt["timed_ms"] / st_vt["timed_launches"]
             vol_tex[vname] = {"values_per_s": n_v * args.steps / (ms_vt * 1e-3), "kernel_ms": kvt,
@@ -748,8 +760,8 @@ def run_tensor(args):
     ref = oracle.surface(sub.cpu().numpy(), 32, 32).reshape(1024, -1, 3)
     diag = np.maximum(np.linalg.norm(ref.max(axis=1) - ref.min(axis=1), axis=-1), 2.0 ** -4)
 
-    def surf_err(var, fmt=bez.TexFormat.AUTO, c=sub):
-        got = bez.bez_eval_surface(c, 32, 32, variant=var, ctx=ctx, tex_format=fmt)
+    def surf_err(var, fmt=bez.TexFormat.AUTO, c=sub, spread=0):
+        got = bez.bez_eval_surface(c, 32, 32, variant=var, ctx=ctx, tex_format=fmt, tex_spread=spread)
         got = got.cpu().numpy().reshape(1024, -1, 3)
         return float((np.linalg.norm(got.astype(np.float64) - ref, axis=-1).max(axis=1) / diag).max())
     for key, rec in unorm.items():
@@ -764,11 +776,15 @@ def run_tensor(args):
     vref = oracle.volume(vsub.cpu().numpy(), 16, 16, 16).reshape(256, -1)
     vspan = np.maximum(vref.max(axis=1) - vref.min(axis=1), 2.0 ** -4)
 
-    def vol_err(var):
-        got = bez.bez_eval_volume(vsub, 16, 16, 16, variant=var, ctx=ctx).cpu().numpy()
+    def vol_err(var, spread=0):
+        got = bez.bez_eval_volume(vsub, 16, 16, 16, variant=var, ctx=ctx, tex_spread=spread).cpu().numpy()
         return float((np.abs(got.reshape(256, -1) - vref).max(axis=1) / vspan).max())
     for vname, rec in vol_tex.items():
-        rec["max_norm_err"] = vol_err(bez.Variant[vname])
+        rec["max_norm_err"] = vol_err(bez.Variant[vname.replace("_S8", "")], 8 if vname.endswith("_S8") else 0)
+    for fname, rec in spread_s.items():
+        rec["max_norm_err"] = surf_err(texs, bez.TexFormat[fname], spread=8)
+        rec["bar"] = TEX_BAR
+        rec["meets_bar"] = rec["max_norm_err"] <= TEX_BAR
     surf_err_fp32 = surf_err(bez.Variant.AUTO)
     return _record("tensor: 65,536 bicubic 3D patches on 32x32 + 4,096 tricubic scalar volumes on 16^3",
                    (n_s + n_v) * args.steps / ((ms_s + ms_v) * 1e-3), "points/s", args.steps, args.warmup,
@@ -789,6 +805,8 @@ def run_tensor(args):
                                            "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
                                                      "coordinate)"},
                     "surface_tex_unorm": unorm,
+                    "surface_tex_seiler_spread8": {**spread_s, "kernel": "k_surface_tex<3, Seiler> on 9 x 9 "
+                                                                         "spread tiles"},
                     "volume_tex": vol_tex},
                    traffic=TRAFFIC_SURFACE_65536)
 

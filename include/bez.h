@@ -119,10 +119,10 @@ typedef struct bez_opts {
                         * (s+1) texels and read at s times its coordinates, which cuts   *
                         * the error of the 8-bit filter weights about s-fold (Sec. 2.3)  *
                         * for (s+1)^2 / 4 times the texture memory.  Built for           *
-                        * BEZ_VAR_TEX_SEILER curves of degree 2, 3 (bez_eval) and the    *
-                        * zig-zag chain texture (bez_eval_piecewise); elsewhere a value   *
-                        * above 1 returns BEZ_ERR_UNSUPPORTED.  Other values:             *
-                        * BEZ_ERR_INVALID_ARG.                                           */
+                        * BEZ_VAR_TEX_SEILER curves of degree 2, 3 (bez_eval), the       *
+                        * zig-zag chain texture (bez_eval_piecewise) and TEX_SEILER      *
+                        * surfaces and volumes; elsewhere a value above 1 returns        *
+                        * BEZ_ERR_UNSUPPORTED.  Other values: BEZ_ERR_INVALID_ARG.       */
 } bez_opts;
 
 /* Opaque context: owns staging buffers, texture atlases, timing events. */
@@ -274,7 +274,9 @@ bez_status bez_eval_nurbs(bez_ctx ctx, const float* ctrl, const float* weights, 
  *   row gives the isoline control points, the cubic in v runs in FP32.
  *   variant TEX_SEILER (same limits): the four column cubics in the 2x2
  *   cubic Seiler layout (Sec. 4), one per channel of a 2D tile, read
- *   bilinearly at (u, u (1 - u)).
+ *   bilinearly at (u, u (1 - u)); with opts->tex_spread s >= 2 each
+ *   channel's Seiler function is sampled on an (s+1) x (s+1) tile read at
+ *   (s u, 4 s u (1 - u)), which divides the filter-weight error by about s.
  *   bez_eval_volume with TEX_DECASTELJAU / TEX_SEILER: tricubic scalar
  *   volumes (dim 1, nu <= 32, nw a multiple of 4, out 16-byte aligned);
  *   tile (p, j) holds the u cubics C[.][j][l] in channel l, one read per

@@ -715,7 +715,8 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
         return fail(BEZ_ERR_UNSUPPORTED, "texture volumes take at most %d rows in u and nw a multiple of 4",
                     kVolTexMaxRows);
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
-    if (o->tex_spread > 1) return fail(BEZ_ERR_UNSUPPORTED, "spread tiles are not built for surfaces and volumes");
+    if (o->tex_spread > 1 && var != BEZ_VAR_TEX_SEILER)
+        return fail(BEZ_ERR_UNSUPPORTED, "spread tiles are built for TEX_SEILER surfaces and volumes");
     TensorLaunch t{};
     t.dtype = o->dtype;
     t.n = n;
@@ -745,7 +746,8 @@ static bez_status eval_tensor(bez_ctx c, const void* ctrl, int64_t n, int du, in
     if (tex) {
         // the atlases are shared by all calls of this context: order their use
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        LaunchResult r = launch_tex_surface(t, var == BEZ_VAR_TEX_SEILER, o->tex_format, c->tex, s, hooks_of(c));
+        LaunchResult r =
+            launch_tex_surface(t, var == BEZ_VAR_TEX_SEILER, o->tex_format, o->tex_spread, c->tex, s, hooks_of(c));
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "%lld patches do not fit one texture atlas", (long long)n);
         if (r.err != cudaSuccess) return cuda_fail(r.err, "texture tile launch");

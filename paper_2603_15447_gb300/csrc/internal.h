@@ -155,8 +155,8 @@ LaunchResult launch_tensor_product(const TensorLaunch& t, cudaStream_t s, const 
 // bez_tex_format).
 constexpr int kSurfTexMaxRows = 64;
 constexpr int kVolTexMaxRows = 32;
-LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, TexState& ts, cudaStream_t s,
-                                const LaunchHooks& h);
+LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, int spread, TexState& ts,
+                                cudaStream_t s, const LaunchHooks& h);
 size_t tensor_product_smem(const TensorLaunch& t);
 
 // ---------------------------------------------------------------- adjoint

@@ -64,7 +64,23 @@ struct SurfTexArgs {
     cudaTextureObject_t tex;
     int tw;                 // tiles per atlas row
     const float4* rescale;  // unorm tiles: (lo, scale) per tile, value = lo + scale x code / levels; else NULL
+    int sp;                 // Seiler tiles: texel intervals per tile axis (1: the 2x2 tile read at (u, st);
+                            // s >= 2: (s+1) x (s+1) spread tile read at (s u, 4 s st))
 };
+
+// Unnormalised coordinates of the Seiler read of tile q at parameter u: the
+// paper's 2x2 tile at (u, u (1 - u)), or the spread tile at
+// (s u, 4 s u (1 - u)) (the tile's bilinear function sampled on an
+// (s+1) x (s+1) grid, see tex.cu).
+__device__ __forceinline__ float4 seiler_tile_read(const SurfTexArgs& ta, int64_t q, float u)
+{
+    const int n1 = ta.sp + 1;
+    const float x = (float)((int)(q % ta.tw) * n1) + 0.5f, y = (float)((int)(q / ta.tw) * n1) + 0.5f;
+    const float st = fmaf(-u, u, u);
+    if (ta.sp == 1) return tex2D<float4>(ta.tex, x + u, y + st);
+    const float s = (float)ta.sp;
+    return tex2D<float4>(ta.tex, x + s * u, y + (4.f * s) * st);
+}
 
 // A filtered unorm read mapped back to values: filtering is affine with
 // weights summing to 1, so lo + scale f of the filtered code f.
@@ -139,9 +155,12 @@ __global__ void __launch_bounds__(kSurfWarps * 32) k_volume_tricubic1_warp(const
                 // tile q = 4 p + j at texel (2 (q mod tw), 2 (q div tw)), centres at + 0.5
                 const int64_t q = p * 4 + j;
                 const float u = nu > 1 ? __fdiv_rn((float)ai, (float)(nu - 1)) : 0.f;
-                const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, yb = (float)((int)(q / ta.tw) * 2) + 0.5f;
-                y = USTAGE == VOL_U_TEX_SEILER ? tex2D<float4>(ta.tex, x + u, yb + fmaf(-u, u, u))
-                                               : tex3D<float4>(ta.tex, x + u, yb + u, 0.5f + u);
+                if (USTAGE == VOL_U_TEX_SEILER) {
+                    y = seiler_tile_read(ta, q, u);
+                } else {
+                    const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, yb = (float)((int)(q / ta.tw) * 2) + 0.5f;
+                    y = tex3D<float4>(ta.tex, x + u, yb + u, 0.5f + u);
+                }
                 if (ta.rescale) y = ta_rescale(ta, q, y);
             }
             s_y[w][e] = y;

@@ -20,11 +20,17 @@
 // l = 0..3, one per channel, so one read per (row u, j) gives Y[u][j][.],
 // and v and w contract on the FP32 pipes (k_volume_tricubic1_warp).
 //
+// Spread Seiler tiles (tex_spread s >= 2): each channel's Seiler bilinear
+// function F(X, Y) = L(b0 + (Y/4) d1, b3 + (Y/4) d2, X) sampled on an
+// (s+1) x (s+1) texel grid and read at (s u, 4 s u (1 - u)); the 8-bit
+// filter-weight rounding then moves the read s times less (tex.cu).
+//
 // Layout: surface tile q = p * dim + k sits at texel (2 (q mod tw),
 // 2 (q div tw), 0) of a float4, half4 or unorm 3D atlas of depth 2 (2D for
-// Seiler tiles); coordinates are unnormalised with texel centres at i + 0.5,
-// so row u reads at (x0+0.5+u, y0+0.5+u, 0.5+u) and u = 0, 1 land on texel
-// centres (exact corners).
+// Seiler tiles, (s+1) texels per tile axis when spread); coordinates are
+// unnormalised with texel centres at i + 0.5, so row u reads at
+// (x0+0.5+u, y0+0.5+u, 0.5+u) and u = 0, 1 land on texel centres (exact
+// corners).
 #include "tensor_common.cuh"
 #include "texel.cuh"
 
@@ -110,6 +116,60 @@ __global__ void k_pack_surface(const TensorArgs a, int tw, cudaSurfaceObject_t s
     }
 }
 
+// Spread Seiler tiles: one thread per texel (tile q, row j, column i).
+__global__ void k_pack_surface_spread(const TensorArgs a, int tw, int sp, cudaSurfaceObject_t surf, int fmt,
+                                      float4* rescale)
+{
+    const int n1 = sp + 1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vol = a.dw >= 0;
+    const int dim = a.dim;
+    const int per = vol ? 4 : dim;
+    const int64_t q = idx / (n1 * n1);
+    if (q >= a.n * per) return;
+    const int rr = (int)(idx - q * n1 * n1);
+    const int jj = rr / n1, ii = rr - jj * n1;
+    const int64_t p = q / per;
+    const int r = (int)(q - p * per);
+    const int cs = vol ? 1 : dim;
+    float4 b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t base = vol ? ((p * 4 + i) * 4 + r) * 4 : ((p * 4 + i) * 4) * dim + r;
+        b[i] = make_float4(load_elem(a.ctrl, a.dtype, base), load_elem(a.ctrl, a.dtype, base + cs),
+                           load_elem(a.ctrl, a.dtype, base + 2 * cs), load_elem(a.ctrl, a.dtype, base + 3 * cs));
+    }
+    // d1 = 3 (b1 - b0) - (b3 - b0), d2 = 3 (b2 - b3) - (b0 - b3) per channel (Sec. 3.1)
+    auto comb = [](float4 x0, float4 x1, float4 x3) {
+        return make_float4(3.f * (x1.x - x0.x) - (x3.x - x0.x), 3.f * (x1.y - x0.y) - (x3.y - x0.y),
+                           3.f * (x1.z - x0.z) - (x3.z - x0.z), 3.f * (x1.w - x0.w) - (x3.w - x0.w));
+    };
+    const float4 d1 = comb(b[0], b[1], b[3]), d2 = comb(b[3], b[2], b[0]);
+    const float inv = 1.f / (float)sp;  // sp a power of two: exact
+    auto texel = [&](int x, int y) {
+        const float ys = 0.25f * inv * (float)y, xs = inv * (float)x;
+        const float4 lo = make_float4(b[0].x + ys * d1.x, b[0].y + ys * d1.y, b[0].z + ys * d1.z, b[0].w + ys * d1.w);
+        const float4 hi = make_float4(b[3].x + ys * d2.x, b[3].y + ys * d2.y, b[3].z + ys * d2.z, b[3].w + ys * d2.w);
+        const float xl = 1.f - xs;
+        return make_float4(xl * lo.x + xs * hi.x, xl * lo.y + xs * hi.y, xl * lo.z + xs * hi.z, xl * lo.w + xs * hi.w);
+    };
+    float4 v = texel(ii, jj);
+    if (fmt >= TEXEL_UNORM16) {
+        // per channel over the tile's values: a bilinear function takes its extremes at the corners
+        const float4 c00 = texel(0, 0), c10 = texel(sp, 0), c01 = texel(0, sp), c11 = texel(sp, sp);
+        const float4 lo = min4(min4(c00, c10), min4(c01, c11)), hi = max4(max4(c00, c10), max4(c01, c11));
+        float4 sc = make_float4(hi.x - lo.x, hi.y - lo.y, hi.z - lo.z, hi.w - lo.w);
+        sc = make_float4(sc.x > 0.f ? sc.x : 1.f, sc.y > 0.f ? sc.y : 1.f, sc.z > 0.f ? sc.z : 1.f, sc.w > 0.f ? sc.w : 1.f);
+        if (ii == 0 && jj == 0) {
+            rescale[2 * q] = lo;
+            rescale[2 * q + 1] = sc;
+        }
+        v = make_float4(__fdiv_rn(v.x - lo.x, sc.x), __fdiv_rn(v.y - lo.y, sc.y), __fdiv_rn(v.z - lo.z, sc.z),
+                        __fdiv_rn(v.w - lo.w, sc.w));
+    }
+    put(surf, fmt, (int)(q % tw) * n1 + ii, (int)(q / tw) * n1 + jj, 0, false, v);
+}
+
 // One warp per patch: lanes read the isoline control points of their rows,
 // then the warp sweeps the grid a row segment of up to 32 points at a time
 // and stores it through a warp-private staging buffer as consecutive floats.
@@ -133,9 +193,12 @@ __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const Tensor
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             const int64_t q = pp * DIM + k;
-            const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
-            X[k] = SEILER ? tex2D<float4>(ta.tex, x + u, y + fmaf(-u, u, u))
-                          : tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
+            if (SEILER) {
+                X[k] = seiler_tile_read(ta, q, u);
+            } else {
+                const float x = (float)((int)(q % ta.tw) * 2) + 0.5f, y = (float)((int)(q / ta.tw) * 2) + 0.5f;
+                X[k] = tex3D<float4>(ta.tex, x + u, y + u, 0.5f + u);
+            }
             if (ta.rescale) X[k] = ta_rescale(ta, q, X[k]);
         }
     };
@@ -187,17 +250,18 @@ __global__ void __launch_bounds__(kSurfWarps * 32, 4) k_surface_tex(const Tensor
     }
 }
 
-// tiles per atlas row: a power of two near sqrt(tiles) so the atlas is
-// roughly square (small coordinates keep more fractional bits)
-static int surface_tiles_per_row(int64_t tiles, int max_w)
+// tiles per atlas row: a power of two near sqrt(tiles) so the atlas of
+// n1 x n1 tiles is roughly square (small coordinates keep more fractional
+// bits)
+static int surface_tiles_per_row(int64_t tiles, int max_w, int n1)
 {
     int tw = 1;
-    while ((int64_t)tw * tw < tiles && tw * 4 <= max_w) tw *= 2;
+    while ((int64_t)tw * tw < tiles && tw * 2 * n1 <= max_w) tw *= 2;
     return tw;
 }
 
-LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, TexState& ts, cudaStream_t s,
-                                const LaunchHooks& h)
+LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_format, int spread, TexState& ts,
+                                cudaStream_t s, const LaunchHooks& h)
 {
     TensorArgs a{};
     a.ctrl = t.ctrl;
@@ -213,18 +277,26 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_form
     a.out = t.out;
     const bool vol = a.dw >= 0;
     const int64_t tiles = a.n * (vol ? 4 : a.dim);
-    const int tw = surface_tiles_per_row(tiles, ts.max3d);
+    const int sp = seiler && spread > 1 ? spread : 1;
+    const int n1 = sp + 1;
+    const int tw = surface_tiles_per_row(tiles, ts.max3d, n1);
     const int64_t rows = (tiles + tw - 1) / tw;
-    if (rows * 2 > ts.max3d) return {0, cudaErrorInvalidValue};
+    if (rows * n1 > ts.max3d) return {0, cudaErrorInvalidValue};
     const int fmt = texel_format(a.dtype, tex_format);
     Atlas& at = seiler ? ts.surf2 : ts.surf3;
-    cudaError_t e = atlas_ensure(at, tw * 2, (int)(rows * 2), seiler ? 0 : 2, fmt);
+    cudaError_t e = atlas_ensure(at, tw * n1, (int)(rows * n1), seiler ? 0 : 2, fmt);
     if (e != cudaSuccess) return {0, e};
     float4* rs = nullptr;
     if ((e = rescale_buffer(ts, fmt, tiles, &rs)) != cudaSuccess) return {0, e};
     h.count(h.self);
-    if (seiler) k_pack_surface<true><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt, rs);
-    else k_pack_surface<false><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt, rs);
+    if (sp > 1) {
+        const int64_t n_texels = tiles * n1 * n1;
+        k_pack_surface_spread<<<(unsigned)((n_texels + 255) / 256), 256, 0, s>>>(a, tw, sp, at.surf, fmt, rs);
+    } else if (seiler) {
+        k_pack_surface<true><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt, rs);
+    } else {
+        k_pack_surface<false><<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(a, tw, at.surf, fmt, rs);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return {1, e};
     const void* kern;
@@ -244,7 +316,7 @@ LaunchResult launch_tex_surface(const TensorLaunch& t, bool seiler, int tex_form
     a.vparts = vol ? volume_parts(a.n, a.nu, h.sm_count) : 1;
     const int grid = persistent_grid(kern, kSurfWarps * 32, 0, h.sm_count,
                                      (a.n * a.vparts + kSurfWarps - 1) / kSurfWarps);
-    SurfTexArgs sa{at.tex, tw, rs};
+    SurfTexArgs sa{at.tex, tw, rs, sp};
     void* args[] = {(void*)&a, (void*)&sa};
     h.count(h.self);
     h.begin(h.self, s);

@@ -201,7 +201,7 @@ def test_spread_arguments():
                                variant=bez.Variant.DECASTELJAU, tex_spread=4)
     assert e.value.status == bez.Status.UNSUPPORTED
     with pytest.raises(bez.BezError) as e:
-        bez.bez_eval_surface(torch.zeros((2, 4, 4, 3), device="cuda"), 8, 8, variant=bez.Variant.TEX_SEILER,
+        bez.bez_eval_surface(torch.zeros((2, 4, 4, 3), device="cuda"), 8, 8, variant=bez.Variant.TEX_DECASTELJAU,
                              tex_spread=4)
     assert e.value.status == bez.Status.UNSUPPORTED
 
@@ -280,3 +280,74 @@ def test_chain_spread4_meets_bar_on_the_chain_workload():
     e = normalised_error(got, ref)
     assert e.max() <= TEX_BAR, e.max()
     print(f"\nzig-zag spread 4, {n} chains x {n_t}: max normalised error {e.max():.3g}")
+
+
+# ---------------------------------------------------------------- surfaces and volumes
+
+def _column_bound(c, s):
+    """Spread-tile bound per column cubic: c [..., 4] scalar control values."""
+    c = c.astype(np.float64)
+    d1 = 3 * (c[..., 1] - c[..., 0]) - (c[..., 3] - c[..., 0])
+    d2 = 3 * (c[..., 2] - c[..., 3]) - (c[..., 0] - c[..., 3])
+    ch = c[..., 3] - c[..., 0]
+    fx = np.maximum(np.abs(ch), np.abs(ch + (d2 - d1) / 4)) / s
+    fy = np.maximum(np.abs(d1), np.abs(d2)) / (4 * s)
+    tw = np.abs(d2 - d1) / (4 * s * s)
+    mag = np.maximum.reduce([np.abs(c[..., 0]), np.abs(c[..., 3]), np.abs(c[..., 0] + d1 / 4),
+                             np.abs(c[..., 3] + d2 / 4)])
+    return (E8 + 2.0 ** -11) * (fx + fy) + E8 * tw + 24 * U * np.maximum(mag, 1.0)
+
+
+@pytest.mark.parametrize("s", [4, 8])
+def test_spread_seiler_surface(s):
+    # bicubic 3D patches: point error per coordinate <= the largest bound of
+    # the four column cubics (the v stage is a convex combination of them)
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(700 + s)
+    ctrl = rng.uniform(-1, 1, size=(513, 4, 4, 3)).astype(np.float32)
+    got = bez.bez_eval_surface(_dev(torch, ctrl), 32, 32, variant=bez.Variant.TEX_SEILER, tex_spread=s)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy().reshape(513, -1, 3).astype(np.float64)
+    ref = oracle.surface(ctrl, 32, 32).reshape(513, -1, 3)
+    cols = np.moveaxis(ctrl, 1, -1)                          # [n][j][k][i]
+    per_k = _column_bound(cols, s).max(axis=1)               # [n][k]
+    bound = np.linalg.norm(per_k, axis=-1) + 64 * U
+    err = np.linalg.norm(got - ref, axis=-1).max(axis=1)
+    assert np.all(err <= bound), (err / bound).max()
+    e = normalised_error(got, ref)
+    if s == 8:
+        assert e.max() <= TEX_BAR
+    print(f"\nspread-{s} Seiler surface: max normalised error {e.max():.3g}")
+
+
+def test_spread_seiler_surface_meets_bar_on_the_tensor_workload():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez, synth
+    ctrl = synth.surfaces()[:4096]
+    for fmt in ("AUTO", "UNORM16"):
+        got = bez.bez_eval_surface(_dev(torch, ctrl), 32, 32, variant=bez.Variant.TEX_SEILER, tex_spread=8,
+                                   tex_format=bez.TexFormat[fmt])
+        torch.cuda.synchronize()
+        got = got.cpu().numpy().reshape(4096, -1, 3)
+        ref = oracle.surface(ctrl, 32, 32).reshape(4096, -1, 3)
+        e = normalised_error(got, ref)
+        assert e.max() <= TEX_BAR, (fmt, e.max())
+
+
+def test_spread_seiler_volume_meets_bar():
+    # tricubic scalar volumes N(0,1) on 16^3: error over the volume's value range
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez, synth
+    v = synth.volumes()[:512]
+    got = bez.bez_eval_volume(_dev(torch, v), 16, 16, 16, variant=bez.Variant.TEX_SEILER, tex_spread=8)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy().reshape(512, -1).astype(np.float64)
+    ref = oracle.volume(v, 16, 16, 16).reshape(512, -1)
+    span = np.maximum(ref.max(axis=1) - ref.min(axis=1), 2.0 ** -4)
+    e = np.abs(got - ref).max(axis=1) / span
+    assert e.max() <= TEX_BAR, e.max()
+    # a-priori: the u stage's read per (row, j) is one column cubic per channel; v and w are convex
+    cols = np.moveaxis(v[..., 0], 1, -1)                     # [n][j][l][i]
+    bound = _column_bound(cols, 8).max(axis=(1, 2)) + 64 * U * np.abs(v).max(axis=(1, 2, 3, 4))
+    assert np.all(np.abs(got - ref).max(axis=1) <= bound)
