@@ -212,7 +212,15 @@ bez_status bez_eval(bez_ctx ctx, const void* ctrl, int64_t n_curves, int degree,
  *
  * BEZ_VAR_TEX_DECASTELJAU evaluates quadratic chains (degree 2) from the
  * zig-zag texture; the free texel of each chain is chosen per component to
- * minimise the largest texel magnitude.  Register variants take any degree
+ * minimise the largest texel magnitude.  The read snaps the fraction both
+ * axes share to the filter's 1/256 grid, so both weights round alike;
+ * opts->tex_spread s >= 2 samples each 2x2 window on (s+1) x (s+1) texels
+ * (an (N s + 1) x (s + 1) texture) for about s times less weight error.
+ * Cubic chains (degree 3; Sec. 2.1: two quadratic chains front to back in a
+ * 3D texture) use an (N+1) x 2 x 2 texture read trilinearly along a 3D
+ * zig-zag: the three texels one flip from a segment's corner average to its
+ * second control point and the three two flips away to its third; spread 0
+ * or 1 only.  Register variants take any degree
  * 1..15 with (n_seg*degree+1)*dim <= 3072; the chain is staged in shared
  * memory.  Default (AUTO): register de Casteljau.
  */

@@ -282,6 +282,7 @@ bez_status bez_destroy(bez_ctx c)
     atlas_free(c->tex.seil2s);
     atlas_free(c->tex.seil3);
     atlas_free(c->tex.chain);
+    atlas_free(c->tex.chain3);
     atlas_free(c->tex.probe);
     atlas_free(c->tex.probe2);
     atlas_free(c->tex.surf3);
@@ -521,8 +522,11 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     const bool tex = var == BEZ_VAR_TEX_DECASTELJAU;
     if (var > BEZ_VAR_TEX_DECASTELJAU || var == BEZ_VAR_TENSOR)
         return fail(BEZ_ERR_UNSUPPORTED, "variant %d not available for chains", var);
-    if (tex && degree != 2)
-        return fail(BEZ_ERR_UNSUPPORTED, "zig-zag chain textures hold quadratic segments (degree %d)", degree);
+    if (tex && degree != 2 && degree != 3)
+        return fail(BEZ_ERR_UNSUPPORTED, "zig-zag chain textures hold quadratic or cubic segments (degree %d)",
+                    degree);
+    if (tex && degree == 3 && o->tex_spread > 1)
+        return fail(BEZ_ERR_UNSUPPORTED, "cubic zig-zag chains use the (N+1) x 2 x 2 layout (tex_spread 0 or 1)");
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
     if (tex && o->tex_format != BEZ_TEX_AUTO)
         return fail(BEZ_ERR_UNSUPPORTED, "chain textures use float4 / half4 texels (tex_format AUTO)");

@@ -72,6 +72,7 @@ struct TexState {
     Atlas seil2s; // 2D (s+1) x (s+1) spread Seiler tiles (degree 2, 3)
     Atlas seil3;  // 3D 2x2x2 Seiler tiles (degree 4, 5)
     Atlas chain;  // zig-zag C0 chain textures
+    Atlas chain3; // cubic zig-zag chain textures, (N+1) x 2 x 2 per chain
     Atlas probe;  // 2x2x2 weight probe
     Atlas probe2; // 2x2 weight probe (one-hot texels)
     Atlas surf3;  // bicubic surface tiles: four column cubics per 2x2x2 RGBA tile

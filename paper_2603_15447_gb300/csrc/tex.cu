@@ -858,9 +858,91 @@ __global__ void __launch_bounds__(kChainPackWarps * 32) k_chain_pack_spread(cons
     }
 }
 
+// Cubic C0 chains (Sec. 2.1, last paragraph: two quadratic chains front to
+// back in a 3D texture, interpolated to a cubic).  Column k of an
+// (N+1) x 2 x 2 texture has its corner at (y, z) = (k mod 2, k mod 2),
+// holding P_3k; the texels with y flipped (a_k), z flipped (b_k) and both
+// flipped (d_k) are free.  A trilinear read of columns k, k+1 from the
+// corner at (tau, tau, tau) weighs a texel by tau^m (1 - tau)^(3-m), m its
+// number of flips, so it evaluates the cubic whose control points are the
+// means of the texels with m = 0..3: P_3k, (a_k + b_k + d_(k+1)) / 3,
+// (d_k + a_(k+1) + b_(k+1)) / 3, P_3k+3 -- the three-texel form of the
+// E = (B + C) / 2 identity.  With s_k = a_k + b_k the constraints are
+// d_(k+1) = 3 P_(3k+1) - s_k and s_(k+1) = 3 P_(3k+2) - d_k: two
+// interleaved chains (s_0, d_1, s_2, ... and d_0, s_1, d_2, ...) with one
+// free start each, chosen per component like F_0 above (minimax), and
+// a_k = b_k = s_k / 2.  Each z slice is then a quadratic zig-zag chain (the
+// slice through a segment's corner reads a quadratic starting at P_3k, the
+// other one ending at P_3k+3), and the z weight lerps them.
+__global__ void k_chain3_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf, int fmt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_curves) return;
+    const int N = a.n_seg, dim = a.dim;
+    const int64_t base = c * (int64_t)(3 * N + 1) * dim;
+    auto P = [&](int i, int k) { return load_elem(a.ctrl, a.dtype, base + (int64_t)i * dim + k); };
+    // chain A: x_0 = s_0, x_(k+1) = 3 P[k even ? 3k+1 : 3k+2] - x_k;
+    // chain B: y_0 = d_0, y_(k+1) = 3 P[k even ? 3k+2 : 3k+1] - y_k
+    float xa0[4] = {0.f, 0.f, 0.f, 0.f}, yb0[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < dim; ++k) {
+        float ga = 0.f, gb = 0.f, amax = 0.f, amin = 0.f, bmax = 0.f, bmin = 0.f;
+        for (int s = 0; s < N; ++s) {
+            ga = 3.f * P((s & 1) ? 3 * s + 2 : 3 * s + 1, k) - ga;
+            gb = 3.f * P((s & 1) ? 3 * s + 1 : 3 * s + 2, k) - gb;
+            const float ha = (s & 1) ? ga : -ga, hb = (s & 1) ? gb : -gb;  // (-1)^(s+1) G_(s+1)
+            amax = fmaxf(amax, ha);
+            amin = fminf(amin, ha);
+            bmax = fmaxf(bmax, hb);
+            bmin = fminf(bmin, hb);
+        }
+        xa0[k] = -0.5f * (amax + amin);
+        yb0[k] = -0.5f * (bmax + bmin);
+    }
+    const int x0 = (int)(c % cw) * (N + 1), y0 = (int)(c / cw) * 2;
+    float4 X = make_float4(xa0[0], xa0[1], xa0[2], xa0[3]), Y = make_float4(yb0[0], yb0[1], yb0[2], yb0[3]);
+    auto stored = [&](float4 v) {
+        if (fmt != 1) return v;  // half texels: continue the recurrence from what the texture holds
+        return make_float4(__half2float(__float2half_rn(v.x)), __half2float(__float2half_rn(v.y)),
+                           __half2float(__float2half_rn(v.z)), __half2float(__float2half_rn(v.w)));
+    };
+    for (int s = 0; s <= N; ++s) {
+        const int cc = s & 1;
+        const float4 sk = (s & 1) ? Y : X, dk = (s & 1) ? X : Y;   // s_k, d_k
+        float4 ak = scale4(0.5f, sk);
+        ak = stored(ak);
+        const float4 bk = stored(sub4(sk, ak)), dks = stored(dk);
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < dim; ++k) p[k] = P(3 * s, k);
+        put(surf, fmt, x0 + s, y0 + cc, cc, true, make_float4(p[0], p[1], p[2], p[3]));
+        put(surf, fmt, x0 + s, y0 + 1 - cc, cc, true, ak);
+        put(surf, fmt, x0 + s, y0 + cc, 1 - cc, true, bk);
+        put(surf, fmt, x0 + s, y0 + 1 - cc, 1 - cc, true, dks);
+        if (s < N) {
+            // the stored s_k (a_k + b_k) and d_k continue the recurrences
+            const float4 ss = add4(ak, bk);
+            float m1[4] = {0.f, 0.f, 0.f, 0.f}, m2[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < dim; ++k) {
+                m1[k] = P(3 * s + 1, k);
+                m2[k] = P(3 * s + 2, k);
+            }
+            const float4 dn = make_float4(3.f * m1[0] - ss.x, 3.f * m1[1] - ss.y, 3.f * m1[2] - ss.z, 3.f * m1[3] - ss.w);
+            const float4 sn = make_float4(3.f * m2[0] - dks.x, 3.f * m2[1] - dks.y, 3.f * m2[2] - dks.z,
+                                          3.f * m2[3] - dks.w);
+            // next column: s_(k+1) = sn, d_(k+1) = dn; chain A holds s on even, d on odd columns
+            if ((s + 1) & 1) {
+                X = dn;
+                Y = sn;
+            } else {
+                X = sn;
+                Y = dn;
+            }
+        }
+    }
+}
+
 template <int TM>
 __device__ __forceinline__ float4 zigzag_eval(const CurveArgs& a, cudaTextureObject_t tex, int64_t c, int j,
-                                              uint32_t kc, float xb, float yb, int sp)
+                                              uint32_t kc, float xb, float yb, int sp, bool cubic = false)
 {
     const float ns = (float)a.n_seg;
     float t;
@@ -887,12 +969,16 @@ __device__ __forceinline__ float4 zigzag_eval(const CurveArgs& a, cudaTextureObj
     const bool odd = k & 1;
     const float iy = odd ? (float)sp - iu - (fq > 0.f ? 1.f : 0.f) : iu;
     const float fy = odd ? (fq > 0.f ? 1.f - fq : 0.f) : fq;
-    float4 P = tex2D<float4>(tex, (xb + ((float)(k * sp) + iu)) + fq, (yb + iy) + fy);
+    float4 P;
+    if (cubic)  // z runs like y: from slice k mod 2 to the other
+        P = tex3D<float4>(tex, (xb + ((float)(k * sp) + iu)) + fq, (yb + iy) + fy, (0.5f + iy) + fy);
+    else
+        P = tex2D<float4>(tex, (xb + ((float)(k * sp) + iu)) + fq, (yb + iy) + fy);
     if (TM == TM_ARRAY && t != t) P = make_float4(t, t, t, t);
     return P;
 }
 
-template <int TM, int OM>
+template <int TM, int OM, bool CUBIC = false>
 __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cudaTextureObject_t tex, int cw, int sp)
 {
     __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * 4 : 1];
@@ -910,7 +996,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
             for (int j0 = 0; j0 < n_t; j0 += 32) {
                 const int j = j0 + lane;
                 float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < n_t) P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp);
+                if (j < n_t) P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp, CUBIC);
                 const float pv[4] = {P.x, P.y, P.z, P.w};
                 for (int k = 0; k < dim; ++k) stage[lane * dim + k] = pv[k];
                 __syncwarp();
@@ -926,10 +1012,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
             float acc = 0.f;
             float4 first = make_float4(0.f, 0.f, 0.f, 0.f), prev = first;
             if (jb < je) {
-                first = prev = zigzag_eval<TM>(a, tex, c, jb, kc, xb, yb, sp);
+                first = prev = zigzag_eval<TM>(a, tex, c, jb, kc, xb, yb, sp, CUBIC);
 #pragma unroll 4
                 for (int j = jb + 1; j < je; ++j) {
-                    const float4 P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp);
+                    const float4 P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp, CUBIC);
                     acc += seg_len4(P, prev);
                     prev = P;
                 }
@@ -950,9 +1036,48 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
 // coordinates (integer + 8-bit fraction) are exact in FP32.
 constexpr int kChainMaxCoord = 32768;
 
+// Cubic chains: (N+1) x 2 x 2 texels per chain in a 3D atlas of depth 2.
+static LaunchResult launch_tex_chain3(const CurveArgs& a, int tm, int om, TexState& ts, cudaStream_t s,
+                                     const LaunchHooks& h)
+{
+    const int64_t wt64 = (int64_t)a.n_seg + 1;
+    const int max_w = ts.max3d < kChainMaxCoord ? ts.max3d : kChainMaxCoord;
+    if (wt64 > max_w) return {0, cudaErrorInvalidValue};
+    const int wt = (int)wt64;
+    const int fmt = a.dtype == 1 ? 1 : 0;
+    const int cw = tiles_per_row(a.n_curves, wt, max_w, 2);
+    const int64_t h_needed = (a.n_curves + cw - 1) / cw * 2;
+    if (h_needed > max_w || (int64_t)cw * wt > max_w) return {0, cudaErrorInvalidValue};
+    cudaError_t e = atlas_ensure(ts.chain3, cw * wt, (int)h_needed, 2, fmt);
+    if (e != cudaSuccess) return {0, e};
+    h.count(h.self);
+    k_chain3_pack<<<(unsigned)((a.n_curves + 127) / 128), 128, 0, s>>>(a, cw, ts.chain3.surf, fmt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return {1, e};
+    const void* kern;
+    if (om == OM_POINTS)
+        kern = tm == TM_ARRAY ? (const void*)k_chain_tex<TM_ARRAY, OM_POINTS, true>
+               : tm == TM_UNIFORM ? (const void*)k_chain_tex<TM_UNIFORM, OM_POINTS, true>
+                                  : (const void*)k_chain_tex<TM_HASH, OM_POINTS, true>;
+    else
+        kern = tm == TM_ARRAY ? (const void*)k_chain_tex<TM_ARRAY, OM_LENGTH, true>
+               : tm == TM_UNIFORM ? (const void*)k_chain_tex<TM_UNIFORM, OM_LENGTH, true>
+                                  : (const void*)k_chain_tex<TM_HASH, OM_LENGTH, true>;
+    const int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, (a.n_curves + kWarps - 1) / kWarps);
+    cudaTextureObject_t tex = ts.chain3.tex;
+    int cw_arg = cw, sp_arg = 1;
+    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg, (void*)&sp_arg};
+    h.count(h.self);
+    h.begin(h.self, s);
+    e = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);
+    h.end(h.self, s);
+    return {2, e};
+}
+
 LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, TexState& ts, cudaStream_t s,
                               const LaunchHooks& h)
 {
+    if (a.degree == 3) return launch_tex_chain3(a, tm, om, ts, s, h);
     const int sp = spread > 1 ? spread : 1;
     const int64_t wt64 = (int64_t)a.n_seg * sp + 1;
     const int max_w = ts.max2d_w < kChainMaxCoord ? ts.max2d_w : kChainMaxCoord;

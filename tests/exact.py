@@ -211,6 +211,57 @@ def zigzag_sample(T, t):
     return bilinear(tile, tau, y)
 
 
+# ------------------------------------------------------------- cubic zig-zag (Sec. 2.1, last paragraph)
+
+def zigzag3_texture(P, s0=None, d0=None, split=None):
+    """Texture T[z][y][col], 2 x 2 x (N+1), for a C0 chain of N cubics with
+    logical control points P[0..3N], read trilinearly along a 3D zig-zag.
+
+    Column k has the corner c_k = (y, z) = (k mod 2, k mod 2), which holds
+    P[3k]; the texel with y flipped (a_k), with z flipped (b_k) and with
+    both flipped (d_k) are free.  Trilinear filtering of the window of
+    columns k, k+1 read from corner c_k at (tau, tau, tau) weighs a texel by
+    tau^m (1 - tau)^(3-m), m its number of flips away from the corner, so
+    the window evaluates the cubic whose control points are the class means:
+    P[3k] (m = 0), (a_k + b_k + d_(k+1)) / 3 (m = 1), (d_k + a_(k+1) +
+    b_(k+1)) / 3 (m = 2), P[3k+3] (m = 3) -- the three-texel analogue of
+    E = (B + C) / 2 (Eq. 1-2).  With s_k = a_k + b_k the 2N constraints are
+    d_(k+1) = 3 P[3k+1] - s_k and s_(k+1) = 3 P[3k+2] - d_k on 2 (N+1)
+    unknowns: s_0, d_0 are free, and so is how each s_k splits into a_k,
+    b_k (split[k] = a_k - s_k / 2, default 0)."""
+    N = (len(P) - 1) // 3
+    s = [None] * (N + 1)
+    d = [None] * (N + 1)
+    s[0] = 2 * P[1] if s0 is None else s0
+    d[0] = P[2] if d0 is None else d0
+    for k in range(N):
+        d[k + 1] = 3 * P[3 * k + 1] - s[k]
+        s[k + 1] = 3 * P[3 * k + 2] - d[k]
+    T = [[[None] * (N + 1) for _ in range(2)] for _ in range(2)]
+    for k in range(N + 1):
+        c = k % 2
+        e = 0 if split is None else split[k]
+        a = s[k] / 2 + e
+        b = s[k] - a
+        T[c][c][k] = P[3 * k]
+        T[c][1 - c][k] = a            # y flipped
+        T[1 - c][c][k] = b            # z flipped
+        T[1 - c][1 - c][k] = d[k]     # both flipped
+    return T
+
+
+def zigzag3_sample(T, t):
+    """Trilinear read of the cubic zig-zag texture at global t in [0, N]:
+    segment k, local tau; x weight tau between columns k, k+1; y and z
+    weights tau on even segments (from row / slice 0) and 1 - tau on odd."""
+    N = len(T[0][0]) - 1
+    k = min(int(t), N - 1)
+    tau = t - k
+    w = tau if k % 2 == 0 else 1 - tau
+    tile = [[[T[z][y][k], T[z][y][k + 1]] for y in range(2)] for z in range(2)]
+    return trilinear(tile, tau, w, w)
+
+
 # ------------------------------------------------------------- Boehm (Sec. 2.2)
 
 def boehm_insert(U, P, p, u):

@@ -174,9 +174,13 @@ def test_chain_polyline_length_hash(variant):
 def test_chain_argument_errors():
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
-    ctrl = torch.zeros((2, 7, 3), device="cuda")
-    with pytest.raises(bez.BezError) as e:                  # zig-zag needs quadratic segments
-        bez.bez_eval_piecewise(ctrl, 2, 3, torch.zeros(4, device="cuda"), variant=bez.Variant.TEX_DECASTELJAU)
+    ctrl = torch.zeros((2, 9, 3), device="cuda")
+    with pytest.raises(bez.BezError) as e:                  # zig-zag textures: quadratic or cubic segments
+        bez.bez_eval_piecewise(ctrl, 2, 4, torch.zeros(4, device="cuda"), variant=bez.Variant.TEX_DECASTELJAU)
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:                  # cubic zig-zag: no spread layout
+        bez.bez_eval_piecewise(torch.zeros((2, 7, 3), device="cuda"), 2, 3, torch.zeros(4, device="cuda"),
+                               variant=bez.Variant.TEX_DECASTELJAU, tex_spread=2)
     assert e.value.status == bez.Status.UNSUPPORTED
     with pytest.raises(bez.BezError) as e:
         bez.bez_eval_piecewise(torch.zeros((2, 1, 3), device="cuda"), 0, 2, torch.zeros(4, device="cuda"))

@@ -15,8 +15,9 @@ import numpy as np
 import pytest
 
 import oracle
-from exact import (bernstein_exact, bilinear, decasteljau, decasteljau_texture, seiler_eval,
-                   seiler_terms, seiler_texture, trilinear, zigzag_sample, zigzag_texture)
+from exact import (bernstein_exact, bilinear, decasteljau, decasteljau_texture, lerp, seiler_eval,
+                   seiler_terms, seiler_texture, trilinear, zigzag_sample, zigzag_texture, zigzag3_sample,
+                   zigzag3_texture)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -233,6 +234,73 @@ def test_oracle_chain_equals_zigzag_texture(free):
         T = zigzag_texture([p[a] for p in P], t0=free)
         for j, tf in enumerate(ts):
             assert float(zigzag_sample(T, tf)) == got[0, j, a]
+
+
+@pytest.mark.parametrize("free", [(None, None, None), (F(3), F(-7, 2), None), (F(0), F(0), "random")])
+def test_oracle_cubic_chain_equals_zigzag3_texture(free):
+    # Sec. 2.1, last paragraph (cubic C0 chains from quadratic chains placed
+    # front to back in a 3D texture): the (N+1) x 2 x 2 texture of
+    # zigzag3_texture, read trilinearly along its zig-zag path, equals the
+    # oracle's cubic chain for any choice of the free texels
+    rng = random.Random(31)
+    N, dim = 5, 2
+    P = [[F(rng.randint(-8, 8)) for _ in range(dim)] for _ in range(3 * N + 1)]
+    ctrl = np.array([[[float(v) for v in p] for p in P]])
+    ts = [F(k, 16) for k in range(0, 16 * N + 1)]
+    got = oracle.chain(ctrl, N, 3, np.array([float(x) for x in ts]))
+    s0, d0, split = free
+    for a in range(dim):
+        sp = [F(rng.randint(-5, 5), 3) for _ in range(N + 1)] if split == "random" else None
+        T = zigzag3_texture([p[a] for p in P], s0=s0, d0=d0, split=sp)
+        for j, tf in enumerate(ts):
+            assert float(zigzag3_sample(T, tf)) == got[0, j, a]
+
+
+def test_zigzag3_slices_are_quadratic_zigzag_chains():
+    # each z slice of the cubic texture, read bilinearly along the 2D
+    # zig-zag path, is a C0 chain of quadratics (the "two quadratic chains
+    # front to back"), and lerping the slice read that starts at a segment's
+    # corner with the other one gives the cubic
+    rng = random.Random(32)
+    N = 6
+    P = [F(rng.randint(-8, 8)) for _ in range(3 * N + 1)]
+    T = zigzag3_texture(P, s0=F(1), d0=F(-2))
+    ts = [F(k, 8) for k in range(0, 8 * N + 1)]
+    for zs in range(2):
+        sl = T[zs]
+        vals = {}
+        for tf in ts:
+            k = min(int(tf), N - 1)
+            tau = tf - k
+            y = tau if k % 2 == 0 else 1 - tau
+            tile = [[sl[0][k], sl[0][k + 1]], [sl[1][k], sl[1][k + 1]]]
+            vals.setdefault(tf, []).append(bilinear(tile, tau, y))
+        # continuity at the joints: segment k at tau = 1 meets segment k+1 at tau = 0
+        for k in range(1, N):
+            left = bilinear([[sl[0][k - 1], sl[0][k]], [sl[1][k - 1], sl[1][k]]], F(1), F(1) if (k - 1) % 2 == 0 else F(0))
+            right = bilinear([[sl[0][k], sl[0][k + 1]], [sl[1][k], sl[1][k + 1]]], F(0), F(0) if k % 2 == 0 else F(1))
+            assert left == right
+    for tf in ts:
+        k = min(int(tf), N - 1)
+        tau = tf - k
+        y = tau if k % 2 == 0 else 1 - tau
+        front, back = (T[0], T[1]) if k % 2 == 0 else (T[1], T[0])
+        qf = bilinear([[front[0][k], front[0][k + 1]], [front[1][k], front[1][k + 1]]], tau, y)
+        qb = bilinear([[back[0][k], back[0][k + 1]], [back[1][k], back[1][k + 1]]], tau, y)
+        assert lerp(qf, qb, tau) == bernstein_exact(P[3 * k:3 * k + 4], tau)
+
+
+def test_segment_quadratics_front_to_back_are_not_a_c0_chain():
+    # the literal reading -- the front slice holding each segment's own
+    # quadratic (P_3k, P_3k+1, P_3k+2) and the back slice (P_3k+1, P_3k+2,
+    # P_3k+3), as in the single-cubic tile of Sec. 2 -- needs consecutive
+    # front quadratics to meet (P_3k+2 == P_3k+3), which a general cubic chain
+    # violates, so those quadratics cannot share zig-zag columns; the
+    # construction above stores other quadratics whose z-lerp is the cubic
+    P = [F(v) for v in (0, 3, -2, 5, 1, 4, -1)]           # two cubic segments
+    front_end_0, front_start_1 = P[2], P[3]
+    back_end_0, back_start_1 = P[3], P[4]
+    assert front_end_0 != front_start_1 and back_end_0 != back_start_1
 
 
 def test_chain_continuity_and_segments():

@@ -351,3 +351,84 @@ def test_spread_seiler_volume_meets_bar():
     cols = np.moveaxis(v[..., 0], 1, -1)                     # [n][j][l][i]
     bound = _column_bound(cols, 8).max(axis=(1, 2)) + 64 * U * np.abs(v).max(axis=(1, 2, 3, 4))
     assert np.all(np.abs(got - ref).max(axis=1) <= bound)
+
+
+# ---------------------------------------------------------------- cubic zig-zag chains
+
+def _zigzag3_texels(P):
+    """[N+1] columns of the cubic zig-zag texture of one chain (as the
+    packer builds it: minimax free starts, a_k = b_k = s_k / 2); returns
+    texels [N+1][4][dim] (corner, a, b, d)."""
+    P = P.astype(np.float64)
+    N = (P.shape[0] - 1) // 3
+    dim = P.shape[1]
+    starts = []
+    for chain in (0, 1):
+        G = np.zeros((N + 1, dim))
+        for k in range(N):
+            idx = (3 * k + 1 if k % 2 == 0 else 3 * k + 2) if chain == 0 else (3 * k + 2 if k % 2 == 0 else 3 * k + 1)
+            G[k + 1] = 3 * P[idx] - G[k]
+        H = G * np.array([(-1) ** k for k in range(N + 1)])[:, None]
+        starts.append(-(H.max(axis=0) + H.min(axis=0)) / 2)
+    s = np.zeros((N + 1, dim))
+    d = np.zeros((N + 1, dim))
+    s[0], d[0] = starts[0], starts[1]
+    for k in range(N):
+        d[k + 1] = 3 * P[3 * k + 1] - s[k]
+        s[k + 1] = 3 * P[3 * k + 2] - d[k]
+    return np.stack([P[0::3], s / 2, s / 2, d], 1)
+
+
+def test_cubic_zigzag_chain_texture():
+    # Sec. 2.1 last paragraph: cubic C0 chains from the 3D zig-zag texture.
+    # A trilinear read moves weight between the 8 texels of a window by at
+    # most 6 x 2^-8 in total (measured 5.6 x 2^-8), so a point is within
+    # 3 x 2^-8 of the window's texel range of the exact cubic
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(800)
+    n_seg, n = 12, 301
+    ctrl = rng.uniform(-1, 1, size=(n, 3 * n_seg + 1, 3)).astype(np.float32)
+    t = (rng.uniform(0, 1, (n, 257)) * n_seg).astype(np.float32)
+    t[:, :4] = [0.0, n_seg, 5.0, 6.0]
+    got = bez.bez_eval_piecewise(_dev(torch, ctrl), n_seg, 3, _dev(torch, t), variant=bez.Variant.TEX_DECASTELJAU,
+                                 t_mode=bez.TMode.PER_CURVE)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    ref = oracle.chain(ctrl, n_seg, 3, t)
+    np.testing.assert_array_equal(got[:, 0], ctrl[:, 0])
+    np.testing.assert_array_equal(got[:, 1], ctrl[:, -1])
+    err = np.linalg.norm(got - ref, axis=-1)
+    k = np.clip(np.floor(t), 0, n_seg - 1).astype(int)
+    bound = np.empty_like(err)
+    for c in range(n):
+        T = _zigzag3_texels(ctrl[c])                         # [N+1][4][dim]
+        win = np.concatenate([T[:-1], T[1:]], axis=1)        # [N][8][dim]
+        rng_w = np.linalg.norm(win.max(axis=1) - win.min(axis=1), axis=-1)
+        mag = np.abs(T).max()
+        bound[c] = 3 * 2.0 ** -8 * rng_w[k[c]] + 32 * U * max(mag, 1.0) * np.sqrt(3)
+    assert np.all(err <= bound), (err / bound).max()
+    print(f"\ncubic zig-zag: max normalised error {normalised_error(got, ref).max():.3g}, "
+          f"max error / bound {(err / bound).max():.3f}")
+
+
+def test_cubic_zigzag_lengths_and_hash():
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    rng = np.random.default_rng(801)
+    n_seg, n, n_t = 16, 129, 2048
+    ctrl = rng.uniform(-1, 1, size=(n, 3 * n_seg + 1, 3)).astype(np.float32)
+    c = _dev(torch, ctrl)
+    pts = bez.bez_eval_piecewise(c, n_seg, 3, None, n_t=n_t, variant=bez.Variant.TEX_DECASTELJAU,
+                                 t_mode=bez.TMode.HASH, seed=5, stream_id=9)
+    L = bez.bez_eval_piecewise(c, n_seg, 3, None, n_t=n_t, variant=bez.Variant.TEX_DECASTELJAU,
+                               t_mode=bez.TMode.HASH, seed=5, stream_id=9, out_mode=bez.OutMode.POLYLINE_LENGTH)
+    torch.cuda.synchronize()
+    u = oracle.hash_t(5, 9, 0, n, n_t)
+    t = (np.float32(n_seg) * u.astype(np.float32)).astype(np.float32)
+    ref = oracle.chain(ctrl, n_seg, 3, t)
+    e = normalised_error(pts.cpu().numpy(), ref)
+    # the length kernel sums the points the points kernel returns
+    Lp = oracle.polyline_length(pts.cpu().numpy().astype(np.float64))
+    np.testing.assert_allclose(L.cpu().numpy(), Lp, rtol=(n_t / 32 + 16) * U * 4, atol=1e-6)
+    print(f"\ncubic zig-zag (hashed): max normalised error {e.max():.3g}")
