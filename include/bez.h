@@ -350,7 +350,12 @@ typedef struct bez_batch_opts {
     int32_t setup_each_launch; /* re-extract spline spans on every launch        */
     int32_t use_graph;         /* capture setup + evaluation in a CUDA graph     */
     int32_t chunk;             /* samples per work item (multiple of 256), 0 = default / tuned */
-    int32_t schedule;          /* -1 default / tuned, 0 static, 1 atomic queue   */
+    int32_t schedule;          /* -1 default / tuned, 0 static, 1 atomic queue,   *
+                                * 2 atomic queue with the GPU partitioned between *
+                                * the curve classes: every class kernel on its own *
+                                * stream with a grid sized to its share of the     *
+                                * work, measured per class at creation, so all     *
+                                * classes run side by side and finish together    */
     int32_t threads;           /* threads per block (128, 256), 0 = default / tuned */
     int32_t repr;              /* -1 default / tuned, 0 Bezier points (de Casteljau),
                                 * 1 power basis about 1/2 (Horner)              */
@@ -363,7 +368,8 @@ bez_status bez_batch_create(bez_ctx ctx, const bez_curve_desc* desc, int64_t n_c
                             float* out_pool, int64_t out_len, const bez_batch_opts* bopts, void* stream,
                             bez_batch* batch);
 bez_status bez_batch_launch(bez_batch batch, void* stream);
-/* chosen launch shape: chunk, schedule (0 static, 1 atomic), threads, span representation */
+/* chosen launch shape: chunk, schedule (0 static, 1 atomic, 2 atomic partitioned), threads,
+ * span representation */
 bez_status bez_batch_config(bez_batch batch, int32_t* chunk, int32_t* schedule, int32_t* threads, int32_t* repr);
 bez_status bez_batch_destroy(bez_batch batch);
 bez_status bez_eval_batch(bez_ctx ctx, const bez_curve_desc* desc, int64_t n_curves, int dim, const float* ctrl_pool,

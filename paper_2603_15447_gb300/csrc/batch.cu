@@ -442,6 +442,19 @@ static const void* class_kernel(int cls)
     }
 }
 
+static size_t batch_smem(const BatchArgs& a, int threads)
+{
+    return (size_t)(threads / 32) * 32 * (kRun * a.dim + 1) * sizeof(float);
+}
+
+int batch_full_grid(const BatchArgs& a, int threads, int sm_count, int cls)
+{
+    const void* kern = a.repr == 1 ? class_kernel<1>(cls) : class_kernel<0>(cls);
+    const int64_t count = a.class_start[cls + 1] - a.class_start[cls];
+    const int wpb = threads / 32;
+    return persistent_grid(kern, threads, batch_smem(a, threads), sm_count, (count + wpb - 1) / wpb);
+}
+
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
                          const BatchStreams* bs, const LaunchHooks& h, int* launches)
 {
@@ -458,7 +471,13 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
         e = cudaMemsetAsync(a.counter, 0, kBatchClasses * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = (size_t)(threads / 32) * 32 * (kRun * a.dim + 1) * sizeof(float);
+    const size_t smem = batch_smem(a, threads);
+    // Partitioned (atomic schedule): every class on a stream of its own with
+    // a grid sized to its share of the measured work, so all classes are
+    // resident together and finish at about the same time, each hiding the
+    // others' latency; otherwise persistent grids on 4 shared streams.
+    const bool part = a.partition != 0 && a.schedule != 0;
+    const int nside = part ? kBatchSideStreams : kBatchSharedSideStreams;
     int active = 0;
     for (int cls = 0; cls < kBatchClasses; ++cls) active += a.class_start[cls + 1] > a.class_start[cls];
     if (active == 0) return cudaSuccess;
@@ -467,7 +486,7 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
     h.begin(h.self, s);
     if (fork) {
         if ((e = cudaEventRecord(bs->fork, s)) != cudaSuccess) return e;
-        for (int i = 0; i < kBatchSideStreams; ++i)
+        for (int i = 0; i < nside; ++i)
             if ((e = cudaStreamWaitEvent(bs->side[i], bs->fork, 0)) != cudaSuccess) return e;
     }
     e = cudaSuccess;
@@ -475,12 +494,13 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
     for (int cls = 0; cls < kBatchClasses && e == cudaSuccess; ++cls) {
         const int64_t first = a.class_start[cls], count = a.class_start[cls + 1] - first;
         if (count <= 0) continue;
-        const int lane_of = fork ? m % (kBatchSideStreams + 1) : 0;
+        const int lane_of = fork ? m % (nside + 1) : 0;
         ++m;
         cudaStream_t cs = lane_of == 0 ? s : bs->side[lane_of - 1];
         const void* kern = a.repr == 1 ? class_kernel<1>(cls) : class_kernel<0>(cls);
         const int wpb = threads / 32;
         int grid = persistent_grid(kern, threads, smem, sm_count, (count + wpb - 1) / wpb);
+        if (part && a.class_grid[cls] > 0) grid = a.class_grid[cls];
         if (a.schedule == 0) {
             // blocks of kItemsPerWarp items per warp, scheduled by the hardware
             const int64_t g = (count + (int64_t)wpb * kItemsPerWarp - 1) / ((int64_t)wpb * kItemsPerWarp);
@@ -494,7 +514,7 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
     }
     if (fork) {
         // every side stream waited on the fork (and so joined a capture): join all of them back
-        for (int i = 0; i < kBatchSideStreams; ++i) {
+        for (int i = 0; i < nside; ++i) {
             cudaError_t e2 = cudaEventRecord(bs->join[i], bs->side[i]);
             if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, bs->join[i], 0);
             if (e == cudaSuccess) e = e2;

@@ -24,6 +24,7 @@ struct Shape {
     int schedule = 0;
     int threads = 256;
     int repr = 1;  // 0 Bezier points + de Casteljau, 1 centred power basis + Horner
+    int partition = 0;  // atomic schedule: classes share the GPU by measured work (grids set by tune_partition)
 };
 
 void no_count(void*) {}
@@ -65,8 +66,10 @@ void load_cache_file(const char* path)
         field("\"schedule\"", &sh.schedule);
         field("\"threads\"", &sh.threads);
         field("\"repr\"", &sh.repr);
+        field("\"partition\"", &sh.partition);
         if (sh.chunk > 0 && sh.chunk % 256 == 0 && (sh.schedule == 0 || sh.schedule == 1) &&
-            (sh.threads == 128 || sh.threads == 256) && (sh.repr == 0 || sh.repr == 1))
+            (sh.threads == 128 || sh.threads == 256) && (sh.repr == 0 || sh.repr == 1) &&
+            (sh.partition == 0 || (sh.partition == 1 && sh.schedule == 1)))
             g_tune_cache[key] = sh;
         pos = b1 + 1;
     }
@@ -80,9 +83,9 @@ void save_cache_file(const char* path)
     fprintf(f, "{\n");
     size_t i = 0;
     for (auto& kv : g_tune_cache) {
-        fprintf(f, "  \"%s\": {\"chunk\": %d, \"schedule\": %d, \"threads\": %d, \"repr\": %d}%s\n",
+        fprintf(f, "  \"%s\": {\"chunk\": %d, \"schedule\": %d, \"threads\": %d, \"repr\": %d, \"partition\": %d}%s\n",
                 kv.first.c_str(), kv.second.chunk, kv.second.schedule, kv.second.threads, kv.second.repr,
-                ++i < g_tune_cache.size() ? "," : "");
+                kv.second.partition, ++i < g_tune_cache.size() ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
@@ -217,6 +220,7 @@ bez_status apply_shape(bez_batch b, const Shape& sh, cudaStream_t s)
     const bool repr_changed = b->a.repr != sh.repr;
     b->a.schedule = sh.schedule;
     b->a.grab = 4;
+    b->a.partition = 0;
     b->a.repr = sh.repr;
     b->a.op_pool = sh.repr == 1 ? b->d_ops_c : b->d_ops;
     b->shape = sh;
@@ -252,6 +256,62 @@ bez_status time_shape(bez_batch b, const Shape& sh, cudaStream_t s, float* ms_ou
     return BEZ_OK;
 }
 
+// Time `a` (a copy of the plan's arguments): median of 3 after a warm-up.
+bez_status time_args(bez_batch b, const BatchArgs& a, bool with_setup, cudaStream_t s, float* ms_out)
+{
+    const LaunchHooks h{no_count, no_event, no_event, nullptr, b->ctx->sm_count};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float t[3];
+    int k = 0;
+    cudaError_t e = launch_batch(a, b->shape.threads, b->ctx->sm_count, with_setup, s, streams_of(b), h, &k);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+        cudaEventRecord(e0, s);
+        e = launch_batch(a, b->shape.threads, b->ctx->sm_count, with_setup, s, streams_of(b), h, &k);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+    std::sort(t, t + 3);
+    *ms_out = t[1];
+    return BEZ_OK;
+}
+
+// Partition the GPU between the class kernels (atomic schedule, shape
+// already applied): time every class alone on the whole GPU, give class k
+// ceil(G_k t_k / sum t) blocks (G_k its persistent grid), so that all
+// classes run side by side and end together.  Sets b->a.partition and the
+// grids; `ms_out` is the partitioned launch's time.
+bez_status tune_partition(bez_batch b, cudaStream_t s, float* ms_out)
+{
+    BatchArgs& a = b->a;
+    float tc[kBatchClasses] = {};
+    float total = 0.f;
+    for (int cls = 0; cls < kBatchClasses; ++cls) {
+        const int64_t first = a.class_start[cls], last = a.class_start[cls + 1];
+        if (last <= first) continue;
+        BatchArgs one = a;
+        one.partition = 0;
+        for (int k = 0; k < 16; ++k) one.class_start[k] = k <= cls ? first : last;
+        bez_status st = time_args(b, one, false, s, &tc[cls]);
+        if (st != BEZ_OK) return st;
+        total += tc[cls];
+    }
+    for (int k = 0; k < 16; ++k) a.class_grid[k] = 0;
+    for (int cls = 0; cls < kBatchClasses && total > 0.f; ++cls) {
+        if (tc[cls] <= 0.f) continue;
+        const int full = batch_full_grid(a, b->shape.threads, b->ctx->sm_count, cls);
+        const int g = (int)std::ceil((double)full * tc[cls] / total);
+        a.class_grid[cls] = std::max(1, std::min(full, g));
+    }
+    a.partition = 1;
+    return time_args(b, a, b->setup_each, s, ms_out);
+}
+
 bez_status autotune(bez_batch b, cudaStream_t s)
 {
     const char* path = getenv("BEZ_AUTOTUNE_CACHE");
@@ -259,7 +319,15 @@ bez_status autotune(bez_batch b, cudaStream_t s)
         std::lock_guard<std::mutex> g(g_tune_mu);
         if (path) load_cache_file(path);
         auto it = g_tune_cache.find(b->key);
-        if (it != g_tune_cache.end()) return apply_shape(b, it->second, s);
+        if (it != g_tune_cache.end()) {
+            const Shape sh = it->second;
+            bez_status st = apply_shape(b, sh, s);
+            if (st != BEZ_OK || !sh.partition) return st;
+            float ms = 0.f;
+            st = tune_partition(b, s, &ms);
+            b->shape.partition = 1;
+            return st;
+        }
     }
     Shape best;
     float best_ms = 1e30f;
@@ -276,12 +344,26 @@ bez_status autotune(bez_batch b, cudaStream_t s)
                     best = sh;
                 }
             }
+    bez_status st = apply_shape(b, best, s);
+    if (st != BEZ_OK) return st;
+    if (best.schedule == 1) {
+        // the best shape with the GPU partitioned between the classes
+        float ms = 0.f;
+        st = tune_partition(b, s, &ms);
+        if (st != BEZ_OK) return st;
+        if (ms < best_ms) {
+            best.partition = 1;
+            b->shape.partition = 1;
+        } else {
+            b->a.partition = 0;
+        }
+    }
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_cache[b->key] = best;
         if (path) save_cache_file(path);
     }
-    return apply_shape(b, best, s);
+    return BEZ_OK;
 }
 
 void free_batch(bez_batch b)
@@ -523,7 +605,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     b->setup_each = bo ? bo->setup_each_launch != 0 : true;
     b->use_graph = bo ? bo->use_graph != 0 : false;
     char key[160];
-    snprintf(key, sizeof(key), "batch-v2:setup%d:n%d:dim%d:mix%lld/%lld/%lld:deg%d:s%d", b->setup_each ? 1 : 0,
+    snprintf(key, sizeof(key), "batch-v3:setup%d:n%d:dim%d:mix%lld/%lld/%lld:deg%d:s%d", b->setup_each ? 1 : 0,
              log2_bucket((double)n_curves), dim,
              (long long)(n_curves ? 100 * n_type[0] / n_curves : 0), (long long)(n_curves ? 100 * n_type[1] / n_curves : 0),
              (long long)(n_curves ? 100 * n_type[2] / n_curves : 0), n_curves ? (int)std::lround((double)deg_sum / n_curves) : 0,
@@ -533,6 +615,8 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     Shape sh;
     if (bo && bo->chunk > 0) sh.chunk = bo->chunk;
     if (bo && (bo->schedule == 0 || bo->schedule == 1)) sh.schedule = bo->schedule;
+    const bool want_partition = bo && bo->schedule == 2;  // atomic queue, GPU partitioned between the classes
+    if (want_partition) sh.schedule = 1;
     if (bo && (bo->threads == 128 || bo->threads == 256)) sh.threads = bo->threads;
     if (bo && (bo->repr == 0 || bo->repr == 1)) sh.repr = bo->repr;
     if (bo && bo->chunk > 0 && bo->chunk % 256 != 0) {
@@ -545,6 +629,11 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     }
     bez_status st = BEZ_OK;
     if (st == BEZ_OK) st = (bo && bo->autotune) ? autotune(b, s) : apply_shape(b, sh, s);
+    if (st == BEZ_OK && want_partition && !(bo && bo->autotune)) {
+        float ms = 0.f;
+        st = tune_partition(b, s, &ms);
+        b->shape.partition = 1;
+    }
     if (st == BEZ_OK && b->use_graph) {
         cudaStream_t cs = nullptr;
         cudaGraph_t graph = nullptr;
@@ -600,7 +689,7 @@ bez_status bez_batch_config(bez_batch b, int32_t* chunk, int32_t* schedule, int3
     if (!b) return fail(BEZ_ERR_INVALID_ARG, "null batch");
     if (repr) *repr = b->shape.repr;
     if (chunk) *chunk = b->shape.chunk;
-    if (schedule) *schedule = b->shape.schedule;
+    if (schedule) *schedule = b->shape.schedule == 1 && b->shape.partition ? 2 : b->shape.schedule;
     if (threads) *threads = b->shape.threads;
     return BEZ_OK;
 }

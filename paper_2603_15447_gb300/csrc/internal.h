@@ -199,7 +199,8 @@ static_assert(sizeof(BatchItem) == 48, "BatchItem is read as three 16-byte loads
 
 // Side streams of a batch: class evaluators run concurrently between a fork
 // and a join on the launching stream (also inside graph capture).
-constexpr int kBatchSideStreams = 3;
+constexpr int kBatchSideStreams = 14;  // one stream per class when the GPU is partitioned between them
+constexpr int kBatchSharedSideStreams = 3;  // otherwise classes share the main stream and 3 side streams
 struct BatchStreams {
     cudaStream_t side[kBatchSideStreams];
     cudaEvent_t fork;
@@ -240,6 +241,8 @@ struct BatchArgs {
     int32_t schedule;            // 0 static round-robin, 1 atomic queue
     int32_t grab;                // items taken per atomic
     void* counter;               // one 8-byte work counter per class (atomic schedule)
+    int32_t partition;           // atomic schedule: class k launches class_grid[k] blocks on a stream of its own
+    int32_t class_grid[16];
 };
 // row stride (entries) of a degree-p extraction operator in the batch pool:
 // p + 1 rounded up to even, so every row starts on a 16-byte boundary
@@ -252,6 +255,8 @@ constexpr int kBatchClasses = 15;  // 7 degrees x {integral, rational} for 3D cu
 int batch_item_class(const bez_curve_desc& d, int dim);
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
                          const BatchStreams* bs, const LaunchHooks& h, int* launches);
+// the grid a class kernel gets without partitioning (persistent: every SM full)
+int batch_full_grid(const BatchArgs& a, int threads, int sm_count, int cls);
 
 // Peak microbenchmarks (peaks.cu): kind 0 FP32 FMA lane-ops/s, 1..4 texture
 // fetches/s (2D float4, 2D half4, 3D float4, 3D half4), 5 store GB/s,

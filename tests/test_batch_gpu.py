@@ -73,7 +73,8 @@ def _desc(w):
 
 
 @pytest.mark.parametrize("schedule,chunk,threads,repr", [(0, 256, 256, 1), (1, 512, 128, 0), (0, 2048, 128, 1),
-                                                          (1, 1024, 256, 1), (0, 512, 256, 0)])
+                                                          (1, 1024, 256, 1), (0, 512, 256, 0), (2, 512, 128, 1),
+                                                          (2, 256, 256, 0)])
 def test_batch_plan_graph_replay(workload, schedule, chunk, threads, repr):
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez
@@ -123,14 +124,14 @@ def test_batch_autotune_and_static_spans(workload, tmp_path, monkeypatch):
     ctrl, wts, out = _pools(torch, w)
     b = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, autotune=True, setup_each_launch=False)
     cfg = b.config()
-    assert cfg["chunk"] in (256, 512, 1024, 2048) and cfg["schedule"] in (0, 1) and cfg["threads"] in (128, 256)
+    assert cfg["chunk"] in (256, 512, 1024, 2048) and cfg["schedule"] in (0, 1, 2) and cfg["threads"] in (128, 256)
     out.fill_(float("nan"))
     b.launch()
     torch.cuda.synchronize()
     assert _check_all(out.cpu().numpy(), ref, w) <= FP32_BAR
     b.close()
     text = (tmp_path / "tune.json").read_text()
-    assert '"chunk"' in text and "batch-v2:setup0" in text
+    assert '"chunk"' in text and "batch-v3:setup0" in text and '"partition"' in text
     # a second plan of the same shape and setup mode takes the cached choice
     b2 = bez.Batch(_desc(w), w["dim"], ctrl, wts, out, autotune=True, setup_each_launch=False)
     assert b2.config() == cfg
@@ -195,3 +196,44 @@ def test_batch_grid_values_are_exact_quotients(repr):
                 np.testing.assert_array_equal(pts[:, k], t)
         else:
             assert np.abs(pts - t[:, None]).max() <= 1e-7
+
+
+def test_batch_full_sample_range_and_long_nurbs():
+    # the batch workload's full range of sample counts (16..4096, log-uniform)
+    # and degree-7 NURBS with 64 control points and long runs of samples per
+    # curve (several work items each, many spans per item), every curve
+    # against the oracle, under the tuned shape and the partitioned schedule
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez, synth
+    w = synth.batch(n_curves=1500, max_samples=4096, seed=synth.BASE_SEED + 77)
+    # a block of long degree-7 NURBS: 64 control points, 4096 and 3000 samples
+    rng = np.random.default_rng(77)
+    extra = 24
+    base_c, base_w, base_o = len(w["ctrl_pool"]), len(w["weight_pool"]), w["out_len"]
+    ns_extra = np.where(np.arange(extra) % 2 == 0, 4096, 3000).astype(np.int32)
+    ctrl_x = rng.uniform(-1, 1, extra * 64 * 3).astype(np.float32)
+    w_x = rng.uniform(0.5, 2, extra * 64).astype(np.float32)
+    w = dict(w)
+    w["type"] = np.concatenate([w["type"], np.full(extra, 2, np.int32)])
+    w["degree"] = np.concatenate([w["degree"], np.full(extra, 7, np.int32)])
+    w["n_ctrl"] = np.concatenate([w["n_ctrl"], np.full(extra, 64, np.int32)])
+    w["n_samples"] = np.concatenate([w["n_samples"], ns_extra])
+    w["ctrl_off"] = np.concatenate([w["ctrl_off"], base_c + np.arange(extra, dtype=np.int64) * 192])
+    w["weight_off"] = np.concatenate([w["weight_off"], base_w + np.arange(extra, dtype=np.int64) * 64])
+    w["out_off"] = np.concatenate([w["out_off"], base_o + np.concatenate([[0], np.cumsum(ns_extra[:-1] * 3)])])
+    w["ctrl_pool"] = np.concatenate([w["ctrl_pool"], ctrl_x])
+    w["weight_pool"] = np.concatenate([w["weight_pool"], w_x])
+    w["out_len"] = int(base_o + ns_extra.sum() * 3)
+    assert w["n_samples"].max() >= 4000 and w["n_samples"].min() <= 20
+    ref = _reference(w)
+    ctrl, wts, out = _pools(torch, w)
+    for kw in (dict(autotune=True), dict(schedule=2, chunk=512, threads=128, repr=1),
+               dict(schedule=2, chunk=1024, threads=256, repr=0)):
+        b = bez.Batch(_desc(w), 3, ctrl, wts, out, **kw)
+        out.fill_(float("nan"))
+        b.launch()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert _check_all(got, ref, w) <= FP32_BAR, kw
+        b.close()
