@@ -369,3 +369,19 @@ def test_hash_parameters_uniform_and_fp32_exact():
         y = (y * inv1) % M
         y = unxorshift(y, 16)
         assert y == x
+
+
+def test_hash_avalanche():
+    # a property of the mixer rather than its formula: flipping any one input
+    # bit flips every output bit with probability close to 1/2 (a weak or
+    # mistyped multiplier leaves some bit pairs far from it); 4096 random
+    # inputs, so the sampling error of each probability is about 0.008
+    rng = np.random.default_rng(15)
+    xs = [int(v) for v in rng.integers(0, 2 ** 32, 4096, dtype=np.uint64)]
+    base = np.array([oracle.lowbias32(x) for x in xs], np.uint64)
+    p = np.zeros((32, 32))
+    for i in range(32):
+        flipped = np.array([oracle.lowbias32(x ^ (1 << i)) for x in xs], np.uint64)
+        diff = base ^ flipped
+        p[i] = [(((diff >> np.uint64(j)) & np.uint64(1)).astype(np.float64)).mean() for j in range(32)]
+    assert np.abs(p - 0.5).max() < 0.05, np.abs(p - 0.5).max()

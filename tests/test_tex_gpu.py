@@ -294,6 +294,40 @@ def test_texture_bicubic_surface(variant, dim, nu, nv, half):
 
 
 @pytest.mark.parametrize("variant", ["TEX_DECASTELJAU", "TEX_SEILER"])
+@pytest.mark.parametrize("fmt", ["AUTO", "UNORM16"])
+def test_texture_surface_warps_loop_over_patches(variant, fmt):
+    # With at most 32 rows a warp issues the filtered reads of its next patch
+    # before sweeping the current one.  20,001 patches on a 5 x 3 grid is more
+    # than the resident warps (8 a block x 4 blocks an SM x the SM count), so
+    # every warp handles several patches and uses the prefetched rows; each
+    # patch is checked against the oracle at the tolerance of the tests above.
+    torch = need_gpu()
+    from paper_2603_15447_gb300 import bez
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 20001
+    assert n > 8 * 4 * n_sm
+    rng = np.random.default_rng(7300 + (fmt == "AUTO"))
+    ctrl = rng.uniform(-1, 1, (n, 4, 4, 3)).astype(np.float32)
+    got = bez.bez_eval_surface(torch.from_numpy(ctrl).cuda(), 5, 3, variant=bez.Variant[variant],
+                               tex_format=bez.TexFormat[fmt]).cpu().numpy().astype(np.float64)
+    ref = oracle.surface(ctrl, 5, 3)
+    b = ctrl.astype(np.float64)
+    if variant == "TEX_DECASTELJAU":
+        tiles = b                                                          # [n][i][j][k]
+        axes = 3
+    else:
+        d1 = 3 * (b[:, 1] - b[:, 0]) - (b[:, 3] - b[:, 0])
+        d2 = 3 * (b[:, 2] - b[:, 3]) - (b[:, 0] - b[:, 3])
+        tiles = np.stack([b[:, 0], b[:, 3], b[:, 0] + d1, b[:, 3] + d2], 1)
+        axes = 2
+    col_range = (tiles.max(axis=1) - tiles.min(axis=1)).max(axis=1)        # [n][dim]
+    mag = np.abs(tiles).max(axis=(1, 2))
+    q = 2.0 ** -17 if fmt == "UNORM16" else 0.0                             # half a code of the tile's range
+    tol = axes * WERR * col_range + q * col_range + 8 * U * mag
+    assert np.all(np.abs(got - ref) <= tol[:, None, None, :])
+
+
+@pytest.mark.parametrize("variant", ["TEX_DECASTELJAU", "TEX_SEILER"])
 @pytest.mark.parametrize("fmt,levels", [("UNORM16", 65535.0), ("UNORM8", 255.0)])
 @pytest.mark.parametrize("dim,nu,nv", [(3, 32, 32), (1, 7, 19), (4, 64, 5)])
 def test_texture_surface_unorm(variant, fmt, levels, dim, nu, nv):
