@@ -167,6 +167,12 @@ bez_status build_items(bez_batch b, int chunk, cudaStream_t s)
             v.push_back(it);
         }
     }
+    // Within a class, longest items first (largest-processing-time order):
+    // warps that take the short items last finish close together, so the
+    // class kernel's last wave is short for either schedule.
+    for (auto& v : per_class)
+        std::stable_sort(v.begin(), v.end(),
+                         [](const BatchItem& x, const BatchItem& y) { return x.j1 - x.j0 > y.j1 - y.j0; });
     std::vector<BatchItem> items;
     for (int k = 0; k < kBatchClasses; ++k) {
         b->a.class_start[k] = (int64_t)items.size();
