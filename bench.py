@@ -462,6 +462,28 @@ def run_precision(args, rank, world, local_rank):
                                t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, ctx=ctx, tex_share=share)
             coissue[key]["max_rel_length_err"] = float(np.max(np.abs(got.cpu().numpy() - L) / L))
 
+    # the fastest variant meeting each accuracy bar (FP32 1e-6; FP16 / BF16 /
+    # texture 2e-3), over every measured storage and texel format, as a
+    # speed-up over FP32 Horner in this run
+    best_by_bar = None
+    if not args.skip_accuracy:
+        cands = [(v, "f32", r) for v, r in variants.items()]
+        cands += [(v, "f16 storage", r) for v, r in variants16.items()]
+        cands += [(v, f"{f.lower()} texels", r) for f, tab in variants_unorm.items() for v, r in tab.items()]
+        best_by_bar = {}
+        for label, bar in (("fp32_1e-6", FP32_BAR), ("reduced_precision_2e-3", TEX_BAR)):
+            ok = [(r["points_per_s"], v, fmt, r) for v, fmt, r in cands
+                  if r.get("max_norm_err") is not None and r["max_norm_err"] <= bar]
+            if ok:
+                pps, v, fmt, r = max(ok, key=lambda x: x[0])
+                best_by_bar[label] = {"variant": v, "storage": fmt, "points_per_s": pps,
+                                      "speedup_vs_horner": pps / horner, "max_norm_err": r["max_norm_err"]}
+        tex_ok = [(r["points_per_s"], v, fmt, r) for v, fmt, r in cands
+                  if v.startswith("TEX") and r.get("max_norm_err") is not None and r["max_norm_err"] <= TEX_BAR]
+        if tex_ok:
+            pps, v, fmt, r = max(tex_ok, key=lambda x: x[0])
+            best_by_bar["texture_path_2e-3"] = {"variant": v, "storage": fmt, "points_per_s": pps,
+                                                "speedup_vs_horner": pps / horner, "max_norm_err": r["max_norm_err"]}
     head = variants[args.variant]
     traffic = args.traffic
     if traffic is None and args.variant in TRAFFIC_PER_CURVE:
@@ -498,6 +520,7 @@ def run_precision(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(ctrl_np.nbytes), "d2h_bytes_per_step": int(args.n_curves * 4)},
         "gpu_launches": int(results[args.variant]["stats"]["launches"]),
         "clocks": clock_summary,
+        "best_by_accuracy_bar": best_by_bar,
         "variants": variants,
         "variants_f16_storage": variants16 or None,
         "variants_unorm_texels": variants_unorm or None,
