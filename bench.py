@@ -273,6 +273,13 @@ def run_precision(args, rank, world, local_rank):
             for v in run_variants:
                 ms, st = timer.run(step_for(v, ctrl16), args.steps, args.warmup)
                 results16[v] = {"ms": ms, "stats": st}
+            # bfloat16 storage, FP32 arithmetic (register evaluators: no bfloat16 texel format)
+            results_bf = {}
+            ctrl_bf = ctrl.bfloat16()
+            for v in run_variants:
+                if v in REG_VARIANTS and v != "HALF2":
+                    ms, st = timer.run(step_for(v, ctrl_bf), args.steps, args.warmup)
+                    results_bf[v] = {"ms": ms, "stats": st}
         # unorm texels with per-curve rescale (texture variants only)
         results_unorm = {}
         if not args.skip_f16:
@@ -406,6 +413,12 @@ def run_precision(args, rank, world, local_rank):
         kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
         variants_unorm.setdefault(fname, {})[v] = {"points_per_s": pts_step * args.steps / (r["ms"] * 1e-3),
                                                    "kernel_ms": kern_ms}
+    variants_bf = {}
+    for v, r in (results_bf.items() if ctrl16 is not None else []):
+        st = r["stats"]
+        kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
+        variants_bf[v] = {"points_per_s": pts_step * args.steps / (r["ms"] * 1e-3), "kernel_ms": kern_ms,
+                          "speedup_vs_horner": pts_step * args.steps / (r["ms"] * 1e-3) / horner}
     variants16 = {}
     for v, r in results16.items():
         st = r["stats"]
@@ -443,6 +456,12 @@ def run_precision(args, rank, world, local_rank):
                                        tex_spread=spread)
                     err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
                     tab[v]["max_norm_err"] = float(err.max())
+            if v in variants_bf:
+                # against the oracle of the FP32 control points: includes the 2^-8 storage rounding
+                pts = bez.bez_eval(sample.bfloat16(), None, n_t=args.n_t, variant=bez.Variant[var],
+                                   t_mode=bez.TMode.HASH, seed=seed, stream_id=ts, ctx=ctx)
+                err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - ref, axis=-1).max(axis=1) / diag
+                variants_bf[v]["max_norm_err"] = float(err.max())
             if v in variants16:
                 # against the oracle of the FP32 control points: includes the 2^-11 storage rounding
                 pts = bez.bez_eval(sample.half(), None, n_t=args.n_t, variant=bez.Variant[var],
@@ -469,6 +488,7 @@ def run_precision(args, rank, world, local_rank):
     if not args.skip_accuracy:
         cands = [(v, "f32", r) for v, r in variants.items()]
         cands += [(v, "f16 storage", r) for v, r in variants16.items()]
+        cands += [(v, "bf16 storage", r) for v, r in variants_bf.items()]
         cands += [(v, f"{f.lower()} texels", r) for f, tab in variants_unorm.items() for v, r in tab.items()]
         best_by_bar = {}
         for label, bar in (("fp32_1e-6", FP32_BAR), ("reduced_precision_2e-3", TEX_BAR)):
@@ -523,6 +543,7 @@ def run_precision(args, rank, world, local_rank):
         "best_by_accuracy_bar": best_by_bar,
         "variants": variants,
         "variants_f16_storage": variants16 or None,
+        "variants_bf16_storage": variants_bf or None,
         "variants_unorm_texels": variants_unorm or None,
         "coissue": coissue or None,
         "peaks_measured": {"fma_tops": peaks["fma"] / 1e12,
