@@ -80,6 +80,33 @@ __device__ __forceinline__ void setup_comp(const BatchArgs& a, const SpanRec& r,
     }
     constexpr int S = kOpRowStride(P);
     const float2* M = a.op_pool + (spline ? r.op : a.tpow_off[P]);
+    if (P <= 3 && !rat) {
+        // Integral spans of degree <= 3: rows of at most 4 entries, so a plain
+        // FP32 dot product (operator hi part by fma, lo parts summed apart)
+        // stays within a few ulps of the row's absolute sum -- well inside
+        // the evaluation's 1e-6 bar -- at a quarter of the compensated cost.
+        // (Rational spans keep the compensated form: the plain one moved the
+        // batch's NURBS error from 4.0e-7 to 5.7e-7 for 1 % of speed.)
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+            const float4* r4 = reinterpret_cast<const float4*>(M + i * S);
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int q2 = 0; q2 < S / 2; ++q2) {
+                const float4 v = __ldg(r4 + q2);
+                if (2 * q2 <= P) {
+                    hi = fmaf(v.x, xh[2 * q2], hi);
+                    lo = fmaf(v.y, xh[2 * q2], lo);
+                }
+                if (2 * q2 + 1 <= P) {
+                    hi = fmaf(v.z, xh[2 * q2 + 1], hi);
+                    lo = fmaf(v.w, xh[2 * q2 + 1], lo);
+                }
+            }
+            dst[i * comps + q] = hi + lo;
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i <= P; ++i) {
         float sh = 0.f, corr = 0.f;
