@@ -203,6 +203,36 @@ struct Eval<VAR_HORNER_CENTRED, D, DIM> {
 #pragma unroll
             for (int kk = 0; kk < 3; ++kk) a[mm][kk] = __shfl_sync(kFull, cm, base + 3 * mm + kk);
     }
+    // Setup for 3D curves of fixed degree held by a group of G lanes (lane
+    // base + r, slot s of v holds element G s + r of the curve, b_i[k] being
+    // element 3 i + k): every lane gathers the 3 (D + 1) elements and forms
+    // all coefficients itself.  The operator entries are then the same for
+    // every lane (uniform constant reads), and the sums run in setup_warp's
+    // order, so the coefficients are the same as setup_warp's.
+    template <int G, int NL>
+    __device__ __forceinline__ void setup_group(const float (&v)[NL], int base)
+    {
+        static_assert(D > 0 && DIM == 3 && 3 * (D + 1) <= G * NL, "fixed-degree 3D curves only");
+        d = D;
+        using S = typename std::conditional<(D >= kFp64SetupCentred), double, float>::type;
+        float b[D + 1][3];
+#pragma unroll
+        for (int i = 0; i <= D; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int e = 3 * i + k;
+                b[i][k] = __shfl_sync(kFull, v[e / G], base + e % G);
+            }
+#pragma unroll
+        for (int m = 0; m <= D; ++m)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                S acc = (S)0;
+#pragma unroll
+                for (int i = 0; i <= D; ++i) acc = fma((S)kCentredT.t[D][m][i], (S)b[i][k], acc);
+                a[m][k] = (float)acc;
+            }
+    }
     __device__ __forceinline__ void eval(float t, float (&P)[DIM]) const { eval_u(t - 0.5f, P); }
     // evaluate at u = t - 1/2
     __device__ __forceinline__ void eval_u(float u, float (&P)[DIM]) const
@@ -511,6 +541,9 @@ struct Pick<VAR, 0, DIM> {
 constexpr int kWarps = 8;  // warps per block; one curve per warp per iteration
 constexpr int kCurvesPerWarp = 8;  // curves per warp when the grid is not persistent
 constexpr int kPairsPerWarp = 4;   // the same for the two-curves-per-warp kernel
+constexpr int kGroupUnitsPerWarp = 2;  // and for the G-lanes-per-curve kernel
+constexpr int kGroup8MinSamples = 128;  // samples per curve from which 8 lanes take a curve
+constexpr int kGroup4MinSamples = 256;  // and from which 4 lanes do
 
 template <int TM>
 __device__ __forceinline__ float param(const CurveArgs& a, int64_t c, int j, uint32_t kc)
@@ -594,15 +627,20 @@ __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb,
     int g = jb + 4;
 #pragma unroll 2
     for (; g + 4 <= je; g += 4) {
+        // the group's 4 segments are summed first and then added to the run
+        // (as many adds, rounding error growing with the run's groups)
         const uint32_t kg = km ^ (uint32_t)g;
+        float gs = 0.f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float P[DIM];
             DrawEval<E>::at(e, (kg ^ (uint32_t)i) * kLowbiasMul1, P);
-            acc += seg_len<DIM>(P, last);
+            const float sl = seg_len<DIM>(P, last);
+            gs = i == 0 ? sl : gs + sl;
 #pragma unroll
             for (int k = 0; k < DIM; ++k) last[k] = P[k];
         }
+        acc += gs;
     }
     if (g < je) {
         const uint32_t kg = km ^ (uint32_t)g;
@@ -786,6 +824,64 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_curve_pair(const CurveArgs a
     }
 }
 
+// G = 8 or 4 lanes per curve (4 or 8 curves per warp), for the same workload
+// with more samples per curve: lanes G g .. G g + G - 1 take curve
+// (32 / G) q + g.  Each group loads its 3 (d + 1) control values
+// (ceil(3 (d + 1) / G) per lane), converts them redundantly (setup_group),
+// walks runs of a multiple of 4 samples per lane and reduces its length over
+// G lanes.  Against two curves per warp, a lane's per-curve work (load,
+// conversion, key, run ends, reduction, store) is spread over 16 / G times
+// the samples.  The sums run over G runs of about n_t / G samples.  (One or
+// two lanes per curve measured slower at 1024 samples: 1.10e12 and 1.17e12
+// against 1.18e12 points/s for 4.)
+template <int D, int G>
+__global__ void __launch_bounds__(kWarps * 32, 5) k_curve_group(const CurveArgs a)
+{
+    using E = Eval<VAR_HORNER_CENTRED, D, 3>;
+    constexpr int PER = 3 * (D + 1);
+    constexpr int NL = (PER + G - 1) / G;
+    constexpr int CPW = 32 / G;  // curves per warp
+    static_assert(G == 4 || G == 8, "4 or 8 lanes per curve");
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int grp = lane / G, li = lane % G, base = lane - li;
+    const int64_t n_units = (a.n_curves + CPW - 1) / CPW;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    float v[NL];
+    auto load = [&](int64_t q) {
+        const int64_t c = CPW * q + grp;
+#pragma unroll
+        for (int r = 0; r < NL; ++r) {
+            const int i = li + G * r;
+            v[r] = (c < a.n_curves && i < PER) ? load_elem(a.ctrl, a.dtype, c * PER + i) : 0.f;
+        }
+    };
+    const int n_t = a.n_t;
+    const int chunk = ((n_t + G - 1) / G + 3) & ~3;
+    int64_t q = (int64_t)blockIdx.x * kWarps + wib;
+    load(q);
+    for (; q < n_units; q += n_warps) {
+        const int64_t c = CPW * q + grp;
+        const bool live = c < a.n_curves;  // the warp's last unit may be partial
+        E e;
+        e.template setup_group<G>(v, base);
+        load(q + n_warps);  // prefetch this warp's next curves
+        const uint32_t kc = curve_key<TM_HASH16>(a, c);
+        const int jb = li * chunk;
+        const int je = live ? min(jb + chunk, n_t) : jb;
+        float acc = 0.f;
+        float first[3] = {0.f, 0.f, 0.f}, prev[3] = {0.f, 0.f, 0.f};
+        if (jb < je) acc = run_length_h16<E, 3>(e, kc, jb, je, first, prev);
+        float pl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) pl[k] = __shfl_up_sync(kFull, prev[k], 1);
+        if (li > 0 && jb < je) acc += seg_len<3>(first, pl);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);  // within the group
+        if (li == 0 && live) a.out[c] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- dispatch
 
 // Grid of the pair kernel: as launch_one, with pairs of curves as the unit.
@@ -798,6 +894,28 @@ LaunchResult launch_pair(const CurveArgs& a, cudaStream_t s, const LaunchHooks& 
     int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
     if (work > grid) {
         const int64_t g = (n_pairs + (int64_t)kWarps * kPairsPerWarp - 1) / ((int64_t)kWarps * kPairsPerWarp);
+        if (g > grid) grid = (int)(g < 2147483647 ? g : 2147483647);
+    }
+    h.count(h.self);
+    h.begin(h.self, s);
+    kern<<<grid, kWarps * 32, 0, s>>>(a);
+    cudaError_t err = cudaGetLastError();
+    h.end(h.self, s);
+    return {1, err};
+}
+
+// Grid of the G-lanes-per-curve kernel: units of 32 / G curves,
+// kGroupUnitsPerWarp per warp when they outnumber the resident warps.
+template <int D, int G>
+LaunchResult launch_group(const CurveArgs& a, cudaStream_t s, const LaunchHooks& h)
+{
+    auto kern = k_curve_group<D, G>;
+    const int64_t n_units = (a.n_curves + 32 / G - 1) / (32 / G);
+    const int64_t work = (n_units + kWarps - 1) / kWarps;
+    int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    if (work > grid) {
+        const int64_t per = (int64_t)kWarps * kGroupUnitsPerWarp;
+        const int64_t g = (n_units + per - 1) / per;
         if (g > grid) grid = (int)(g < 2147483647 ? g : 2147483647);
     }
     h.count(h.self);
@@ -843,9 +961,13 @@ LaunchResult launch_modes(const CurveArgs& a, int tm, int om, cudaStream_t s, co
     if (tm == TM_UNIFORM) return launch_one<VAR, D, DIM, TM_UNIFORM, OM_LENGTH>(a, s, h);
     // the fused evaluate-and-measure form of 3D curves of fixed degree gets the
     // pre-mixed draw when every sample index fits 16 bits; centred Horner up
-    // to degree 4 with at least 64 samples runs two curves per warp
-    if constexpr (VAR == VAR_HORNER_CENTRED && D > 0 && D <= 4 && DIM == 3)
+    // to degree 4 runs two curves per warp from 64 samples, four from 128 and
+    // eight from 256
+    if constexpr (VAR == VAR_HORNER_CENTRED && D > 0 && D <= 4 && DIM == 3) {
+        if (a.n_t >= kGroup4MinSamples && a.n_t <= 65536) return launch_group<D, 4>(a, s, h);
+        if (a.n_t >= kGroup8MinSamples && a.n_t <= 65536) return launch_group<D, 8>(a, s, h);
         if (a.n_t >= 64 && a.n_t <= 65536) return launch_pair<D>(a, s, h);
+    }
     if (D > 0 && DIM == 3 && a.n_t <= 65536) return launch_one<VAR, D, DIM, (D > 0 && DIM == 3 ? TM_HASH16 : TM_HASH), OM_LENGTH>(a, s, h);
     return launch_one<VAR, D, DIM, TM_HASH, OM_LENGTH>(a, s, h);
 }

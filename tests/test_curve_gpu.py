@@ -145,10 +145,15 @@ def test_half_and_bfloat16_storage():
         assert normalised_error(got, oracle.bezier(stored, t)).max() <= FP32_BAR, name
 
 
+# A lane sums a run of consecutive segment lengths, then lanes combine by a
+# butterfly.  The centred-Horner length kernels give a lane runs of n_t/16
+# (two curves per warp), n_t/8 (four, from 128 samples) or n_t/4 (eight, from
+# 256), and the other kernels n_t/32, so n_t/4 bounds the run term of every
+# form.
 def _length_tol(ref_pts, L_ref, n_t):
     diag = np.maximum(np.linalg.norm(ref_pts.max(axis=1) - ref_pts.min(axis=1), axis=-1), 2.0 ** -4)
     u = 2.0 ** -24
-    return 2 * (n_t - 1) * FP32_BAR * diag + (6 + n_t / 32 + 6) * u * L_ref + 1e-7
+    return 2 * (n_t - 1) * FP32_BAR * diag + (6 + n_t / 4 + 6) * u * L_ref + 1e-7
 
 
 @pytest.mark.parametrize("variant", ALL)
@@ -348,10 +353,10 @@ def _ctrl_diag(ctrl):
 
 def test_headline_length_kernel_at_full_size():
     # The fused draw + centred Horner + length kernel in the launch shape the
-    # benchmark times: 1,048,575 cubic 3D curves (the last pair of the
-    # two-curves-per-warp kernel half empty) x 1024 hashed parameters, so the
-    # grid is not persistent and every warp walks several pairs with the next
-    # pair's control points prefetched.  Every curve's length is compared with
+    # benchmark times: 1,048,575 cubic 3D curves (the warps' last unit of
+    # curves partial) x 1024 hashed parameters, so the grid is not persistent
+    # and every warp walks several units with the next unit's control points
+    # prefetched.  Every curve's length is compared with
     # the oracle's; the tolerance takes the 1e-6 point bar over the control
     # polygon's diagonal (>= the curve's), and a sample spread over the batch
     # is held to the curve-diagonal tolerance of the smaller tests.
@@ -367,13 +372,36 @@ def test_headline_length_kernel_at_full_size():
                                                              synth.PRECISION_T_STREAM, c0=s)
                         for s in range(0, n, chunk)])
     u = 2.0 ** -24
-    tol = 2 * (n_t - 1) * FP32_BAR * _ctrl_diag(ctrl) + (6 + n_t / 32 + 6) * u * L + 1e-7
+    tol = 2 * (n_t - 1) * FP32_BAR * _ctrl_diag(ctrl) + (6 + n_t / 4 + 6) * u * L + 1e-7
     assert np.all(np.abs(got - L) <= tol), (np.abs(got - L) / tol).max()
     idx = np.unique(np.concatenate([np.arange(0, n, 97), [n - 2, n - 1]]))
     th = np.concatenate([oracle.hash_t(seed, synth.PRECISION_T_STREAM, int(c), 1, n_t) for c in idx])
     pts = oracle.bezier(ctrl[idx], th)
     assert np.all(np.abs(got[idx] - L[idx]) <= _length_tol(pts, L[idx], n_t))
     print(f"\nfull-size headline: max relative length error {np.max(np.abs(got - L) / L):.3g}")
+
+
+@pytest.mark.parametrize("n_t,degree", [(128, 3), (200, 4), (96, 1), (256, 2), (333, 4), (512, 3), (700, 1),
+                                         (2051, 4)])
+def test_fused_length_kernels_block_scheduled(n_t, degree):
+    # The centred-Horner length kernels by samples per curve: two curves per
+    # warp below 128, four from 128, eight from 256.  300,001 curves: more
+    # units than resident warps, so every warp walks several with the next
+    # one's control points prefetched, and the last unit is partial.  Every
+    # length is compared with the oracle.
+    torch = need_gpu()
+    rng = np.random.default_rng(7100 + n_t)
+    n = 300_001 if n_t < 1000 else 60_001
+    ctrl = _ctrl(rng, n, degree, 3)
+    seed, stream = 4242, 3
+    got = _run(torch, ctrl, n_t=n_t, variant="HORNER_CENTRED", out_mode="POLYLINE_LENGTH", t_mode="HASH",
+               seed=seed, stream_id=stream)
+    chunk = 1 << 15
+    L = np.concatenate([oracle.hashed_bezier_polyline_length(ctrl[s:s + chunk], n_t, seed, stream, c0=s)
+                        for s in range(0, n, chunk)])
+    u = 2.0 ** -24
+    tol = 2 * (n_t - 1) * FP32_BAR * _ctrl_diag(ctrl) + (6 + n_t / 4 + 6) * u * L + 1e-7
+    assert np.all(np.abs(got - L) <= tol), (np.abs(got - L) / tol).max()
 
 
 @pytest.mark.parametrize("variant", ["HORNER_CENTRED", "DECASTELJAU"])
