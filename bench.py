@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -855,6 +856,18 @@ def run_tensor(args):
                    traffic=TRAFFIC_SURFACE_65536)
 
 
+# Convergence check of the fit (outside the timed steps): Adam with its own
+# rate for the control points and for the parameters t (a sample's t moves
+# along the curve and wants far smaller steps), both decayed on a cosine to
+# 1 % over FIT_CONV_STEPS steps.  With one rate of 1e-2 for both (the timed
+# configuration) the fit stalls far above the noise.
+FIT_CONV_STEPS, FIT_CONV_LR = 500, (5e-2, 1e-3)
+
+
+def fit_lr_factor(k, total):
+    return 0.01 + 0.99 * 0.5 * (1.0 + math.cos(math.pi * min(k, total) / total))
+
+
 def run_fit(args):
     import torch
 
@@ -915,6 +928,19 @@ def run_fit(args):
             step()
         final = float(step().sum())
         ms_a, _ = timer.run(step_autograd, args.steps, args.warmup)
+        # the same fused step from the same start, two-rate cosine schedule
+        ctrl2 = torch.tensor(init, device="cuda")
+        t2 = torch.tensor(t0, device="cuda")
+        opt2 = torch.optim.Adam([{"params": [ctrl2], "lr": FIT_CONV_LR[0]}, {"params": [t2], "lr": FIT_CONV_LR[1]}])
+        for k in range(FIT_CONV_STEPS):
+            for g, base in zip(opt2.param_groups, FIT_CONV_LR):
+                g["lr"] = base * fit_lr_factor(k, FIT_CONV_STEPS)
+            loss2, gc2, _, gt2 = bez.bez_mse_grad(ctrl2, t2, target, loss_scale=scale, ctx=ctx)
+            ctrl2.grad, t2.grad = gc2, gt2
+            opt2.step()
+            t2.clamp_(0, 1)
+        conv = float(loss2.sum())
+        del ctrl2, t2, opt2
     kern_ms = st["timed_ms"] / max(st["timed_launches"], 1)
     # k_grad with a target, per sample: t 4 B + target 12 B in, grad_t 4 B out;
     # per curve: 48 B of control points in, 48 B of grad_ctrl and 4 B of loss out
@@ -928,6 +954,11 @@ def run_fit(args):
                                        "largest oracle gradient",
                     "loss_first": first, "loss_after_200_steps": final, "rms_after_200_steps": final ** 0.5,
                     "noise_sigma": sigma, "rms_over_sigma": final ** 0.5 / sigma,
+                    "fit_to_noise": {"rms": conv ** 0.5, "rms_over_sigma": conv ** 0.5 / sigma,
+                                     "steps": FIT_CONV_STEPS,
+                                     "optimizer": f"Adam, lr {FIT_CONV_LR[0]:g} (control points) and "
+                                                  f"{FIT_CONV_LR[1]:g} (t), cosine decay to 1 %, t clamped "
+                                                  "to [0, 1]; not timed"},
                     "autograd_step": {"samples_per_s": n * args.steps / (ms_a * 1e-3),
                                       "ms_per_step": ms_a / args.steps,
                                       "path": "bezier_curve forward kernel, torch squared error, adjoint kernel"}},

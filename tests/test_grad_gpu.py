@@ -142,25 +142,33 @@ def test_autograd_function_matches_adjoint_and_finite_differences():
         assert abs(fd - float(t.grad[i, j])) <= 5e-3 * max(1.0, abs(fd))
 
 
-def test_adam_fit_reduces_loss():
+def test_adam_fit_reaches_noise_floor():
     # the fitting workload at reduced size: curves fitted to noisy samples of
-    # random cubics (sigma 0.01) with Adam (lr 1e-2, 200 steps) through the
-    # autograd Function, t clamped to [0,1] after each step.  200 steps at
-    # this rate cut the loss about 30-fold but stop well above the noise
-    # floor (RMS ~0.1 against sigma 0.01); the benchmark reports the final
-    # RMS, and test_adam_trajectory_matches_oracle_steps checks the steps
+    # random cubics (sigma 0.01) through the autograd Function, from random
+    # control points and uniformly spaced t.  Adam with its own rate for the
+    # control points (5e-2) and for t (1e-3), both decayed on a cosine to 1 %
+    # over 500 steps, t clamped to [0, 1] after each step -- the schedule of
+    # the benchmark's convergence check.  The RMS residual must come down to the
+    # noise level (free t absorb the noise along the curve, so it may end a
+    # little below sigma); test_adam_trajectory_matches_oracle_steps checks
+    # the individual steps against the oracle.
     torch = need_gpu()
+    import math
     from paper_2603_15447_gb300 import synth
     from paper_2603_15447_gb300.autograd import bezier_curve
-    truth, t_true, noise, init = synth.fit(n_curves=2048, n_t=512)
+    sigma, steps, lr = 0.01, 500, (5e-2, 1e-3)
+    truth, t_true, noise, init = synth.fit(n_curves=2048, n_t=512, sigma=sigma)
     ref = oracle.bezier(truth, t_true)
     target = torch.tensor((ref + noise).astype(np.float32), device="cuda")
     ctrl = torch.tensor(init, device="cuda", requires_grad=True)
     t = torch.tensor(np.tile((np.arange(512) / 511.0).astype(np.float32), (2048, 1)), device="cuda",
                      requires_grad=True)
-    opt = torch.optim.Adam([ctrl, t], lr=1e-2)
+    opt = torch.optim.Adam([{"params": [ctrl], "lr": lr[0]}, {"params": [t], "lr": lr[1]}])
     first = None
-    for step in range(200):
+    for k in range(steps):
+        f = 0.01 + 0.99 * 0.5 * (1.0 + math.cos(math.pi * k / steps))
+        for g, base in zip(opt.param_groups, lr):
+            g["lr"] = base * f
         opt.zero_grad()
         loss = ((bezier_curve(ctrl, t) - target) ** 2).mean()
         loss.backward()
@@ -169,9 +177,9 @@ def test_adam_fit_reduces_loss():
             t.clamp_(0, 1)
         if first is None:
             first = float(loss.detach())
-    final = float(loss.detach())
-    assert final < first / 20, (first, final)
-    assert np.sqrt(final) < 0.1
+    rms = float(loss.detach()) ** 0.5
+    assert first ** 0.5 > 30 * sigma, first
+    assert 0.7 * sigma < rms < 1.2 * sigma, rms
 
 
 def _adam_fp64(theta, g, m, v, k, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
