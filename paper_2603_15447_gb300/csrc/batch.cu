@@ -16,6 +16,7 @@
 // streams.  Warps take items round-robin, reading the next record while they
 // evaluate the current item (static), or `grab` at a time from an atomic
 // counter.  Within an item, each lane evaluates runs of 8 consecutive samples
+// (1, 2 or 4 in a tile of at most 32, 64 or 128 samples)
 // t_j = fl32(j) / fl32(n_samples - 1), keeping the coefficients of its
 // current span in registers and reloading them only when the span changes;
 // results go through a padded per-warp shared-memory tile and out with
@@ -263,10 +264,15 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
     int cached = -1;
     float* out = a.out_pool + it.out_off;
     for (int tb = j0; tb < j1; tb += kTile) {
-        const int my0 = tb + lane * kRun;
+        // a tile of at most 32, 64 or 128 samples (a short item, the ragged
+        // end of a long one) gives each lane a run of 1, 2 or 4 samples, so
+        // the warp's lanes share it instead of a few lanes walking runs of 8
+        const int vs = min(kTile, j1 - tb);
+        const int lr = vs > 128 ? 3 : vs > 64 ? 2 : vs > 32 ? 1 : 0;  // log2 of the run
+        const int my0 = tb + (lane << lr);
         int s_run = -1;  // span of this lane's previous sample in the run
 #pragma unroll 2
-        for (int r = 0; r < kRun; ++r) {
+        for (int r = 0; r < (1 << lr); ++r) {
             const int j = my0 + r;
             if (j < j1) {
                 const float t = grid(j);
@@ -311,14 +317,24 @@ __device__ void item_fixed(const BatchArgs& a, const BatchItem& it, float* stage
         // offset = o0 + 8 m - 24 w where w = (a + m) div 3, so its staged
         // position is base + m (LS + 8) + w (LS - 24).
         static_assert(kRun * DIM == 24 && LS == 25, "write-out index formula");
-        const int valid = min(kTile, j1 - tb) * DIM;
-        float* o = out + (int64_t)tb * DIM + lane;
-        const int a3 = (lane % 24) / 8;
-        const int base = (lane / 24) * LS + lane % 24;
+        const int valid = vs * DIM;
+        if (lr == 3) {
+            float* o = out + (int64_t)tb * DIM + lane;
+            const int a3 = (lane % 24) / 8;
+            const int base = (lane / 24) * LS + lane % 24;
 #pragma unroll
-        for (int m = 0; m < kRun * DIM; ++m) {
-            const int w = m / 3 + ((m % 3) != 0 && a3 >= 3 - (m % 3) ? 1 : 0);
-            if (32 * m + lane < valid) o[32 * m] = stage[base + m * (LS + 8) + w * (LS - 24)];
+            for (int m = 0; m < kRun * DIM; ++m) {
+                const int w = m / 3 + ((m % 3) != 0 && a3 >= 3 - (m % 3) ? 1 : 0);
+                if (32 * m + lane < valid) o[32 * m] = stage[base + m * (LS + 8) + w * (LS - 24)];
+            }
+        } else {
+            // short runs: float f is component f mod 3 of sample f div 3,
+            // element (sample mod run) of lane (sample div run)'s run
+            float* o = out + (int64_t)tb * DIM;
+            for (int f = lane; f < valid; f += 32) {
+                const int smp = f / 3, q = f - 3 * smp;
+                o[f] = stage[(smp >> lr) * LS + (smp & ((1 << lr) - 1)) * DIM + q];
+            }
         }
         __syncwarp();
     }
