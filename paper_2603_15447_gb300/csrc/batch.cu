@@ -153,17 +153,17 @@ __device__ __forceinline__ SpanRec load_span_rec(const SpanRec* p)
     return r;
 }
 
-// Span extraction, one thread per (span, component).  Each thread reads its
-// span's record and then, independently of each other, the control points
-// (and weights) and the operator rows.
-__global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a)
+// Span extraction of span records [rec0, rec0 + n_rec), one thread per (span,
+// component).  Each thread reads its span's record and then, independently
+// of each other, the control points (and weights) and the operator rows.
+__global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a, int64_t rec0, int64_t n_rec)
 {
     const int per = a.dim + 1;  // component slots per span (dim + 1 for homogeneous NURBS)
-    const int64_t total = a.n_span_rec * per;
+    const int64_t total = n_rec * per;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-        const int64_t sp = idx / per;
-        const int q = (int)(idx - sp * per);
+        const int64_t sp = rec0 + idx / per;
+        const int q = (int)(idx - (sp - rec0) * per);
         const SpanRec r = load_span_rec(a.span_rec + sp);
         const int comps = r.type == BEZ_CURVE_NURBS ? a.dim + 1 : a.dim;
         if (q >= comps) continue;
@@ -498,17 +498,33 @@ int batch_full_grid(const BatchArgs& a, int threads, int sm_count, int cls)
     return persistent_grid(kern, threads, batch_smem(a, threads), sm_count, (count + wpb - 1) / wpb);
 }
 
+// span extraction of records [rec0, rec0 + n_rec) on stream s
+static cudaError_t launch_setup(const BatchArgs& a, int64_t rec0, int64_t n_rec, int sm_count, cudaStream_t s,
+                                const LaunchHooks& h, int* launches)
+{
+    if (n_rec <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n_rec * (a.dim + 1) + 255) / 256, (int64_t)sm_count * 16);
+    h.count(h.self);
+    k_batch_setup<<<grid > 0 ? grid : 1, 256, 0, s>>>(a, rec0, n_rec);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool with_setup, cudaStream_t s,
                          const BatchStreams* bs, const LaunchHooks& h, int* launches)
 {
     *launches = 0;
     cudaError_t e;
-    if (with_setup && a.n_curves > 0) {
-        const int grid = (int)std::min<int64_t>((a.n_span_rec * (a.dim + 1) + 255) / 256, (int64_t)sm_count * 16);
-        h.count(h.self);
-        k_batch_setup<<<grid > 0 ? grid : 1, 256, 0, s>>>(a);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int active = 0;
+    for (int cls = 0; cls < kBatchClasses; ++cls) active += a.class_start[cls + 1] > a.class_start[cls];
+    // class evaluators run side by side on forked streams; with the setup in
+    // the same launch, each class's spans are extracted on its own stream just
+    // before its evaluator, so one class's extraction overlaps the others'
+    // evaluation
+    const bool fork = bs && active > 1;
+    const bool split_setup = with_setup && a.n_curves > 0 && fork;
+    if (with_setup && a.n_curves > 0 && !split_setup) {
+        if ((e = launch_setup(a, 0, a.n_span_rec, sm_count, s, h, launches)) != cudaSuccess) return e;
     }
     if (a.schedule != 0) {
         e = cudaMemsetAsync(a.counter, 0, kBatchClasses * sizeof(unsigned long long), s);
@@ -521,11 +537,8 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
     // others' latency; otherwise persistent grids on 4 shared streams.
     const bool part = a.partition != 0 && a.schedule != 0;
     const int nside = part ? kBatchSideStreams : kBatchSharedSideStreams;
-    int active = 0;
-    for (int cls = 0; cls < kBatchClasses; ++cls) active += a.class_start[cls + 1] > a.class_start[cls];
     if (active == 0) return cudaSuccess;
-    // class evaluators run side by side: fork the side streams off `s`
-    const bool fork = bs && active > 1;
+    // fork the side streams off `s`
     h.begin(h.self, s);
     if (fork) {
         if ((e = cudaEventRecord(bs->fork, s)) != cudaSuccess) return e;
@@ -536,10 +549,13 @@ cudaError_t launch_batch(const BatchArgs& a, int threads, int sm_count, bool wit
     int m = 0;
     for (int cls = 0; cls < kBatchClasses && e == cudaSuccess; ++cls) {
         const int64_t first = a.class_start[cls], count = a.class_start[cls + 1] - first;
-        if (count <= 0) continue;
+        const int64_t rec0 = a.span_class_start[cls], n_rec = a.span_class_start[cls + 1] - rec0;
+        if (count <= 0 && !(split_setup && n_rec > 0)) continue;
         const int lane_of = fork ? m % (nside + 1) : 0;
         ++m;
         cudaStream_t cs = lane_of == 0 ? s : bs->side[lane_of - 1];
+        if (split_setup && (e = launch_setup(a, rec0, n_rec, sm_count, cs, h, launches)) != cudaSuccess) break;
+        if (count <= 0) continue;
         const void* kern = a.repr == 1 ? class_kernel<1>(cls) : class_kernel<0>(cls);
         const int wpb = threads / 32;
         int grid = persistent_grid(kern, threads, smem, sm_count, (count + wpb - 1) / wpb);

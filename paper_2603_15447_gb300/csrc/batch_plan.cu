@@ -537,14 +537,27 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     alloc((void**)&b->d_ops_c, ops2c.size() * sizeof(float2));
     alloc((void**)&b->d_spans, (size_t)spans * sizeof(float));
     alloc(&b->d_counter, kBatchClasses * sizeof(unsigned long long));
-    // every span with its offsets resolved, grouped by (degree, type) so that
-    // the warps of the setup kernel run one degree's code at a time
+    // every span with its offsets resolved, grouped by item class (so that a
+    // class's spans can be extracted on its own stream just before its
+    // evaluator) and within a class by (degree, type) (so that the warps of
+    // the setup kernel run one degree's code at a time)
+    std::vector<int64_t> order((size_t)n_curves);
+    for (int64_t i = 0; i < n_curves; ++i) order[(size_t)i] = i;
+    auto span_key = [&](int64_t i) {
+        const bez_curve_desc& d = b->hdesc[(size_t)i];
+        return ((int64_t)batch_item_class(d, dim) * 64 + d.degree) * 4 + d.type;
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t x, int64_t y) { return span_key(x) < span_key(y); });
     std::vector<SpanRec> span_rec;
-    for (int deg = 1; deg <= 7; ++deg)
-        for (int ty = BEZ_CURVE_BEZIER; ty <= BEZ_CURVE_NURBS; ++ty)
-            for (int64_t i = 0; i < n_curves; ++i) {
-                const bez_curve_desc& d = b->hdesc[(size_t)i];
-                if (d.degree != deg || d.type != ty) continue;
+    int64_t span_class_start[16] = {};
+    {
+        int cls_next = 0;
+        for (int64_t i : order) {
+            const bez_curve_desc& d = b->hdesc[(size_t)i];
+            const int cls = batch_item_class(d, dim);
+            while (cls_next <= cls) span_class_start[cls_next++] = (int64_t)span_rec.size();
+            {
                 const bool spline = d.type != BEZ_CURVE_BEZIER, rat = d.type == BEZ_CURVE_NURBS;
                 const int comps = rat ? dim + 1 : dim;
                 const int n_spans = spline ? d.n_ctrl - d.degree : 1;
@@ -559,6 +572,9 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
                     span_rec.push_back(r);
                 }
             }
+        }
+        while (cls_next < 16) span_class_start[cls_next++] = (int64_t)span_rec.size();
+    }
     alloc((void**)&b->d_span_rec, span_rec.size() * sizeof(SpanRec));
     if (e == cudaSuccess && !span_rec.empty())
         e = cudaMemcpy(b->d_span_rec, span_rec.data(), span_rec.size() * sizeof(SpanRec), cudaMemcpyHostToDevice);
@@ -606,6 +622,7 @@ bez_status bez_batch_create(bez_ctx c, const bez_curve_desc* desc, int64_t n_cur
     a.op_pool = b->d_ops;
     a.span_rec = b->d_span_rec;
     a.n_span_rec = (int64_t)span_rec.size();
+    for (int k = 0; k < 16; ++k) a.span_class_start[k] = span_class_start[k];
     a.repr = -1;  // set by apply_shape, which then runs the setup
     a.counter = b->d_counter;
     b->setup_each = bo ? bo->setup_each_launch != 0 : true;

@@ -233,6 +233,7 @@ struct BatchArgs {
     int64_t tpow_off[8];         // offset of T_p (Bezier -> centred power basis) in the centred op_pool
     const SpanRec* span_rec;     // every span, offsets resolved: one setup thread per component
     int64_t n_span_rec;
+    int64_t span_class_start[16];  // spans of item class k: [span_class_start[k], span_class_start[k+1])
     int32_t repr;                // 0 Bezier points (de Casteljau), 1 power basis about 1/2 (Horner)
     const BatchItem* items;      // work items, sorted by item class
     int64_t n_items;
