@@ -63,7 +63,7 @@ T_OPS, LEN_OPS = 9, 8
 # points; the 4 B lengths stay in L2) and scales with the curve count; the
 # surface kernel on the full 65,536-patch tensor workload; the fused adjoint
 # on the full 65,536 x 512 fit step.
-TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6308608 / 131072}
+TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6312448 / 131072}
 # the kernel behind each headline variant's fused length (cubic 3D, hashed t)
 KERNEL_NAME = {"HORNER_CENTRED": "k_curve_group<3, 4> (four lanes per curve)", "HALF2": "k_curve_h2"}
 TRAFFIC_SURFACE_65536 = 12652544 + 742988544

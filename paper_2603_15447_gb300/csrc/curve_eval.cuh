@@ -605,7 +605,7 @@ struct DrawEval<Eval<VAR_HORNER_CENTRED, D, DIM0>> {
 // needs four more registers per lane, and measured slower.)  `first` and
 // `last` return the run's end points for the join with the neighbouring
 // lanes.
-template <class E, int DIM>
+template <class E, int DIM, int UNROLL = 2>
 __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb, int je, float (&first)[DIM],
                                                 float (&last)[DIM])
 {
@@ -625,7 +625,7 @@ __device__ __forceinline__ float run_length_h16(const E& e, uint32_t km, int jb,
         }
     }
     int g = jb + 4;
-#pragma unroll 2
+#pragma unroll UNROLL
     for (; g + 4 <= je; g += 4) {
         // the group's 4 segments are summed first and then added to the run
         // (as many adds, rounding error growing with the run's groups)
@@ -833,9 +833,11 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_curve_pair(const CurveArgs a
 // conversion, key, run ends, reduction, store) is spread over 16 / G times
 // the samples.  The sums run over G runs of about n_t / G samples.  (One or
 // two lanes per curve measured slower at 1024 samples: 1.10e12 and 1.17e12
-// against 1.18e12 points/s for 4.)
+// against 1.18e12 points/s for 4.)  64 registers (4 blocks per SM) with the
+// group loop unrolled by 4: 1.21e12 against 1.18e12 at 48 registers with 2;
+// 80 registers measured slower.
 template <int D, int G>
-__global__ void __launch_bounds__(kWarps * 32, 5) k_curve_group(const CurveArgs a)
+__global__ void __launch_bounds__(kWarps * 32, 4) k_curve_group(const CurveArgs a)
 {
     using E = Eval<VAR_HORNER_CENTRED, D, 3>;
     constexpr int PER = 3 * (D + 1);
@@ -871,7 +873,7 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_curve_group(const CurveArgs 
         const int je = live ? min(jb + chunk, n_t) : jb;
         float acc = 0.f;
         float first[3] = {0.f, 0.f, 0.f}, prev[3] = {0.f, 0.f, 0.f};
-        if (jb < je) acc = run_length_h16<E, 3>(e, kc, jb, je, first, prev);
+        if (jb < je) acc = run_length_h16<E, 3, 4>(e, kc, jb, je, first, prev);
         float pl[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) pl[k] = __shfl_up_sync(kFull, prev[k], 1);
