@@ -1,5 +1,7 @@
-// curve_eval.cuh -- register evaluators for Bezier curves and the warp-per-curve
-// kernel that drives them.
+// curve_eval.cuh -- register evaluators for Bezier curves and the kernels that
+// drive them: one curve per warp (every variant), and for the fused
+// evaluate-and-measure form of centred Horner on 3D curves of degree <= 4 two
+// curves per warp (k_curve_pair) or 8 / 4 lanes per curve (k_curve_group).
 //
 // Each evaluator is a struct with setup(b) (per curve, once) and eval(t, P)
 // (per parameter).  D is the degree when known at compile time, or 0 for the
