@@ -69,17 +69,18 @@ KERNEL_NAME = {"HORNER_CENTRED": "k_curve_group<3, 4> (four lanes per curve)", "
 TRAFFIC_SURFACE_65536 = 12652544 + 742988544
 TRAFFIC_FIT_65536x512 = 540098304 + 121953024
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
-            "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10, "TEX_SEILER_S8": 3}
+            "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10, "TEX_SEILER_S8": 3, "TEX_SEILER_S4": 3}
 # filtered fetches per point and the peak they are held to
 TEX_FETCHES = {"TEX_DECASTELJAU": (1, "tex3d_f32"), "TEX_SEILER": (1, "tex2d_f32"), "TEX_HYBRID": (2, "tex2d_f32"),
-               "TEX_SEILER_S8": (1, "tex2d_f32")}
+               "TEX_SEILER_S8": (1, "tex2d_f32"), "TEX_SEILER_S4": (1, "tex2d_f32")}
 REG_VARIANTS = ["HORNER", "HORNER_CENTRED", "BERNSTEIN", "SEILER", "DECASTELJAU", "HALF2"]
-TEX_VARIANTS = ["TEX_DECASTELJAU", "TEX_SEILER", "TEX_HYBRID", "TEX_SEILER_S8"]
+TEX_VARIANTS = ["TEX_DECASTELJAU", "TEX_SEILER", "TEX_HYBRID", "TEX_SEILER_S8", "TEX_SEILER_S4"]
 VARIANTS = REG_VARIANTS + TEX_VARIANTS
-# bench name -> (bez_variant name, tex_spread): TEX_SEILER_S8 is the cubic
-# Seiler tile spread over 9 x 9 texels
+# bench name -> (bez_variant name, tex_spread): TEX_SEILER_S8 / _S4 are the
+# cubic Seiler tile spread over 9 x 9 / 5 x 5 texels
 VARIANT_SPEC = {v: (v, 0) for v in VARIANTS}
 VARIANT_SPEC["TEX_SEILER_S8"] = ("TEX_SEILER", 8)
+VARIANT_SPEC["TEX_SEILER_S4"] = ("TEX_SEILER", 4)
 FP32_BAR, TEX_BAR = 1e-6, 2e-3
 FALLBACK_SMS, LANES = 152, 128
 
