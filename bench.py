@@ -760,16 +760,20 @@ def run_tensor(args):
                                args.warmup)
         ms_ts, st_ts = timer.run(lambda: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx),
                                  args.steps, args.warmup)
-        # Seiler tiles spread over 9 x 9 texels (float4 and unorm16 texels)
+        # Seiler tiles spread over 9 x 9 and 5 x 5 texels (float4 and unorm16 texels)
         spread_s = {}
-        for fname in ("AUTO", "UNORM16"):
-            fmt = bez.TexFormat[fname]
-            ms_x, st_x = timer.run(lambda fmt=fmt: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so, ctx=ctx,
-                                                                        tex_format=fmt, tex_spread=8),
-                                   args.steps, args.warmup)
-            kx = st_x["timed_ms"] / st_x["timed_launches"]
-            spread_s[fname] = {"points_per_s": n_s * args.steps / (ms_x * 1e-3), "kernel_ms": kx,
-                               "pack_ms": ms_x / args.steps - kx, "gbs": n_s * 12 / (kx * 1e-3) / 1e9}
+        for sp in (8, 4):
+            for fname in ("AUTO", "UNORM16"):
+                fmt = bez.TexFormat[fname]
+                ms_x, st_x = timer.run(lambda fmt=fmt, sp=sp: bez.bez_eval_surface(s, 32, 32, variant=texs, out=so,
+                                                                                   ctx=ctx, tex_format=fmt,
+                                                                                   tex_spread=sp),
+                                       args.steps, args.warmup)
+                kx = st_x["timed_ms"] / st_x["timed_launches"]
+                spread_s[f"spread{sp}/{fname}"] = {"points_per_s": n_s * args.steps / (ms_x * 1e-3), "kernel_ms": kx,
+                                                   "pack_ms": ms_x / args.steps - kx,
+                                                   "gbs": n_s * 12 / (kx * 1e-3) / 1e9, "tex_spread": sp,
+                                                   "tex_format": fname}
         # half / bfloat16 control-point storage, FP32 contraction
         low = {}
         for lname, lt in (("f16", s.half()), ("bf16", s.bfloat16())):
@@ -778,9 +782,8 @@ def run_tensor(args):
             low[lname] = {"points_per_s": n_s * args.steps / (ms_l * 1e-3),
                           "kernel_ms": st_l["timed_ms"] / max(st_l["timed_launches"], 1)}
         vol_tex = {}
-        for vname in ("TEX_DECASTELJAU", "TEX_SEILER", "TEX_SEILER_S8"):
-            var = bez.Variant[vname.replace("_S8", "")]
-            sp = 8 if vname.endswith("_S8") else 0
+        for vname in ("TEX_DECASTELJAU", "TEX_SEILER", "TEX_SEILER_S8", "TEX_SEILER_S4"):
+            var, sp = bez.Variant[VARIANT_SPEC[vname][0]], VARIANT_SPEC[vname][1]
             ms_vt, st_vt = timer.run(lambda var=var, sp=sp: bez.bez_eval_volume(v, 16, 16, 16, variant=var, out=vo,
                                                                                 ctx=ctx, tex_spread=sp),
                                      args.steps, args.warmup)
@@ -826,9 +829,9 @@ def run_tensor(args):
         got = bez.bez_eval_volume(vsub, 16, 16, 16, variant=var, ctx=ctx, tex_spread=spread).cpu().numpy()
         return float((np.abs(got.reshape(256, -1) - vref).max(axis=1) / vspan).max())
     for vname, rec in vol_tex.items():
-        rec["max_norm_err"] = vol_err(bez.Variant[vname.replace("_S8", "")], 8 if vname.endswith("_S8") else 0)
-    for fname, rec in spread_s.items():
-        rec["max_norm_err"] = surf_err(texs, bez.TexFormat[fname], spread=8)
+        rec["max_norm_err"] = vol_err(bez.Variant[VARIANT_SPEC[vname][0]], VARIANT_SPEC[vname][1])
+    for rec in spread_s.values():
+        rec["max_norm_err"] = surf_err(texs, bez.TexFormat[rec["tex_format"]], spread=rec["tex_spread"])
         rec["bar"] = TEX_BAR
         rec["meets_bar"] = rec["max_norm_err"] <= TEX_BAR
     surf_err_fp32 = surf_err(bez.Variant.AUTO)
@@ -851,8 +854,8 @@ def run_tensor(args):
                                            "kernel": "k_surface_tex<3, Seiler> (one bilinear read per row and "
                                                      "coordinate)"},
                     "surface_tex_unorm": unorm,
-                    "surface_tex_seiler_spread8": {**spread_s, "kernel": "k_surface_tex<3, Seiler> on 9 x 9 "
-                                                                         "spread tiles"},
+                    "surface_tex_seiler_spread": {**spread_s, "kernel": "k_surface_tex<3, Seiler> on spread "
+                                                                        "tiles (9 x 9 or 5 x 5 texels)"},
                     "volume_tex": vol_tex},
                    traffic=TRAFFIC_SURFACE_65536)
 

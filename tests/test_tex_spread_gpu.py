@@ -326,26 +326,29 @@ def test_spread_seiler_surface(s):
     print(f"\nspread-{s} Seiler surface: max normalised error {e.max():.3g}")
 
 
-def test_spread_seiler_surface_meets_bar_on_the_tensor_workload():
+@pytest.mark.parametrize("s", [8, 4])
+def test_spread_seiler_surface_meets_bar_on_the_tensor_workload(s):
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez, synth
     ctrl = synth.surfaces()[:4096]
+    ref = oracle.surface(ctrl, 32, 32).reshape(4096, -1, 3)
     for fmt in ("AUTO", "UNORM16"):
-        got = bez.bez_eval_surface(_dev(torch, ctrl), 32, 32, variant=bez.Variant.TEX_SEILER, tex_spread=8,
+        got = bez.bez_eval_surface(_dev(torch, ctrl), 32, 32, variant=bez.Variant.TEX_SEILER, tex_spread=s,
                                    tex_format=bez.TexFormat[fmt])
         torch.cuda.synchronize()
         got = got.cpu().numpy().reshape(4096, -1, 3)
-        ref = oracle.surface(ctrl, 32, 32).reshape(4096, -1, 3)
         e = normalised_error(got, ref)
         assert e.max() <= TEX_BAR, (fmt, e.max())
+        print(f"\nspread-{s} Seiler surfaces ({fmt}), tensor workload: max normalised error {e.max():.3g}")
 
 
-def test_spread_seiler_volume_meets_bar():
+@pytest.mark.parametrize("s", [8, 4])
+def test_spread_seiler_volume_meets_bar(s):
     # tricubic scalar volumes N(0,1) on 16^3: error over the volume's value range
     torch = need_gpu()
     from paper_2603_15447_gb300 import bez, synth
     v = synth.volumes()[:512]
-    got = bez.bez_eval_volume(_dev(torch, v), 16, 16, 16, variant=bez.Variant.TEX_SEILER, tex_spread=8)
+    got = bez.bez_eval_volume(_dev(torch, v), 16, 16, 16, variant=bez.Variant.TEX_SEILER, tex_spread=s)
     torch.cuda.synchronize()
     got = got.cpu().numpy().reshape(512, -1).astype(np.float64)
     ref = oracle.volume(v, 16, 16, 16).reshape(512, -1)
@@ -354,8 +357,9 @@ def test_spread_seiler_volume_meets_bar():
     assert e.max() <= TEX_BAR, e.max()
     # a-priori: the u stage's read per (row, j) is one column cubic per channel; v and w are convex
     cols = np.moveaxis(v[..., 0], 1, -1)                     # [n][j][l][i]
-    bound = _column_bound(cols, 8).max(axis=(1, 2)) + 64 * U * np.abs(v).max(axis=(1, 2, 3, 4))
+    bound = _column_bound(cols, s).max(axis=(1, 2)) + 64 * U * np.abs(v).max(axis=(1, 2, 3, 4))
     assert np.all(np.abs(got - ref).max(axis=1) <= bound)
+    print(f"\nspread-{s} Seiler volumes: max normalised error {e.max():.3g}")
 
 
 # ---------------------------------------------------------------- cubic zig-zag chains
