@@ -316,19 +316,25 @@ def run_precision(args, rank, world, local_rank):
         cout = torch.empty(args.n_chains, dtype=torch.float32, device=dev)
         chains = {}
         csteps = max(args.steps // 4, 3)
-        chain_variants = {"DECASTELJAU": ("DECASTELJAU", 0), "HORNER_CENTRED": ("HORNER_CENTRED", 0),
-                          "TEX_DECASTELJAU": ("TEX_DECASTELJAU", 0), "TEX_DECASTELJAU_S4": ("TEX_DECASTELJAU", 4)}
-        for name, (v, spread) in chain_variants.items():
-            def cstep(v=v, spread=spread, o=cout, n_t=args.chain_t, c=cctrl):
+        # name -> (variant, tex_spread, texel format)
+        chain_variants = {"DECASTELJAU": ("DECASTELJAU", 0, "AUTO"), "HORNER_CENTRED": ("HORNER_CENTRED", 0, "AUTO"),
+                          "TEX_DECASTELJAU": ("TEX_DECASTELJAU", 0, "AUTO"),
+                          "TEX_DECASTELJAU_S4": ("TEX_DECASTELJAU", 4, "AUTO"),
+                          "TEX_DECASTELJAU_S4_UNORM16": ("TEX_DECASTELJAU", 4, "UNORM16")}
+        for name, (v, spread, fmt) in chain_variants.items():
+            def cstep(v=v, spread=spread, fmt=fmt, o=cout, n_t=args.chain_t, c=cctrl):
                 bez.bez_eval_piecewise(c, 64, 2, None, n_t=n_t, variant=bez.Variant[v],
                                        out_mode=bez.OutMode.POLYLINE_LENGTH, t_mode=bez.TMode.HASH, seed=seed,
-                                       stream_id=12, out=o, ctx=ctx, tex_spread=spread)
+                                       stream_id=12, out=o, ctx=ctx, tex_spread=spread,
+                                       tex_format=bez.TexFormat[fmt])
             ms, st = timer.run(cstep, csteps, 2)
             n_pts = args.n_chains * args.chain_t * csteps
             chains[name] = {"points_per_s": n_pts / (ms * 1e-3),
                             "kernel_ms": st["timed_ms"] / max(st["timed_launches"], 1)}
             if spread:
                 chains[name]["tex_spread"] = spread
+            if fmt != "AUTO":
+                chains[name]["tex_format"] = fmt
         if not args.skip_accuracy:
             # points of the first chains at 4096 of their hashed parameters against the oracle
             import oracle
@@ -337,10 +343,10 @@ def run_precision(args, rank, world, local_rank):
             tch = (np.float32(64) * u.astype(np.float32)).astype(np.float32)
             cref = oracle.chain(cctrl_np[:nc], 64, 2, tch)
             cdiag = np.maximum(np.linalg.norm(cref.max(axis=1) - cref.min(axis=1), axis=-1), 2.0 ** -4)
-            for name, (v, spread) in chain_variants.items():
+            for name, (v, spread, fmt) in chain_variants.items():
                 pts = bez.bez_eval_piecewise(cctrl[:nc].contiguous(), 64, 2, None, n_t=nt, variant=bez.Variant[v],
                                              t_mode=bez.TMode.HASH, seed=seed, stream_id=12, ctx=ctx,
-                                             tex_spread=spread)
+                                             tex_spread=spread, tex_format=bez.TexFormat[fmt])
                 err = np.linalg.norm(pts.cpu().numpy().astype(np.float64) - cref, axis=-1).max(axis=1) / cdiag
                 bar = TEX_BAR if v.startswith("TEX") else FP32_BAR
                 chains[name].update({"max_norm_err": float(err.max()), "bar": bar,

@@ -216,7 +216,13 @@ bez_status bez_eval(bez_ctx ctx, const void* ctrl, int64_t n_curves, int degree,
  * axes share to the filter's 1/256 grid, so both weights round alike;
  * opts->tex_spread s >= 2 samples each 2x2 window on (s+1) x (s+1) texels
  * (an (N s + 1) x (s + 1) texture) for about s times less weight error.
- * Cubic chains (degree 3; Sec. 2.1: two quadratic chains front to back in a
+ * Texels are float4 (FP32 control points), half4 (F16), or, with
+ * opts->tex_format BEZ_TEX_UNORM16 and FP32 control points, unorm16 codes
+ * of each chain's per-component texel range (Sec. 2.3's low-bit-depth
+ * formats; the filtered value is mapped back by the range, adding at most
+ * range / 131070 per component); BEZ_TEX_UNORM8 returns
+ * BEZ_ERR_UNSUPPORTED (the free texels span tens of the control points'
+ * extent).  Cubic chains (degree 3; Sec. 2.1: two quadratic chains front to back in a
  * 3D texture) use an (N+1) x 2 x 2 texture read trilinearly along a 3D
  * zig-zag: the three texels one flip from a segment's corner average to its
  * second control point and the three two flips away to its third; spread 0

@@ -528,8 +528,10 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     if (tex && degree == 3 && o->tex_spread > 1)
         return fail(BEZ_ERR_UNSUPPORTED, "cubic zig-zag chains use the (N+1) x 2 x 2 layout (tex_spread 0 or 1)");
     if (tex && o->dtype == BEZ_BF16) return fail(BEZ_ERR_UNSUPPORTED, "no bfloat16 texture format");
-    if (tex && o->tex_format != BEZ_TEX_AUTO)
-        return fail(BEZ_ERR_UNSUPPORTED, "chain textures use float4 / half4 texels (tex_format AUTO)");
+    if (tex && o->tex_format == BEZ_TEX_UNORM8)
+        return fail(BEZ_ERR_UNSUPPORTED, "zig-zag texels span tens of the control points' extent: unorm8 is too coarse");
+    if (tex && o->tex_format == BEZ_TEX_UNORM16 && (degree != 2 || o->dtype != BEZ_F32))
+        return fail(BEZ_ERR_UNSUPPORTED, "unorm16 chain textures: quadratic chains of FP32 control points");
     if (!tex && o->tex_spread > 1)
         return fail(BEZ_ERR_UNSUPPORTED, "tex_spread applies to the zig-zag chain texture (TEX_DECASTELJAU)");
     if (degree > kMaxDegree) return fail(BEZ_ERR_UNSUPPORTED, "degree %d > %d", degree, kMaxDegree);
@@ -576,7 +578,7 @@ bez_status bez_eval_piecewise(bez_ctx c, const void* ctrl, int64_t n_chains, int
     LaunchResult r{0, cudaSuccess};
     if (tex) {
         if (c->tex_used) BEZ_CUDA(cudaStreamWaitEvent(s, c->tex_done, 0), "cudaStreamWaitEvent");
-        r = launch_tex_chain(a, tm, om, o->tex_spread, c->tex, s, h);
+        r = launch_tex_chain(a, tm, om, o->tex_spread, o->tex_format, c->tex, s, h);
         if (r.err == cudaErrorInvalidValue && r.launches == 0)
             return fail(BEZ_ERR_UNSUPPORTED, "%lld chains of %d segments do not fit one texture atlas",
                         (long long)n_chains, n_seg);

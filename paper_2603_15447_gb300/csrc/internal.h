@@ -112,7 +112,7 @@ LaunchResult launch_chain_decasteljau(const CurveArgs& a, int tm, int om, cudaSt
 LaunchResult launch_chain_seiler(const CurveArgs& a, int tm, int om, cudaStream_t s, const LaunchHooks& h);
 // Zig-zag texture for C0 quadratic chains (tex.cu).
 // `spread` s >= 1: each 2x2 window sampled on an (s+1) x (s+1) texel grid.
-LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, TexState& ts, cudaStream_t s,
+LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, int tex_format, TexState& ts, cudaStream_t s,
                               const LaunchHooks& h);
 constexpr int kChainMaxFloats = 3072;  // (n_seg*degree+1)*dim per chain staged in shared memory
 

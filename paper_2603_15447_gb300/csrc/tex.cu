@@ -753,26 +753,73 @@ LaunchResult launch_tex_coissue(const CurveArgs& a, int share, int tex_format, T
 // texture is (N s + 1) x (s + 1), and segment k is read at
 // (s (k + tau), s tau) or (s (k + tau), s (1 - tau)); the rounding terms
 // shrink by s (the twist term by s^2).
-__global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf, int fmt)
+// free texel F_0 of a quadratic chain: the minimax start (smallest largest
+// |F_k| over the chain)
+__device__ __forceinline__ float4 chain_f0(const CurveArgs& a, int64_t base)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.n_curves) return;
     const int N = a.n_seg, dim = a.dim;
-    const int64_t base = c * (int64_t)(2 * N + 1) * dim;
-    auto P = [&](int i, int k) { return load_elem(a.ctrl, a.dtype, base + (int64_t)i * dim + k); };
     float f0[4] = {0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < dim; ++k) {
         float g = 0.f, hmax = 0.f, hmin = 0.f;  // G_0 = 0
         for (int s = 0; s < N; ++s) {
-            g = 2.f * P(2 * s + 1, k) - g;      // G_(s+1)
+            g = 2.f * load_elem(a.ctrl, a.dtype, base + (int64_t)(2 * s + 1) * dim + k) - g;  // G_(s+1)
             const float h = (s & 1) ? g : -g;   // H_(s+1) = (-1)^(s+1) G_(s+1)
             hmax = fmaxf(hmax, h);
             hmin = fminf(hmin, h);
         }
         f0[k] = -0.5f * (hmax + hmin);
     }
+    return make_float4(f0[0], f0[1], f0[2], f0[3]);
+}
+
+// Unorm16 chain texels: the chain's per-component range over its column
+// texels P_2k and F_k (every spread texel is a convex combination of them),
+// recorded as (lo, scale) in rescale[2 c], rescale[2 c + 1].  Texels store
+// (v - lo) / scale and the evaluator maps the filtered value back by
+// lo + scale * f.
+__device__ __forceinline__ void chain_range(const CurveArgs& a, int64_t base, float4 F, float4& lo, float4& sc)
+{
+    const int N = a.n_seg, dim = a.dim;
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+    lo = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    for (int s = 0; s <= N; ++s) {
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < dim; ++k) p[k] = load_elem(a.ctrl, a.dtype, base + (int64_t)(2 * s) * dim + k);
+        const float4 Pe = make_float4(p[0], p[1], p[2], p[3]);
+        lo = min4(lo, min4(Pe, F));
+        hi = max4(hi, max4(Pe, F));
+        if (s < N) {
+            float m[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < dim; ++k) m[k] = load_elem(a.ctrl, a.dtype, base + (int64_t)(2 * s + 1) * dim + k);
+            F = make_float4(2.f * m[0] - F.x, 2.f * m[1] - F.y, 2.f * m[2] - F.z, 2.f * m[3] - F.w);
+        }
+    }
+    sc = sub4(hi, lo);
+    sc = make_float4(sc.x > 0.f ? sc.x : 1.f, sc.y > 0.f ? sc.y : 1.f, sc.z > 0.f ? sc.z : 1.f, sc.w > 0.f ? sc.w : 1.f);
+}
+
+__device__ __forceinline__ float4 unorm_of(float4 v, float4 lo, float4 sc)
+{
+    return make_float4(__fdiv_rn(v.x - lo.x, sc.x), __fdiv_rn(v.y - lo.y, sc.y), __fdiv_rn(v.z - lo.z, sc.z),
+                       __fdiv_rn(v.w - lo.w, sc.w));
+}
+
+__global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf, int fmt, float4* rescale)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_curves) return;
+    const int N = a.n_seg, dim = a.dim;
+    const int64_t base = c * (int64_t)(2 * N + 1) * dim;
+    auto P = [&](int i, int k) { return load_elem(a.ctrl, a.dtype, base + (int64_t)i * dim + k); };
     const int x0 = (int)(c % cw) * (N + 1), y0 = (int)(c / cw) * 2;
-    float4 F = make_float4(f0[0], f0[1], f0[2], f0[3]);
+    float4 F = chain_f0(a, base);
+    const bool un = fmt == TEXEL_UNORM16;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), sc = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (un) {
+        chain_range(a, base, F, lo, sc);
+        rescale[2 * c] = lo;
+        rescale[2 * c + 1] = sc;
+    }
     for (int s = 0; s <= N; ++s) {
         float p[4] = {0.f, 0.f, 0.f, 0.f};
         for (int k = 0; k < dim; ++k) p[k] = P(2 * s, k);
@@ -782,8 +829,8 @@ __global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf
             F = make_float4(__half2float(__float2half_rn(F.x)), __half2float(__float2half_rn(F.y)),
                             __half2float(__float2half_rn(F.z)), __half2float(__float2half_rn(F.w)));
         }
-        put(surf, fmt, x0 + s, y0 + (s & 1), 0, false, Pe);
-        put(surf, fmt, x0 + s, y0 + 1 - (s & 1), 0, false, F);
+        put(surf, fmt, x0 + s, y0 + (s & 1), 0, false, un ? unorm_of(Pe, lo, sc) : Pe);
+        put(surf, fmt, x0 + s, y0 + 1 - (s & 1), 0, false, un ? unorm_of(F, lo, sc) : F);
         if (s < N) {
             float m[4] = {0.f, 0.f, 0.f, 0.f};
             for (int k = 0; k < dim; ++k) m[k] = P(2 * s + 1, k);
@@ -796,33 +843,31 @@ __global__ void k_chain_pack(const CurveArgs a, int cw, cudaSurfaceObject_t surf
 // F_k as k_chain_pack does and stages the column texels (P_2k, F_k) in shared
 // memory; then the lanes write the (N s + 1) x (s + 1) grid column by column.
 constexpr int kChainPackWarps = 4;
-constexpr size_t kChainPackMaxSmem = 192 * 1024;  // spread chains up to 1535 segments
+constexpr size_t kChainPackMaxSmem = 192 * 1024;  // spread chains up to 1534 segments
 __global__ void __launch_bounds__(kChainPackWarps * 32) k_chain_pack_spread(const CurveArgs a, int cw, int sp,
-                                                                            cudaSurfaceObject_t surf, int fmt)
+                                                                            cudaSurfaceObject_t surf, int fmt,
+                                                                            float4* rescale)
 {
-    extern __shared__ float4 s_cols[];  // per warp: [N+1] P_2k, then [N+1] F_k
+    extern __shared__ float4 s_cols[];  // per warp: [N+1] P_2k, then [N+1] F_k, then (lo, scale)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * kChainPackWarps + wib;
     if (c >= a.n_curves) return;
     const int N = a.n_seg, dim = a.dim;
-    float4* Pc = s_cols + (size_t)wib * 2 * (N + 1);
+    float4* Pc = s_cols + (size_t)wib * (2 * (N + 1) + 2);
     float4* Fc = Pc + (N + 1);
+    float4* Rs = Fc + (N + 1);
     const int64_t base = c * (int64_t)(2 * N + 1) * dim;
     auto P = [&](int i, int k) { return load_elem(a.ctrl, a.dtype, base + (int64_t)i * dim + k); };
+    const bool un = fmt == TEXEL_UNORM16;
     if (lane == 0) {
-        float f0[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k = 0; k < dim; ++k) {
-            float g = 0.f, hmax = 0.f, hmin = 0.f;
-            for (int s = 0; s < N; ++s) {
-                g = 2.f * P(2 * s + 1, k) - g;
-                const float h = (s & 1) ? g : -g;
-                hmax = fmaxf(hmax, h);
-                hmin = fminf(hmin, h);
-            }
-            f0[k] = -0.5f * (hmax + hmin);
+        float4 F = chain_f0(a, base);
+        if (un) {
+            float4 lo, sc;
+            chain_range(a, base, F, lo, sc);
+            rescale[2 * c] = Rs[0] = lo;
+            rescale[2 * c + 1] = Rs[1] = sc;
         }
-        float4 F = make_float4(f0[0], f0[1], f0[2], f0[3]);
         for (int s = 0; s <= N; ++s) {
             float p[4] = {0.f, 0.f, 0.f, 0.f};
             for (int k = 0; k < dim; ++k) p[k] = P(2 * s, k);
@@ -853,7 +898,8 @@ __global__ void __launch_bounds__(kChainPackWarps * 32) k_chain_pack_spread(cons
         const float4 r1 = add4(scale4(1.f - xs, t01), scale4(xs, t11));
         for (int j = 0; j <= sp; ++j) {
             const float ys = inv * (float)j;
-            put(surf, fmt, x0 + i, y0 + j, 0, false, add4(scale4(1.f - ys, r0), scale4(ys, r1)));
+            const float4 v = add4(scale4(1.f - ys, r0), scale4(ys, r1));
+            put(surf, fmt, x0 + i, y0 + j, 0, false, un ? unorm_of(v, Rs[0], Rs[1]) : v);
         }
     }
 }
@@ -979,7 +1025,8 @@ __device__ __forceinline__ float4 zigzag_eval(const CurveArgs& a, cudaTextureObj
 }
 
 template <int TM, int OM, bool CUBIC = false>
-__global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cudaTextureObject_t tex, int cw, int sp)
+__global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cudaTextureObject_t tex, int cw, int sp,
+                                                           const float4* rescale)
 {
     __shared__ float s_stage[OM == OM_POINTS ? kWarps * 32 * 4 : 1];
     const int lane = threadIdx.x & 31;
@@ -991,12 +1038,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
         const float yb = (float)((int)(c / cw) * (sp + 1)) + 0.5f;
         const uint32_t kc = (TM == TM_HASH) ? lowbias32(a.key ^ (uint32_t)c) : 0u;
         const int n_t = a.n_t;
+        // unorm16 texels: the filtered value maps back by lo + scale * f
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), sc = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (rescale) {
+            lo = rescale[2 * c];
+            sc = rescale[2 * c + 1];
+        }
+        auto point = [&](int j) {
+            const float4 f = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp, CUBIC);
+            if (!rescale) return f;
+            return make_float4(fmaf(sc.x, f.x, lo.x), fmaf(sc.y, f.y, lo.y), fmaf(sc.z, f.z, lo.z),
+                               fmaf(sc.w, f.w, lo.w));
+        };
         if (OM == OM_POINTS) {
             float* stage = s_stage + wib * 32 * 4;
             for (int j0 = 0; j0 < n_t; j0 += 32) {
                 const int j = j0 + lane;
                 float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < n_t) P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp, CUBIC);
+                if (j < n_t) P = point(j);
                 const float pv[4] = {P.x, P.y, P.z, P.w};
                 for (int k = 0; k < dim; ++k) stage[lane * dim + k] = pv[k];
                 __syncwarp();
@@ -1012,10 +1071,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_chain_tex(const CurveArgs a, cu
             float acc = 0.f;
             float4 first = make_float4(0.f, 0.f, 0.f, 0.f), prev = first;
             if (jb < je) {
-                first = prev = zigzag_eval<TM>(a, tex, c, jb, kc, xb, yb, sp, CUBIC);
+                first = prev = point(jb);
 #pragma unroll 4
                 for (int j = jb + 1; j < je; ++j) {
-                    const float4 P = zigzag_eval<TM>(a, tex, c, j, kc, xb, yb, sp, CUBIC);
+                    const float4 P = point(j);
                     acc += seg_len4(P, prev);
                     prev = P;
                 }
@@ -1066,7 +1125,8 @@ static LaunchResult launch_tex_chain3(const CurveArgs& a, int tm, int om, TexSta
     const int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, (a.n_curves + kWarps - 1) / kWarps);
     cudaTextureObject_t tex = ts.chain3.tex;
     int cw_arg = cw, sp_arg = 1;
-    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg, (void*)&sp_arg};
+    const float4* no_rescale = nullptr;
+    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg, (void*)&sp_arg, (void*)&no_rescale};
     h.count(h.self);
     h.begin(h.self, s);
     e = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);
@@ -1074,8 +1134,8 @@ static LaunchResult launch_tex_chain3(const CurveArgs& a, int tm, int om, TexSta
     return {2, e};
 }
 
-LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, TexState& ts, cudaStream_t s,
-                              const LaunchHooks& h)
+LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, int tex_format, TexState& ts,
+                              cudaStream_t s, const LaunchHooks& h)
 {
     if (a.degree == 3) return launch_tex_chain3(a, tm, om, ts, s, h);
     const int sp = spread > 1 ? spread : 1;
@@ -1084,24 +1144,26 @@ LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, Te
     const int max_h = ts.max2d_h < kChainMaxCoord ? ts.max2d_h : kChainMaxCoord;
     if (wt64 > max_w) return {0, cudaErrorInvalidValue};
     const int wt = (int)wt64;
-    const int fmt = a.dtype == 1 ? 1 : 0;
+    const int fmt = tex_format == BEZ_TEX_UNORM16 ? TEXEL_UNORM16 : a.dtype == 1 ? TEXEL_F16 : TEXEL_F32;
     const int cw = tiles_per_row(a.n_curves, wt, max_w, sp + 1);
     const int64_t h_needed = (a.n_curves + cw - 1) / cw * (sp + 1);
     if (h_needed > max_h || (int64_t)cw * wt > max_w) return {0, cudaErrorInvalidValue};
     cudaError_t e = atlas_ensure(ts.chain, cw * wt, (int)h_needed, 0, fmt);
     if (e != cudaSuccess) return {0, e};
+    float4* rs = nullptr;
+    if ((e = rescale_buffer(ts, fmt, a.n_curves, &rs)) != cudaSuccess) return {0, e};
     h.count(h.self);
     if (sp == 1) {
-        k_chain_pack<<<(unsigned)((a.n_curves + 127) / 128), 128, 0, s>>>(a, cw, ts.chain.surf, fmt);
+        k_chain_pack<<<(unsigned)((a.n_curves + 127) / 128), 128, 0, s>>>(a, cw, ts.chain.surf, fmt, rs);
     } else {
-        const size_t smem = (size_t)kChainPackWarps * 2 * (a.n_seg + 1) * sizeof(float4);
+        const size_t smem = (size_t)kChainPackWarps * (2 * (a.n_seg + 1) + 2) * sizeof(float4);
         if (smem > kChainPackMaxSmem) return {0, cudaErrorInvalidValue};
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(k_chain_pack_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return {0, e};
         }
         k_chain_pack_spread<<<(unsigned)((a.n_curves + kChainPackWarps - 1) / kChainPackWarps), kChainPackWarps * 32,
-                              smem, s>>>(a, cw, sp, ts.chain.surf, fmt);
+                              smem, s>>>(a, cw, sp, ts.chain.surf, fmt, rs);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return {1, e};
@@ -1117,7 +1179,8 @@ LaunchResult launch_tex_chain(const CurveArgs& a, int tm, int om, int spread, Te
     const int grid = persistent_grid(kern, kWarps * 32, 0, h.sm_count, (a.n_curves + kWarps - 1) / kWarps);
     cudaTextureObject_t tex = ts.chain.tex;
     int cw_arg = cw, sp_arg = sp;
-    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg, (void*)&sp_arg};
+    const float4* rs_arg = rs;
+    void* args[] = {(void*)&a, (void*)&tex, (void*)&cw_arg, (void*)&sp_arg, (void*)&rs_arg};
     h.count(h.self);
     h.begin(h.self, s);
     e = cudaLaunchKernel(kern, dim3(grid), dim3(kWarps * 32), args, 0, s);

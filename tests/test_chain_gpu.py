@@ -182,6 +182,14 @@ def test_chain_argument_errors():
         bez.bez_eval_piecewise(torch.zeros((2, 7, 3), device="cuda"), 2, 3, torch.zeros(4, device="cuda"),
                                variant=bez.Variant.TEX_DECASTELJAU, tex_spread=2)
     assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:                  # zig-zag texels: unorm8 is too coarse
+        bez.bez_eval_piecewise(torch.zeros((2, 5, 3), device="cuda"), 2, 2, torch.zeros(4, device="cuda"),
+                               variant=bez.Variant.TEX_DECASTELJAU, tex_format=bez.TexFormat.UNORM8)
+    assert e.value.status == bez.Status.UNSUPPORTED
+    with pytest.raises(bez.BezError) as e:                  # unorm16: quadratic chains only
+        bez.bez_eval_piecewise(torch.zeros((2, 7, 3), device="cuda"), 2, 3, torch.zeros(4, device="cuda"),
+                               variant=bez.Variant.TEX_DECASTELJAU, tex_format=bez.TexFormat.UNORM16)
+    assert e.value.status == bez.Status.UNSUPPORTED
     with pytest.raises(bez.BezError) as e:
         bez.bez_eval_piecewise(torch.zeros((2, 1, 3), device="cuda"), 0, 2, torch.zeros(4, device="cuda"))
     assert e.value.status == bez.Status.INVALID_ARG

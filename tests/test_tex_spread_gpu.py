@@ -213,12 +213,13 @@ def test_spread_arguments():
 
 # ---------------------------------------------------------------- chains
 
-def _chain(torch, ctrl, n_seg, t=None, n_t=None, spread=1, t_mode=None, out_mode="POINTS", seed=0, stream_id=0):
+def _chain(torch, ctrl, n_seg, t=None, n_t=None, spread=1, t_mode=None, out_mode="POINTS", seed=0, stream_id=0,
+           tex_format="AUTO"):
     from paper_2603_15447_gb300 import bez
     out = bez.bez_eval_piecewise(_dev(torch, ctrl), n_seg, 2, _dev(torch, None if t is None else np.asarray(t, np.float32)),
                                  n_t=n_t, variant=bez.Variant.TEX_DECASTELJAU, out_mode=bez.OutMode[out_mode],
                                  t_mode=None if t_mode is None else bez.TMode[t_mode], seed=seed,
-                                 stream_id=stream_id, tex_spread=spread)
+                                 stream_id=stream_id, tex_spread=spread, tex_format=bez.TexFormat[tex_format])
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -236,9 +237,12 @@ def _free_texels_max(P):
     return np.abs(F).max()
 
 
-def chain_bound(ctrl, t, s):
+def chain_bound(ctrl, t, s, unorm16=False):
     """Per-point bound of the snapped read (module doc), plus FP32 rounding
-    of the texels (free texels up to M in magnitude)."""
+    of the texels (free texels up to M in magnitude); unorm16 texels add
+    their rounding to the nearest of 65,535 steps of the chain's range (at
+    most 2 M per component; the filtered value is a convex combination of
+    texels, so its error is at most one texel's)."""
     C, npts, dim = ctrl.shape
     N = (npts - 1) // 2
     P = ctrl.astype(np.float64)
@@ -249,42 +253,47 @@ def chain_bound(ctrl, t, s):
     dq = 2 * np.maximum(nrm(P1 - P0), nrm(P2 - P1))
     tw = nrm(P0 - 2 * P1 + P2)
     M = np.array([_free_texels_max(P[c]) for c in range(C)])[:, None]
-    return E8 / s * dq + E8 * tw / (s * s) + 24 * U * np.maximum(M, 1.0) * np.sqrt(dim)
+    quant = (2 * np.maximum(M, 1.0) / 131070 + 4 * U * np.maximum(M, 1.0)) * np.sqrt(dim) if unorm16 else 0.0
+    return E8 / s * dq + E8 * tw / (s * s) + 24 * U * np.maximum(M, 1.0) * np.sqrt(dim) + quant
 
 
+@pytest.mark.parametrize("tex_format", ["AUTO", "UNORM16"])
 @pytest.mark.parametrize("s", [1, 2, 4, 8])
-def test_chain_snapped_reads_within_bound(s):
+def test_chain_snapped_reads_within_bound(s, tex_format):
     torch = need_gpu()
     rng = np.random.default_rng(600 + s)
     n_seg = 16
     ctrl = rng.uniform(-1, 1, size=(257, 2 * n_seg + 1, 3)).astype(np.float32)
     t = (rng.uniform(0, 1, (257, 301)) * n_seg).astype(np.float32)
     t[:, :4] = [0.0, n_seg, 3.0, 4.0]                  # ends and two joints (even and odd segments)
-    got = _chain(torch, ctrl, n_seg, t, spread=s, t_mode="PER_CURVE")
+    got = _chain(torch, ctrl, n_seg, t, spread=s, t_mode="PER_CURVE", tex_format=tex_format)
     ref = oracle.chain(ctrl, n_seg, 2, t)
     err = np.linalg.norm(got - ref, axis=-1)
-    bound = chain_bound(ctrl, t, s)
+    bound = chain_bound(ctrl, t, s, unorm16=tex_format == "UNORM16")
     assert np.all(err <= bound), (err / bound).max()
-    np.testing.assert_array_equal(got[:, 0], ctrl[:, 0])
-    np.testing.assert_array_equal(got[:, 1], ctrl[:, -1])
-    print(f"\nzig-zag s={s}: max normalised error {normalised_error(got, ref).max():.3g}")
+    if tex_format == "AUTO":   # float texels hold the end points exactly
+        np.testing.assert_array_equal(got[:, 0], ctrl[:, 0])
+        np.testing.assert_array_equal(got[:, 1], ctrl[:, -1])
+    print(f"\nzig-zag s={s} ({tex_format}): max normalised error {normalised_error(got, ref).max():.3g}")
 
 
-def test_chain_spread4_meets_bar_on_the_chain_workload():
+@pytest.mark.parametrize("tex_format", ["AUTO", "UNORM16"])
+def test_chain_spread4_meets_bar_on_the_chain_workload(tex_format):
     # the benchmark's chain configuration (64 quadratic segments, control
-    # points U[-1,1]^3, parameters drawn U[0,64) in the kernel), spread 4
+    # points U[-1,1]^3, parameters drawn U[0,64) in the kernel), spread 4,
+    # float4 or unorm16 texels
     torch = need_gpu()
     from paper_2603_15447_gb300 import synth
     seed = synth.BASE_SEED + 1
     n, n_t = 2049, 4096
     ctrl, _ = synth.chains(n_chains=n, n_t=1)
-    got = _chain(torch, ctrl, 64, n_t=n_t, spread=4, t_mode="HASH", seed=seed, stream_id=12)
+    got = _chain(torch, ctrl, 64, n_t=n_t, spread=4, t_mode="HASH", seed=seed, stream_id=12, tex_format=tex_format)
     u = oracle.hash_t(seed, 12, 0, n, n_t)
     t = (np.float32(64) * u).astype(np.float32)
     ref = oracle.chain(ctrl, 64, 2, t)
     e = normalised_error(got, ref)
     assert e.max() <= TEX_BAR, e.max()
-    print(f"\nzig-zag spread 4, {n} chains x {n_t}: max normalised error {e.max():.3g}")
+    print(f"\nzig-zag spread 4 ({tex_format}), {n} chains x {n_t}: max normalised error {e.max():.3g}")
 
 
 # ---------------------------------------------------------------- surfaces and volumes
