@@ -242,6 +242,16 @@ struct GradCurve {
     }
 };
 
+// read-only load asking L2 to fetch the whole 256-byte block around the
+// address, so that a warp's streaming reads of t and the targets bring the
+// next rows into L2 with the current ones
+__device__ __forceinline__ float ld_stream(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 template <int M>
 __device__ __forceinline__ void load_sample(const float* tc, const float* vc, int dim, int n_t, int j, float& t,
                                             float (&v)[M])
@@ -250,10 +260,10 @@ __device__ __forceinline__ void load_sample(const float* tc, const float* vc, in
 #pragma unroll
     for (int k = 0; k < M; ++k) v[k] = 0.f;
     if (j < n_t) {
-        t = __ldg(tc + j);
+        t = ld_stream(tc + j);
 #pragma unroll
         for (int k = 0; k < M; ++k)
-            if (k < dim) v[k] = __ldg(vc + j * dim + k);
+            if (k < dim) v[k] = ld_stream(vc + j * dim + k);
     }
 }
 
