@@ -648,6 +648,29 @@ def run_plain(args):
         got = bez.bez_eval(ctrl, t, variant=bez.Variant[v], ctx=ctx).cpu().numpy().astype(np.float64)
         res[v]["max_norm_err"] = float((np.linalg.norm(got - ref, axis=-1).max(axis=1) / diag).max())
         res[v]["speedup_vs_horner"] = res[v]["points_per_s"] / res["HORNER"]["points_per_s"]
+    # steady state of repeated evaluation: 32 back-to-back launches captured
+    # in one CUDA graph and replayed, no L2 flush between them (the output
+    # stays in L2); supplementary to the flushed per-launch value above
+    steady = {}
+    n_graph = 32
+    for v in ("DECASTELJAU", "HORNER_CENTRED"):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(n_graph):
+                bez.bez_eval(ctrl, t, variant=bez.Variant[v], out=out, ctx=ctx)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_g = e0.elapsed_time(e1)
+        steady[v] = {"points_per_s": 4096 * 256 * n_graph * 10 / (ms_g * 1e-3),
+                     "us_per_launch": ms_g * 1e3 / (n_graph * 10)}
+        del graph
     head = res["DECASTELJAU"]
     return _record("plain: 4,096 cubic 3D curves x 256 shared uniform t, points stored", head["points_per_s"],
                    "points/s", steps, args.warmup, head["ms"], 4096 * 256 * 12 + 4096 * 48 + 1024,
@@ -655,7 +678,10 @@ def run_plain(args):
                    {"max_norm_err": head["max_norm_err"], "bar": FP32_BAR,
                     "variants": {v: {k: x for k, x in r.items() if k != "ms"} for v, r in res.items()},
                     "note": "12.6 MB of output fits in L2; the launch is latency-bound, so its HBM fraction is "
-                            "not a roofline statement"})
+                            "not a roofline statement",
+                    "graph_steady_state": {**steady, "launches_per_graph": n_graph,
+                                           "note": "back-to-back launches replayed from one CUDA graph, no L2 "
+                                                   "flush between them: repeated-evaluation rate, not the metric"}})
 
 
 def _batch_reference_sample(w, ids):
