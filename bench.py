@@ -67,7 +67,7 @@ TRAFFIC_PER_CURVE = {"HORNER_CENTRED": 6312448 / 131072}
 # the kernel behind each headline variant's fused length (cubic 3D, hashed t)
 KERNEL_NAME = {"HORNER_CENTRED": "k_curve_group<3, 4> (four lanes per curve)", "HALF2": "k_curve_h2"}
 TRAFFIC_SURFACE_65536 = 12652544 + 742988544
-TRAFFIC_FIT_65536x512 = 540098304 + 121953024
+TRAFFIC_FIT_65536x512 = 540180736 + 121996800
 EVAL_OPS = {"HORNER": 9, "HORNER_CENTRED": 9, "HALF2": 5, "BERNSTEIN": 19, "SEILER": 16, "DECASTELJAU": 36,
             "TEX_DECASTELJAU": 3, "TEX_SEILER": 3, "TEX_HYBRID": 10, "TEX_SEILER_S8": 3, "TEX_SEILER_S4": 3}
 # filtered fetches per point and the peak they are held to
