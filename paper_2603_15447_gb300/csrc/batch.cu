@@ -156,7 +156,10 @@ __device__ __forceinline__ SpanRec load_span_rec(const SpanRec* p)
 // Span extraction of span records [rec0, rec0 + n_rec), one thread per (span,
 // component).  Each thread reads its span's record and then, independently
 // of each other, the control points (and weights) and the operator rows.
-__global__ void __launch_bounds__(256) k_batch_setup(const BatchArgs a, int64_t rec0, int64_t n_rec)
+// 48 registers (5 blocks of 256 per SM, 16 bytes of spill) rather than 62:
+// the kernel waits on its operator and control-point loads, and the extra
+// warps hide more of that than the spill costs (2 % of the batch launch)
+__global__ void __launch_bounds__(256, 5) k_batch_setup(const BatchArgs a, int64_t rec0, int64_t n_rec)
 {
     const int per = a.dim + 1;  // component slots per span (dim + 1 for homogeneous NURBS)
     const int64_t total = n_rec * per;
