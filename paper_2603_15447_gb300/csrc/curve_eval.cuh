@@ -544,6 +544,7 @@ constexpr int kWarps = 8;  // warps per block; one curve per warp per iteration
 constexpr int kCurvesPerWarp = 8;  // curves per warp when the grid is not persistent
 constexpr int kPairsPerWarp = 4;   // the same for the two-curves-per-warp kernel
 constexpr int kGroupUnitsPerWarp = 2;  // and for the G-lanes-per-curve kernel
+constexpr int kGroupWarps = 16;        // warps per block of the G-lanes-per-curve kernel (2 blocks per SM)
 constexpr int kGroup8MinSamples = 128;  // samples per curve from which 8 lanes take a curve
 constexpr int kGroup4MinSamples = 256;  // and from which 4 lanes do
 
@@ -837,9 +838,10 @@ __global__ void __launch_bounds__(kWarps * 32, 5) k_curve_pair(const CurveArgs a
 // two lanes per curve measured slower at 1024 samples: 1.10e12 and 1.17e12
 // against 1.18e12 points/s for 4.)  64 registers (4 blocks per SM) with the
 // group loop unrolled by 4: 1.21e12 against 1.18e12 at 48 registers with 2;
-// 80 registers measured slower.
+// 80 registers measured slower.  Blocks of 16 warps (2 per SM) measured 1 %
+// faster than 8 (4 per SM) or 4 (8 per SM).
 template <int D, int G>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_curve_group(const CurveArgs a)
+__global__ void __launch_bounds__(kGroupWarps * 32, 2) k_curve_group(const CurveArgs a)
 {
     using E = Eval<VAR_HORNER_CENTRED, D, 3>;
     constexpr int PER = 3 * (D + 1);
@@ -850,7 +852,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_curve_group(const CurveArgs 
     const int wib = threadIdx.x >> 5;
     const int grp = lane / G, li = lane % G, base = lane - li;
     const int64_t n_units = (a.n_curves + CPW - 1) / CPW;
-    const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+    const int64_t n_warps = (int64_t)gridDim.x * kGroupWarps;
     float v[NL];
     auto load = [&](int64_t q) {
         const int64_t c = CPW * q + grp;
@@ -862,7 +864,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_curve_group(const CurveArgs 
     };
     const int n_t = a.n_t;
     const int chunk = ((n_t + G - 1) / G + 3) & ~3;
-    int64_t q = (int64_t)blockIdx.x * kWarps + wib;
+    int64_t q = (int64_t)blockIdx.x * kGroupWarps + wib;
     load(q);
     for (; q < n_units; q += n_warps) {
         const int64_t c = CPW * q + grp;
@@ -915,16 +917,16 @@ LaunchResult launch_group(const CurveArgs& a, cudaStream_t s, const LaunchHooks&
 {
     auto kern = k_curve_group<D, G>;
     const int64_t n_units = (a.n_curves + 32 / G - 1) / (32 / G);
-    const int64_t work = (n_units + kWarps - 1) / kWarps;
-    int grid = persistent_grid((const void*)kern, kWarps * 32, 0, h.sm_count, work);
+    const int64_t work = (n_units + kGroupWarps - 1) / kGroupWarps;
+    int grid = persistent_grid((const void*)kern, kGroupWarps * 32, 0, h.sm_count, work);
     if (work > grid) {
-        const int64_t per = (int64_t)kWarps * kGroupUnitsPerWarp;
+        const int64_t per = (int64_t)kGroupWarps * kGroupUnitsPerWarp;
         const int64_t g = (n_units + per - 1) / per;
         if (g > grid) grid = (int)(g < 2147483647 ? g : 2147483647);
     }
     h.count(h.self);
     h.begin(h.self, s);
-    kern<<<grid, kWarps * 32, 0, s>>>(a);
+    kern<<<grid, kGroupWarps * 32, 0, s>>>(a);
     cudaError_t err = cudaGetLastError();
     h.end(h.self, s);
     return {1, err};
