@@ -59,3 +59,21 @@ def test_roofline_block_arithmetic():
     assert ops == 152 * 128 * 2070.0e6 and "fallback" in note
     ops, note = bench.alu_peak({"sm_max_mhz": 2000.0}, sms=100)
     assert ops == 100 * 128 * 2000.0e6 and "device" in note
+
+
+def test_variant_table_and_fit_schedule():
+    # the spread texture variants resolve to TEX_SEILER with their spread,
+    # every texture variant has a fetch count and an eval op count, and the
+    # fit convergence check's cosine schedule starts at the full rate, ends
+    # at 1 % and never rises
+    import bench
+    assert bench.VARIANT_SPEC["TEX_SEILER_S8"] == ("TEX_SEILER", 8)
+    assert bench.VARIANT_SPEC["TEX_SEILER_S4"] == ("TEX_SEILER", 4)
+    for v in bench.TEX_VARIANTS:
+        assert v in bench.TEX_FETCHES and v in bench.EVAL_OPS
+    assert set(bench.VARIANT_SPEC) == set(bench.VARIANTS)
+    T = bench.FIT_CONV_STEPS
+    f = [bench.fit_lr_factor(k, T) for k in range(T + 1)]
+    assert f[0] == 1.0 and abs(f[-1] - 0.01) < 1e-12
+    assert all(a >= b for a, b in zip(f, f[1:]))
+    assert bench.fit_lr_factor(2 * T, T) == f[-1]
